@@ -1,0 +1,348 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
+
+This module holds no arithmetic of the LABFM method itself.  It generates
+node sets (perturbed Cartesian lattices, Sec. 3.1 of King, Lind & Nasar,
+"High order difference schemes using the Local Anisotropic Basis Function
+Method"), test fields with their exact derivatives, and nothing else.  Both
+the oracle tests and the GPU tests draw from here so that the two sides see
+identical inputs; neither side's numerics live here.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), used counter-style: draw ``k``
+of stream ``seed`` is ``mix(seed * G + (k + 1) * G)`` with ``G`` the 64-bit
+golden-ratio increment, mapped to a double in [0, 1) from its top 53 bits.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "splitmix64_u64",
+    "uniform01",
+    "normal01",
+    "NodeSet",
+    "jittered_lattice",
+    "variable_wall_nodes",
+    "FourierField",
+    "fourier_field",
+    "sincos_field",
+    "p6_field",
+    "op_c_vector",
+    "element_index",
+    "p_of_k",
+]
+
+_G = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64_u64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Draws ``offset .. offset+n-1`` of SplitMix64 stream ``seed`` as uint64."""
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed) * _G + k * _G
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Uniform doubles in [0, 1) built from the top 53 bits of each draw."""
+    z = splitmix64_u64(seed, n, offset)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Standard normal deviates by the Box-Muller transform of two uniform streams."""
+    u1 = uniform01(seed, n, offset)
+    u2 = uniform01(seed ^ 0x5DEECE66D, n, offset)
+    u1 = 1.0 - u1  # (0, 1]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+@dataclass
+class NodeSet:
+    """A 2D node distribution.
+
+    ``xy`` is float64 ``[n, 2]`` (row i = (x_i, y_i)), ``h`` float64 ``[n]`` the
+    per-node stencil scale (stencil radius is 2h), ``s`` float64 ``[n]`` the local
+    unperturbed spacing, ``order`` int8 ``[n]`` the per-node reconstruction
+    order k (all equal for uniform sets), ``periodic`` whether the box
+    ``[lo, hi)^2`` wraps.
+    """
+
+    xy: np.ndarray
+    h: np.ndarray
+    s: np.ndarray
+    order: np.ndarray
+    periodic: bool
+    lo: tuple
+    hi: tuple
+    wall: np.ndarray | None = None  # bool [n]: node lies on a wall
+
+    @property
+    def n(self) -> int:
+        return int(self.xy.shape[0])
+
+
+def jittered_lattice(n_side: int, h_over_s: float, k: int, jitter: float = 0.3,
+                     seed: int = 1, periodic: bool = True) -> NodeSet:
+    """Cartesian lattice on the unit square, spacing s = 1/n_side, each node at
+    ((i+1/2)s, (j+1/2)s) moved by independent U(-jitter*s, +jitter*s) offsets in x
+    and y (the "noisy Cartesian" distribution of Sec. 3.1, maximum perturbation
+    eps = jitter*s per coordinate).  Node index = j*n_side + i (row-major in y).
+    Periodic sets are wrapped back into [0, 1).
+    """
+    s = 1.0 / n_side
+    n = n_side * n_side
+    ii, jj = np.meshgrid(np.arange(n_side), np.arange(n_side), indexing="xy")
+    x = (ii.ravel() + 0.5) * s
+    y = (jj.ravel() + 0.5) * s
+    u = uniform01(seed, 2 * n)
+    x = x + (2.0 * u[0::2] - 1.0) * jitter * s
+    y = y + (2.0 * u[1::2] - 1.0) * jitter * s
+    if periodic:
+        x = np.where(x < 0.0, x + 1.0, x)
+        x = np.where(x >= 1.0, x - 1.0, x)
+        y = np.where(y < 0.0, y + 1.0, y)
+        y = np.where(y >= 1.0, y - 1.0, y)
+    xy = np.ascontiguousarray(np.stack([x, y], axis=1))
+    return NodeSet(xy=xy, h=np.full(n, h_over_s * s), s=np.full(n, s),
+                   order=np.full(n, k, dtype=np.int8), periodic=periodic,
+                   lo=(0.0, 0.0), hi=(1.0, 1.0))
+
+
+# h/s per order for the variable-resolution set (each above the critical h/dr of Sec. 2.2).
+H_OVER_S_BY_ORDER = {2: 1.0, 3: 1.1, 4: 1.4, 5: 1.6, 6: 1.8, 7: 2.0, 8: 2.2}
+
+
+def variable_wall_nodes(n_side: int, seed: int = 4, jitter: float = 0.3,
+                        stretch: float = 0.6, wall_order_cap: int = 4,
+                        wall_h_boost: float = 1.3) -> NodeSet:
+    """Non-periodic unit square with walls and a smoothly varying spacing.
+
+    Computational coordinates xi, eta take n_side equispaced values on [0, 1];
+    x = xi - stretch*sin(2 pi xi)/(2 pi) (same for y), so the local spacing
+    s = (1 - stretch*cos(2 pi xi)) / (n_side - 1) varies by (1+stretch)/(1-stretch)
+    (4x at stretch 0.6): fine at the walls, coarse in the middle.  Interior nodes
+    are jittered by +-jitter*s per coordinate, wall nodes only along their wall,
+    corners are fixed.  Order k_i = min(8, 2 + floor(7 x_i)) rises left to right,
+    capped at ``wall_order_cap`` within 2h of a wall (one-sided stencils keep
+    order up to 4 there, Sec. 3.1); h_i = (h/s)(k_i) * s_i, times
+    ``wall_h_boost`` in that band (larger stencils at incomplete support).
+    """
+    m = n_side
+    xi = np.linspace(0.0, 1.0, m)
+    ii, jj = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+    xi_n = xi[ii.ravel()]
+    eta_n = xi[jj.ravel()]
+    tw = 2.0 * np.pi
+    x = xi_n - stretch * np.sin(tw * xi_n) / tw
+    y = eta_n - stretch * np.sin(tw * eta_n) / tw
+    sx = (1.0 - stretch * np.cos(tw * xi_n)) / (m - 1)
+    sy = (1.0 - stretch * np.cos(tw * eta_n)) / (m - 1)
+    s = np.minimum(sx, sy)
+    n = m * m
+    u = uniform01(seed, 2 * n)
+    on_x_wall = (ii.ravel() == 0) | (ii.ravel() == m - 1)
+    on_y_wall = (jj.ravel() == 0) | (jj.ravel() == m - 1)
+    jx = (2.0 * u[0::2] - 1.0) * jitter * sx
+    jy = (2.0 * u[1::2] - 1.0) * jitter * sy
+    x = x + np.where(on_x_wall, 0.0, jx)
+    y = y + np.where(on_y_wall, 0.0, jy)
+    x = np.clip(x, 0.0, 1.0)
+    y = np.clip(y, 0.0, 1.0)
+    k = np.minimum(8, 2 + np.floor(7.0 * x).astype(np.int64))
+    hs = np.array([H_OVER_S_BY_ORDER[int(v)] for v in range(9) if v >= 2])
+    h = hs[k - 2] * s
+    dwall = np.minimum.reduce([x, 1.0 - x, y, 1.0 - y])
+    band = dwall < 2.0 * h * wall_h_boost
+    k = np.where(band, np.minimum(k, wall_order_cap), k)
+    h = np.where(band, hs[k - 2] * s * wall_h_boost, hs[k - 2] * s)
+    xy = np.ascontiguousarray(np.stack([x, y], axis=1))
+    return NodeSet(xy=xy, h=h.astype(np.float64), s=s, order=k.astype(np.int8),
+                   periodic=False, lo=(0.0, 0.0), hi=(1.0, 1.0),
+                   wall=(on_x_wall | on_y_wall))
+
+
+# ----------------------------------------------------------------------------------
+# Index conventions of the monomial vector X and derivative vector D (Sec. 2):
+# total degree n = 1, 2, ...; within a degree the power of x runs from n down to 0.
+# ----------------------------------------------------------------------------------
+
+def p_of_k(k: int) -> int:
+    """Number of elements of X up to total degree k in 2D: p = (k^2 + 3k)/2 (Sec. 2.1)."""
+    return (k * k + 3 * k) // 2
+
+
+def element_index(a: int, b: int) -> int:
+    """0-based position of x^a y^b (derivative d^(a+b)/dx^a dy^b) in X and D."""
+    n = a + b
+    return p_of_k(n - 1) + (n - a)
+
+
+def op_c_vector(name: str, k: int) -> np.ndarray:
+    """Target vector C^d (length p(k)) for the named operator.
+
+    ``dx``, ``dy``: first derivatives; ``lap``: Laplacian (elements 3 and 5,
+    Sec. 2); ``lap2``: biharmonic, ``lap3``: triharmonic, ``lap4``: nabla^8,
+    each the multinomial expansion of (d_xx + d_yy)^m (Sec. 2.3 gives the
+    element positions for m = 2 and m = 3; m = 4 follows the same rule).  The
+    hyperviscosity coefficient and its sign are left to the caller.
+    """
+    p = p_of_k(k)
+    c = np.zeros(p)
+    if name == "dx":
+        c[element_index(1, 0)] = 1.0
+    elif name == "dy":
+        c[element_index(0, 1)] = 1.0
+    elif name.startswith("lap"):
+        m = 1 if name == "lap" else int(name[3:])
+        if 2 * m > k:
+            raise ValueError(f"nabla^{2*m} needs order >= {2*m}, got {k}")
+        for t in range(m + 1):
+            c[element_index(2 * (m - t), 2 * t)] = math.comb(m, t)
+    else:
+        raise ValueError(name)
+    return c
+
+
+# ----------------------------------------------------------------------------------
+# Test fields with exact derivatives.
+# ----------------------------------------------------------------------------------
+
+class _Field:
+    def value(self, xy):  # pragma: no cover - interface
+        raise NotImplementedError
+
+    def deriv(self, name, xy):  # pragma: no cover - interface
+        raise NotImplementedError
+
+
+class SinCosField(_Field):
+    """f = sin(2 pi x + ax) cos(2 pi y + ay) (period 1 in x and y; ax = ay = 0 by default)."""
+
+    def __init__(self, ax: float = 0.0, ay: float = 0.0):
+        self.ax, self.ay = ax, ay
+
+    def value(self, xy):
+        return np.sin(2 * np.pi * xy[:, 0] + self.ax) * np.cos(2 * np.pi * xy[:, 1] + self.ay)
+
+    def deriv(self, name, xy):
+        tp = 2 * np.pi
+        tx, ty = tp * xy[:, 0] + self.ax, tp * xy[:, 1] + self.ay
+        sx, cx = np.sin(tx), np.cos(tx)
+        sy, cy = np.sin(ty), np.cos(ty)
+        if name == "dx":
+            return tp * cx * cy
+        if name == "dy":
+            return -tp * sx * sy
+        if name.startswith("lap"):
+            m = 1 if name == "lap" else int(name[3:])
+            return (-2 * tp * tp) ** m * sx * cy
+        raise ValueError(name)
+
+
+def sincos_field(ax: float = 0.0, ay: float = 0.0) -> SinCosField:
+    return SinCosField(ax, ay)
+
+
+@dataclass
+class FourierField(_Field):
+    """f = sum_m a_m cos(2 pi (kx_m x + ky_m y) + phi_m): periodic on the unit square."""
+
+    kx: np.ndarray
+    ky: np.ndarray
+    amp: np.ndarray
+    phase: np.ndarray
+
+    def _theta(self, xy):
+        return 2 * np.pi * (np.outer(xy[:, 0], self.kx) + np.outer(xy[:, 1], self.ky)) + self.phase
+
+    def value(self, xy):
+        return np.cos(self._theta(xy)) @ self.amp
+
+    def deriv(self, name, xy):
+        th = self._theta(xy)
+        tp = 2 * np.pi
+        if name == "dx":
+            return -np.sin(th) @ (self.amp * tp * self.kx)
+        if name == "dy":
+            return -np.sin(th) @ (self.amp * tp * self.ky)
+        if name.startswith("lap"):
+            m = 1 if name == "lap" else int(name[3:])
+            k2 = (tp * tp) * (self.kx.astype(np.float64) ** 2 + self.ky.astype(np.float64) ** 2)
+            return np.cos(th) @ (self.amp * (-k2) ** m)
+        raise ValueError(name)
+
+
+def fourier_field(n_modes: int = 16, kmax: int = 32, seed: int = 3) -> FourierField:
+    """Sum of ``n_modes`` Fourier modes with integer wavenumbers uniform in
+    [-kmax, kmax]^2 minus the origin, N(0,1) amplitudes and U[0, 2pi) phases."""
+    kx = np.zeros(n_modes, dtype=np.int64)
+    ky = np.zeros(n_modes, dtype=np.int64)
+    got, off = 0, 0
+    span = 2 * kmax + 1
+    while got < n_modes:
+        u = uniform01(seed, 2, off)
+        off += 2
+        a = int(u[0] * span) - kmax
+        b = int(u[1] * span) - kmax
+        if a == 0 and b == 0:
+            continue
+        kx[got], ky[got] = a, b
+        got += 1
+    amp = normal01(seed + 1, n_modes)
+    phase = 2 * np.pi * uniform01(seed + 2, n_modes)
+    return FourierField(kx=kx, ky=ky, amp=amp, phase=phase)
+
+
+class P6Field(_Field):
+    """The polynomial test function of Eq. (p6): 1 + (xh yh)^4 + sum_{n=1..6} (xh^n + yh^n),
+    xh = x - 0.1453, yh = y - 0.16401 (H = 1).  Its derivatives of order > 8 vanish."""
+
+    X0 = 0.1453
+    Y0 = 0.16401
+
+    @staticmethod
+    def _poly_terms():
+        # list of (coef, a, b) with value coef * xh^a * yh^b
+        t = [(1.0, 0, 0), (1.0, 4, 4)]
+        for n in range(1, 7):
+            t.append((1.0, n, 0))
+            t.append((1.0, 0, n))
+        return t
+
+    def _d(self, xy, dx_order, dy_order):
+        xh = xy[:, 0] - self.X0
+        yh = xy[:, 1] - self.Y0
+        out = np.zeros(xy.shape[0])
+        for c, a, b in self._poly_terms():
+            if dx_order > a or dy_order > b:
+                continue
+            ca = math.perm(a, dx_order)
+            cb = math.perm(b, dy_order)
+            out += c * ca * cb * xh ** (a - dx_order) * yh ** (b - dy_order)
+        return out
+
+    def value(self, xy):
+        return self._d(xy, 0, 0)
+
+    def deriv(self, name, xy):
+        if name == "dx":
+            return self._d(xy, 1, 0)
+        if name == "dy":
+            return self._d(xy, 0, 1)
+        if name.startswith("lap"):
+            m = 1 if name == "lap" else int(name[3:])
+            return sum(math.comb(m, t) * self._d(xy, 2 * (m - t), 2 * t) for t in range(m + 1))
+        raise ValueError(name)
+
+
+def p6_field() -> P6Field:
+    return P6Field()

@@ -1,0 +1,229 @@
+"""CPU oracle for the LABFM weight build, operator application and RK4 driver.
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline of ``bench.py`` use this package.  The library under
+``paper_1912_06441_gb300`` never imports it, and it imports nothing from there.
+
+The numerics live in ``labfm_oracle.c`` (plain C, FP64; a second build in
+``long double`` measures the FP64 rounding floor).  This module compiles it
+with gcc on first use and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "labfm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIBS: dict = {}
+
+RBF = {"wendland_c2": 0, "quadratic": 1, "cone": 2, "wendland_c6": 3, "gaussian": 4}
+PMAX = 44
+ST_OK, ST_SINGULAR, ST_UNDERSAMPLED, ST_NONFINITE = 0, 1, 2, 3
+
+
+def lib_path(precision: str = "f64") -> str:
+    return os.path.join(_BUILD, f"liblabfm_oracle_{precision}.so")
+
+
+def build(precision: str = "f64", force: bool = False) -> str:
+    """Compile the oracle (``f64`` or ``ld`` = long double) into ``oracle/_build``."""
+    out = lib_path(precision)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(_BUILD, exist_ok=True)
+    real = "double" if precision == "f64" else "long double"
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+           f"-DORC_REAL={real}", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+_P = ct.c_void_p
+_I64 = ct.c_int64
+_I = ct.c_int
+_D = ct.c_double
+
+
+def _configure(lib):
+    lib.orc_neighbours.argtypes = [_I64, _P, _P, _I, _P, _P, _P, _I64, _P, _P, _I64]
+    lib.orc_neighbours.restype = _I
+    lib.orc_build_weights.argtypes = [_P, _P, _I, _P, _P, _P, _I64, _P, _P, _P, _I, _I, _I, _P,
+                                      _P, _P, _P, _P, _I]
+    lib.orc_build_weights.restype = _I
+    lib.orc_apply.argtypes = [_P, _I64, _P, _P, _P, _I, _P, _P, _I]
+    lib.orc_apply.restype = None
+    lib.orc_rk4.argtypes = [_I64, _P, _P, _P, _I, _P, _P, _D, _I64, _P, _I]
+    lib.orc_rk4.restype = _I
+    lib.orc_rbf_derivs.argtypes = [_I, _D, _P]
+    lib.orc_rbf_derivs.restype = None
+    lib.orc_dr.argtypes = [_D, _D, _I, _P]
+    lib.orc_dr.restype = None
+    lib.orc_monomials.argtypes = [_D, _D, _I, _P]
+    lib.orc_monomials.restype = None
+    lib.orc_abfs.argtypes = [_I, _D, _D, _I, _P]
+    lib.orc_abfs.restype = None
+    lib.orc_p_of_k.argtypes = [_I]
+    lib.orc_p_of_k.restype = _I
+    lib.orc_real_mant_bits.argtypes = []
+    lib.orc_real_mant_bits.restype = _I
+    return lib
+
+
+def _lib(precision: str = "f64"):
+    with _LOCK:
+        if precision not in _LIBS:
+            _LIBS[precision] = _configure(ct.CDLL(build(precision)))
+        return _LIBS[precision]
+
+
+def compile_variant(source_text: str, out_path: str, precision: str = "f64"):
+    """Compile an edited copy of the oracle source and load it (used only by the test that
+    plants mistakes in the oracle to check that its pins catch them)."""
+    src = out_path + ".c"
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    real = "double" if precision == "f64" else "long double"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                    f"-DORC_REAL={real}", "-o", out_path, src, "-lm"], check=True)
+    return _configure(ct.CDLL(out_path))
+
+
+def source_text() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def p_of_k(k: int) -> int:
+    return int(_lib().orc_p_of_k(k))
+
+
+def mant_bits(precision: str = "f64") -> int:
+    return int(_lib(precision).orc_real_mant_bits())
+
+
+def neighbours(xy, h, periodic, lo=(0.0, 0.0), hi=(1.0, 1.0), queries=None, precision="f64"):
+    """Brute-force stencils (Sec. 2).  Returns (row_ptr int64 [nq+1], col int32 [nnz])."""
+    lib = _lib(precision)
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    n = xy.shape[0]
+    q = None if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    nq = n if q is None else q.shape[0]
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    rp = np.zeros(nq + 1, dtype=np.int64)
+    rc = lib.orc_neighbours(n, _ptr(xy), _ptr(h), int(periodic), _ptr(lo), _ptr(hi), _ptr(q), nq,
+                            _ptr(rp), None, 0)
+    assert rc == 0
+    col = np.zeros(max(int(rp[-1]), 1), dtype=np.int32)
+    rc = lib.orc_neighbours(n, _ptr(xy), _ptr(h), int(periodic), _ptr(lo), _ptr(hi), _ptr(q), nq,
+                            _ptr(rp), _ptr(col), col.shape[0])
+    assert rc == 0
+    return rp, col[: int(rp[-1])]
+
+
+def build_weights(xy, h, periodic, row_ptr, col, C, k=None, order=None, rbf="wendland_c2",
+                  lo=(0.0, 0.0), hi=(1.0, 1.0), queries=None, precision="f64", nthreads=0,
+                  want_mhat=False):
+    """Weights for every stencil entry (Eqs. disc_form, lsys, w_abf).
+
+    ``C`` is ``[n_ops, p]`` (or ``[n_ops, 44]``) in D ordering, physical units.
+    Returns dict with ``w`` ``[nnz, n_ops]``, ``status`` ``[nq]``, ``piv_ratio``
+    ``[nq]`` and optionally ``mhat`` ``[nq, p, p]``.
+    """
+    lib = _lib(precision)
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    C = np.atleast_2d(np.asarray(C, dtype=np.float64))
+    n_ops = C.shape[0]
+    Cp = np.zeros((n_ops, PMAX))
+    Cp[:, : C.shape[1]] = C
+    q = None if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    nq = xy.shape[0] if q is None else q.shape[0]
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    nnz = int(rp[-1])
+    w = np.zeros((max(nnz, 1), n_ops))
+    st = np.zeros(nq, dtype=np.int32)
+    pr = np.zeros(nq)
+    od = None if order is None else np.ascontiguousarray(order, dtype=np.int8)
+    mh = np.zeros((nq, PMAX, PMAX)) if want_mhat else None
+    rc = lib.orc_build_weights(_ptr(xy), _ptr(h), int(periodic), _ptr(np.asarray(lo, np.float64)),
+                               _ptr(np.asarray(hi, np.float64)), _ptr(q), nq, _ptr(rp), _ptr(cl),
+                               _ptr(od), int(k or 0), RBF[rbf], n_ops, _ptr(Cp), _ptr(w), _ptr(st),
+                               _ptr(pr), _ptr(mh), int(nthreads))
+    assert rc == 0
+    out = {"w": w[:nnz], "status": st, "piv_ratio": pr}
+    if want_mhat:
+        kk = k if k is not None else int(np.max(order))
+        p = p_of_k(kk)
+        out["mhat"] = mh.reshape(nq, PMAX * PMAX)[:, : p * p].reshape(nq, p, p)
+    return out
+
+
+def apply(row_ptr, col, w, f, queries=None, precision="f64", nthreads=0):
+    """out[d, q] = sum_j (f_j - f_i) w_ji^d (Eq. general_do)."""
+    lib = _lib(precision)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    n_ops = w.shape[1]
+    q = None if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    nq = rp.shape[0] - 1
+    out = np.zeros((n_ops, nq))
+    lib.orc_apply(_ptr(q), nq, _ptr(rp), _ptr(cl), _ptr(w), n_ops, _ptr(f), _ptr(out), int(nthreads))
+    return out
+
+
+def rk4(row_ptr, col, w, beta, u0, dt, nsteps, frozen=None, precision="f64", nthreads=0):
+    """Classical RK4 for du/dt = sum_d beta_d L^d(u) over all nodes (Sec. 4.1)."""
+    lib = _lib(precision)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    u = np.array(u0, dtype=np.float64, copy=True)
+    fz = None if frozen is None else np.ascontiguousarray(frozen, dtype=np.uint8)
+    rc = lib.orc_rk4(u.shape[0], _ptr(rp), _ptr(cl), _ptr(w), w.shape[1], _ptr(beta), _ptr(u), float(dt),
+                     int(nsteps), _ptr(fz), int(nthreads))
+    assert rc == 0
+    return u
+
+
+def rbf_derivs(rbf, q, precision="f64"):
+    d = np.zeros(4)
+    _lib(precision).orc_rbf_derivs(RBF[rbf], float(q), _ptr(d))
+    return d
+
+
+def dr(x, y, kmax, precision="f64"):
+    """Table t[a, b] = d^(a+b)|r| / dx^a dy^b at (x, y), a + b <= kmax."""
+    out = np.zeros((kmax + 1) * (kmax + 1))
+    _lib(precision).orc_dr(float(x), float(y), int(kmax), _ptr(out))
+    return out.reshape(kmax + 1, kmax + 1)
+
+
+def monomials(x, y, k, precision="f64"):
+    out = np.zeros(p_of_k(k))
+    _lib(precision).orc_monomials(float(x), float(y), int(k), _ptr(out))
+    return out
+
+
+def abfs(rbf, x, y, k, precision="f64"):
+    out = np.zeros(p_of_k(k))
+    _lib(precision).orc_abfs(RBF[rbf], float(x), float(y), int(k), _ptr(out))
+    return out

@@ -1,0 +1,59 @@
+"""Each pin must be able to fail: plant one plausible mistake at a time in a copy of
+the oracle (compiled separately, on the CPU) and check that at least one pin rejects it."""
+import pytest
+
+import oracle
+from tests import test_oracle_pins as P
+
+MUTATIONS = {
+    "transposed outer product X (x) W": ("s += X[j * p + m] * W[j * p + c];",
+                                         "s += X[j * p + c] * W[j * p + m];"),
+    "dropped d2W0/dr2 term of element 3": ("if (a == 2) v += f2 * rx * rx;", "if (a == 2) v += 0 * rx * rx;"),
+    "wrong sign of a d2W0/dr2 term, order 3": ("if (a == 3) v += f3 * rx * rx * rx + f2 * 3 * rx * rxx;",
+                                               "if (a == 3) v += f3 * rx * rx * rx - f2 * 3 * rx * rxx;"),
+    "minimum image shifted the wrong way": ("if (dx > halfL[0]) dx -= L[0];", "if (dx > halfL[0]) dx += L[0];"),
+    "h-scaling exponent off by one": ("for (int t = 0; t < a + b; t++) s /= hi;",
+                                      "for (int t = 0; t < a + b - 1; t++) s /= hi;"),
+    "factorial dropped from X": ("for (int t = 1; t <= a; t++) v = v * x / (real)t;",
+                                 "for (int t = 1; t <= a; t++) v = v * x;"),
+    "binomial dropped in the |r| recurrence": ("rhs -= binom(a, a2) * binom(b, b2) * dr[a2][b2] * dr[a - a2][b - b2];",
+                                               "rhs -= binom(a, a2) * dr[a2][b2] * dr[a - a2][b - b2];"),
+    "f_j instead of f_j - f_i": ("s += ((real)f[col[e]] - (real)f[i]) * (real)w[e * n_ops + d];",
+                                 "s += ((real)f[col[e]]) * (real)w[e * n_ops + d];"),
+    "RK4 stage weight": ("(k1[i] + 2 * k2[i] + 2 * k3[i] + k4[i])", "(k1[i] + k2[i] + 2 * k3[i] + k4[i])"),
+    "truncation rule ignored (W'' kept at order 4)": ("        } else if (n == 3) {",
+                                                      "        } else if (n == 4) { v += f2 * rx * rx * rx * rx;\n        } else if (n == 3) {"),
+    "stencil radius h instead of 2h": ("double R = 2.0 * h[i];", "double R = h[i];"),
+}
+
+PINS = [
+    lambda: P.test_abfs_match_printed_forms("wendland_c2"),
+    lambda: P.test_abfs_match_printed_forms("cone"),
+    P.test_r_derivatives_vs_sympy,
+    P.test_x_vector_printed,
+    P.test_neighbours_vs_kdtree,
+    P.test_lattice_parity_zeros,
+    P.test_assembly_and_solve_vs_lapack,
+    lambda: P.test_polynomial_reproduction(4, 1.6, "quadratic", 1e-11),
+    lambda: P.test_polynomial_reproduction(6, 2.0, "wendland_c2", 1e-9),
+    P.test_rk4_linear_system_is_taylor_polynomial,
+    P.test_abfs_truncated_high_orders_vs_sympy,
+]
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path, monkeypatch):
+    old, new = MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, name
+    lib = oracle.compile_variant(src.replace(old, new), str(tmp_path / "mutant.so"))
+    monkeypatch.setitem(oracle._LIBS, "f64", lib)
+    caught = []
+    for pin in PINS:
+        try:
+            pin()
+        except AssertionError:
+            caught.append(pin)
+        except Exception:  # a crash (e.g. a bad stencil size) also rejects the mutant
+            caught.append(pin)
+    assert caught, f"no pin caught: {name}"
