@@ -1,0 +1,178 @@
+/*
+ * labfm.h -- C ABI of the GB300 (sm_103a) implementation of the Local Anisotropic
+ * Basis Function Method (LABFM) of King, Lind & Nasar, "High order difference
+ * schemes using the Local Anisotropic Basis Function Method".
+ *
+ * The library computes, for every node i of a 2D node set, the stencil weights
+ * w_ji^d of Eq. (w_abf) and applies the discrete operators L_i^d of
+ * Eq. (general_do).  All compute runs in CUDA kernels of this library; the
+ * caller supplies device memory (e.g. from PyTorch) and a CUDA stream.
+ *
+ * Conventions (every entry point):
+ *  - Pointers named "device" must be device (or managed) memory readable by the
+ *    context's device; pointers named "host" are ordinary host memory.
+ *  - Caller-owned buffers are only read (or written where stated) during the
+ *    call's stream-ordered work; the library keeps no reference to them.
+ *  - Context-owned buffers (stencils, weights, scratch) live until the context is
+ *    destroyed or the buffer is rebuilt.
+ *  - Work is enqueued on the context stream.  Calls that return counts or
+ *    statuses (labfm_build_neighbours, labfm_build_weights) synchronise that
+ *    stream before returning; labfm_apply and labfm_step do not.
+ *  - No C++ exception crosses the ABI; failures return a labfm_status and
+ *    labfm_last_error() gives a message.  Invalid arguments are rejected on the
+ *    host before any kernel is launched.
+ *  - Per-node numerical failure is data, not an abort: see LABFM_NODE_*.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LABFM_H
+#define LABFM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct labfm_ctx labfm_ctx;
+
+typedef enum {
+    LABFM_OK = 0,
+    LABFM_ERR_ARG = 1,      /* invalid argument, detected on the host */
+    LABFM_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+    LABFM_ERR_NOMEM = 3,    /* device allocation failed */
+    LABFM_ERR_CAPACITY = 4, /* a size limit of this build was exceeded (message says which) */
+    LABFM_ERR_SINGULAR = 5, /* weights built, but >= 1 node was flagged (see node_status) */
+    LABFM_ERR_TIMEOUT = 6,  /* a bounded device wait gave up */
+    LABFM_ERR_STATE = 7     /* call out of order (e.g. apply before build_weights) */
+} labfm_status;
+
+/* Fundamental RBFs W0(q), q = |r|/h, support [0, 2] (Sec. 2.2, Appendix A). */
+enum {
+    LABFM_RBF_WENDLAND_C2 = 0, /* 7/(4 pi) (1 - q/2)^4 (1 + 2q) (standard Wendland C2, normalised as Appendix A asks) */
+    LABFM_RBF_QUADRATIC = 1,   /* 3/(16 pi) (q - 2)^2, Appendix A.1 */
+    LABFM_RBF_CONE = 2,        /* 3/(4 pi) (1 - q/2), Sec. 2.2 */
+    LABFM_RBF_WENDLAND_C6 = 3, /* 78/(28 pi) (1 - q/2)^8 (4q^3 + 6.25q^2 + 4q + 1), Appendix A.2 */
+    LABFM_RBF_GAUSSIAN = 4     /* 9/pi exp(-9 q^2), Appendix A.3 */
+};
+
+/* Arithmetic of the moment-matrix assembly (Eq. disc_form) and solve (Eq. lsys). */
+enum {
+    LABFM_PREC_FP64 = 0 /* everything in IEEE double */
+};
+
+/* Storage type of weights and fields. */
+enum { LABFM_F64 = 0, LABFM_F32 = 1 };
+
+/* Per-node status written by labfm_build_weights. */
+enum {
+    LABFM_NODE_OK = 0,
+    LABFM_NODE_SINGULAR = 1,     /* a pivot of the elimination was exactly zero or not finite */
+    LABFM_NODE_UNDERSAMPLED = 2, /* fewer neighbours than p: M_i (a sum of N_i rank-one terms) is singular */
+    LABFM_NODE_NONFINITE = 3     /* a weight came out NaN or infinite */
+};
+
+/* Limits of this build. */
+#define LABFM_MAX_ORDER 8 /* k <= 8, p <= 44 */
+#define LABFM_MAX_OPS 8   /* operators per build */
+#define LABFM_PMAX 44     /* p(8) = (8^2 + 3*8)/2, Sec. 2.1 */
+
+/* Create a context on CUDA device `device` that enqueues work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  Returns LABFM_ERR_CUDA if the device cannot be used. */
+labfm_status labfm_create(labfm_ctx **out, int device, void *stream);
+
+/* Release every context-owned buffer.  NULL is accepted. */
+void labfm_destroy(labfm_ctx *ctx);
+
+/* Message for the last failed call on this context ("" if none).  Valid until the next call. */
+const char *labfm_last_error(const labfm_ctx *ctx);
+
+/* Change the stream subsequent work is enqueued on. */
+labfm_status labfm_set_stream(labfm_ctx *ctx, void *stream);
+
+/*
+ * Stencils (Sec. 2): for every node i, all j != i with |r_j - r_i| < 2 h_i.
+ *   n        number of nodes, 1 <= n < 2^31
+ *   xy       device double[2n], interleaved (x_0, y_0, x_1, y_1, ...)
+ *   h        device double[n], h_i > 0 and finite
+ *   periodic 1: the box [lo, hi)^2 wraps and offsets use the minimum image;
+ *            0: no wrap.  Every node must lie in the closed box.
+ *   box_lo, box_hi  host double[2]
+ *   nnz_out  host, receives the total number of stencil entries
+ * The predicate is evaluated exactly as written, in IEEE double without fused
+ * multiply-add: dx = x_j - x_i (then +-L once if |dx| > L/2 in a periodic box),
+ * r2 = dx*dx + dy*dy, accept r2 < (2 h_i)*(2 h_i).  Output is CSR, context-owned:
+ * row_ptr int64[n+1], col int32[nnz], each row ascending in j.  Rebuilding
+ * stencils invalidates any weights.  Errors: LABFM_ERR_ARG for a bad size, box,
+ * h or a node outside the box; LABFM_ERR_CAPACITY if the cell grid would exceed
+ * 2^28 cells.
+ */
+labfm_status labfm_build_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const double *h,
+                                    int periodic, const double box_lo[2], const double box_hi[2],
+                                    int64_t *nnz_out);
+
+/* Context-owned device views of the stencils (valid until rebuilt or destroyed). */
+labfm_status labfm_get_neighbours(labfm_ctx *ctx, const int64_t **row_ptr, const int32_t **col,
+                                  int64_t *n, int64_t *nnz);
+
+/*
+ * Weights (Sec. 2.1-2.2): per node i, build M_i = sum_j X_ji (outer) W_ji
+ * (Eq. disc_form) from the Taylor monomials X (Sec. 2) and the ABFs
+ * W = D(W0)|r_ji (Sec. 2.2; elements >= 10 keep only the dW0/dr term, Appendix A),
+ * solve M_i Psi^d = C^d (Eq. lsys) by Gaussian elimination with partial pivoting,
+ * and set w_ji^d = W_ji . Psi^d (Eq. w_abf).  Offsets are taken in units of h_i
+ * and C^d is scaled by h_i^-|alpha| (an exact similarity transform of M_i).
+ *   order        device int8[n] per-node order k_i in 1..8, or NULL to use uniform_order
+ *   uniform_order  1..8 when order == NULL
+ *   rbf          LABFM_RBF_*
+ *   n_ops        number of operators, 1..LABFM_MAX_OPS
+ *   C            host double[n_ops * 44]: row d is C^d in the derivative ordering D of
+ *                Sec. 2 (d/dx, d/dy, d2/dx2, d2/dxdy, d2/dy2, d3/dx3, ...), physical units;
+ *                entries beyond p(k_i) are ignored for node i
+ *   precision    LABFM_PREC_*
+ *   weight_dtype LABFM_F64 or LABFM_F32: storage of the context-owned weights,
+ *                layout [nnz][n_ops] (entry e of the CSR, operator d at e*n_ops + d)
+ *   node_status  device int32[n] receiving LABFM_NODE_* per node, or NULL
+ *   n_bad_out    host, receives the number of flagged nodes (may be NULL)
+ * Flagged nodes get zero weights.  Returns LABFM_ERR_SINGULAR if any node was
+ * flagged (the weights of all other nodes are valid), LABFM_ERR_STATE if no
+ * stencils were built.
+ */
+labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf,
+                                 int n_ops, const double *C, int precision, int weight_dtype,
+                                 int32_t *node_status, int64_t *n_bad_out);
+
+/* Context-owned device view of the weights: *w points to [nnz][n_ops] of *dtype. */
+labfm_status labfm_get_weights(labfm_ctx *ctx, const void **w, int *dtype, int *n_ops);
+
+/*
+ * Apply the discrete operators (Eq. general_do): out_d[i] = sum_j (f_j - f_i) w_ji^d
+ * for every operator d selected by op_mask (bit d), written in increasing d.
+ *   f           device [n] of field_dtype (LABFM_F64 or LABFM_F32)
+ *   out         device [n_selected][n] of field_dtype, row-major by operator
+ * Accumulation is in double for LABFM_F64 fields and in float for LABFM_F32 fields.
+ * Asynchronous.  LABFM_ERR_STATE before labfm_build_weights.
+ */
+labfm_status labfm_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int field_dtype, void *out);
+
+/*
+ * Explicit time stepping with the classical four-stage Runge-Kutta scheme (Sec. 4.1) of
+ *   du/dt = F(u),  F(u)_i = sum_d beta_d L_i^d(u)
+ * for nsteps steps of size dt.  The operators are combined once into one weight per
+ * stencil entry, w_ji = sum_d beta_d w_ji^d (L^d is linear in w), cached while beta
+ * and the weights are unchanged.  Nodes with frozen[i] != 0 keep their value
+ * (Dirichlet nodes, Sec. 4.1).  The nsteps x 4 stage launches are recorded once into a
+ * CUDA graph and replayed.
+ *   beta    host double[n_ops]
+ *   u       device [n] of field_dtype, updated in place
+ *   frozen  device uint8[n] or NULL
+ * Asynchronous.  LABFM_ERR_STATE before labfm_build_weights.
+ */
+labfm_status labfm_step(labfm_ctx *ctx, const double *beta, void *u, int field_dtype, double dt,
+                        int64_t nsteps, const uint8_t *frozen);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LABFM_H */

@@ -409,6 +409,15 @@ static int build_one(int64_t i, const double *xy, const double *h, int periodic,
         }
     if (mhat_out)
         for (int t = 0; t < p * p; t++) mhat_out[t] = (double)M[t];
+    /* a non-finite entry of M (e.g. a neighbour on top of node i, where the ABFs are
+     * singular, Sec. 2.2) makes the node's weights meaningless */
+    for (int t = 0; t < p * p; t++)
+        if (!isfinite(M[t])) {
+            for (int64_t u = 0; u < ni * n_ops; u++) w[u] = 0;
+            if (piv_ratio) *piv_ratio = 0;
+            free(X); free(W);
+            return ST_NONFINITE;
+        }
     /* scaled targets Chat_alpha = C_alpha h^-|alpha| */
     for (int m = 0; m < p; m++) {
         int a, b;

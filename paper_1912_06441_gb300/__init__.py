@@ -1,0 +1,250 @@
+"""GB300-native Local Anisotropic Basis Function Method (LABFM) stencil library.
+
+A thin ctypes binding over ``liblabfm.so`` (C ABI in ``include/labfm.h``).  Every step of
+the method -- stencil search, ABF/monomial evaluation, moment-matrix assembly, elimination,
+weight formation, operator application and RK4 stepping -- runs in the library's CUDA
+kernels; this module only checks arguments, passes device pointers and the current torch
+stream, and wraps context-owned buffers as torch tensors.  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH, build_library
+
+__all__ = ["Labfm", "LabfmError", "load_library", "RBF", "PREC", "DTYPE", "NODE", "C_FUNCTIONS"]
+
+RBF = {"wendland_c2": 0, "quadratic": 1, "cone": 2, "wendland_c6": 3, "gaussian": 4}
+PREC = {"fp64": 0}
+DTYPE = {"f64": 0, "f32": 1}
+NODE = {"ok": 0, "singular": 1, "undersampled": 2, "nonfinite": 3}
+STATUS = {0: "LABFM_OK", 1: "LABFM_ERR_ARG", 2: "LABFM_ERR_CUDA", 3: "LABFM_ERR_NOMEM", 4: "LABFM_ERR_CAPACITY",
+          5: "LABFM_ERR_SINGULAR", 6: "LABFM_ERR_TIMEOUT", 7: "LABFM_ERR_STATE"}
+PMAX = 44
+MAX_OPS = 8
+
+# every symbol include/labfm.h declares
+C_FUNCTIONS = ["labfm_create", "labfm_destroy", "labfm_last_error", "labfm_set_stream", "labfm_build_neighbours",
+               "labfm_get_neighbours", "labfm_build_weights", "labfm_get_weights", "labfm_apply", "labfm_step"]
+
+_lib = None
+
+
+class LabfmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str | None = None, build_if_missing: bool = False):
+    """Load liblabfm.so (built by ``__graft_entry__.build()`` or ``paper_1912_06441_gb300.build``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        if not build_if_missing:
+            raise OSError(f"liblabfm not built ({p}); run `python -m paper_1912_06441_gb300.build`")
+        build_library()
+    lib = ct.CDLL(p)
+    P, I, I64, U32, D = ct.c_void_p, ct.c_int, ct.c_int64, ct.c_uint32, ct.c_double
+    lib.labfm_create.argtypes = [ct.POINTER(P), I, P]
+    lib.labfm_create.restype = I
+    lib.labfm_destroy.argtypes = [P]
+    lib.labfm_destroy.restype = None
+    lib.labfm_last_error.argtypes = [P]
+    lib.labfm_last_error.restype = ct.c_char_p
+    lib.labfm_set_stream.argtypes = [P, P]
+    lib.labfm_set_stream.restype = I
+    lib.labfm_build_neighbours.argtypes = [P, I64, P, P, I, P, P, ct.POINTER(I64)]
+    lib.labfm_build_neighbours.restype = I
+    lib.labfm_get_neighbours.argtypes = [P, ct.POINTER(P), ct.POINTER(P), ct.POINTER(I64), ct.POINTER(I64)]
+    lib.labfm_get_neighbours.restype = I
+    lib.labfm_build_weights.argtypes = [P, P, I, I, I, P, I, I, P, ct.POINTER(I64)]
+    lib.labfm_build_weights.restype = I
+    lib.labfm_get_weights.argtypes = [P, ct.POINTER(P), ct.POINTER(I), ct.POINTER(I)]
+    lib.labfm_get_weights.restype = I
+    lib.labfm_apply.argtypes = [P, U32, P, I, P]
+    lib.labfm_apply.restype = I
+    lib.labfm_step.argtypes = [P, P, P, I, D, I64, P]
+    lib.labfm_step.restype = I
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class _DevView:
+    """__cuda_array_interface__ wrapper so torch can view a context-owned device buffer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return DTYPE["f64"]
+    if t.dtype == torch.float32:
+        return DTYPE["f32"]
+    raise TypeError(f"field dtype must be float64 or float32, got {t.dtype}")
+
+
+class Labfm:
+    """One library context on one CUDA device.  Method names follow the C ABI."""
+
+    def __init__(self, device: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("labfm needs a CUDA device; no CPU fallback exists")
+        self.lib = load_library()
+        self.device = device
+        self._ctx = ct.c_void_p()
+        with torch.cuda.device(device):
+            stream = torch.cuda.current_stream(device).cuda_stream
+        st = self.lib.labfm_create(ct.byref(self._ctx), device, ct.c_void_p(stream))
+        if st != 0:
+            raise LabfmError(st, "labfm_create failed")
+        self._stream = stream
+        self.n = 0
+        self.nnz = 0
+        self.n_ops = 0
+
+    # -- helpers -------------------------------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            raise LabfmError(st, self.lib.labfm_last_error(self._ctx).decode())
+
+    def _sync_stream(self):
+        torch = _torch()
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            self._check(self.lib.labfm_set_stream(self._ctx, ct.c_void_p(s)))
+            self._stream = s
+
+    def _dev(self, t, dtype, name, numel=None):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.device.index != self.device:
+            raise ValueError(f"{name} must be a torch tensor on cuda:{self.device}")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+        return ct.c_void_p(t.data_ptr())
+
+    def close(self):
+        if self._ctx:
+            self.lib.labfm_destroy(self._ctx)
+            self._ctx = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI ---------------------------------------------------------------------------------
+    def build_neighbours(self, xy, h, periodic: bool, box_lo=(0.0, 0.0), box_hi=(1.0, 1.0)) -> int:
+        """Stencils |r_ji| < 2 h_i, j != i (Sec. 2).  xy: cuda float64 [n, 2]; h: cuda float64 [n]."""
+        torch = _torch()
+        n = int(h.numel())
+        pxy = self._dev(xy, torch.float64, "xy", 2 * n)
+        ph = self._dev(h, torch.float64, "h", n)
+        self._sync_stream()
+        lo = (ct.c_double * 2)(*box_lo)
+        hi = (ct.c_double * 2)(*box_hi)
+        nnz = ct.c_int64()
+        self._check(self.lib.labfm_build_neighbours(self._ctx, n, pxy, ph, int(bool(periodic)), lo, hi, ct.byref(nnz)))
+        self.n, self.nnz = n, int(nnz.value)
+        return self.nnz
+
+    def get_neighbours(self):
+        """(row_ptr int64 [n+1], col int32 [nnz]) as torch views of context-owned memory."""
+        torch = _torch()
+        rp, cl = ct.c_void_p(), ct.c_void_p()
+        n, nnz = ct.c_int64(), ct.c_int64()
+        self._check(self.lib.labfm_get_neighbours(self._ctx, ct.byref(rp), ct.byref(cl), ct.byref(n), ct.byref(nnz)))
+        dev = torch.device("cuda", self.device)
+        row_ptr = torch.as_tensor(_DevView(rp.value, (n.value + 1,), "<i8"), device=dev)
+        col = torch.as_tensor(_DevView(cl.value or 0, (nnz.value,), "<i4"), device=dev) if nnz.value else \
+            torch.zeros(0, dtype=torch.int32, device=dev)
+        return row_ptr, col
+
+    def build_weights(self, C, order=None, uniform_order: int = 4, rbf: str = "wendland_c2",
+                      precision: str = "fp64", weight_dtype: str = "f64", node_status=None) -> int:
+        """Weights w_ji^d for the target vectors C (rows, D ordering, Sec. 2); returns #flagged nodes.
+
+        Raises LabfmError(LABFM_ERR_SINGULAR) only if ``node_status`` is None and a node was
+        flagged; with a node_status tensor the flags are returned there and the count here."""
+        torch = _torch()
+        Cn = np.atleast_2d(np.asarray(C, dtype=np.float64))
+        n_ops = Cn.shape[0]
+        if n_ops < 1 or n_ops > MAX_OPS or Cn.shape[1] > PMAX:
+            raise ValueError("C must be [n_ops <= 8, p <= 44]")
+        Cp = np.zeros((n_ops, PMAX))
+        Cp[:, : Cn.shape[1]] = Cn
+        Cp = np.ascontiguousarray(Cp)
+        po = None if order is None else self._dev(order, torch.int8, "order", self.n)
+        ps = None if node_status is None else self._dev(node_status, torch.int32, "node_status", self.n)
+        self._sync_stream()
+        nbad = ct.c_int64()
+        st = self.lib.labfm_build_weights(self._ctx, po, int(uniform_order), RBF[rbf], n_ops,
+                                          Cp.ctypes.data_as(ct.c_void_p), PREC[precision], DTYPE[weight_dtype], ps,
+                                          ct.byref(nbad))
+        if st == 5 and node_status is not None:
+            st = 0
+        self._check(st)
+        self.n_ops = n_ops
+        return int(nbad.value)
+
+    def get_weights(self):
+        """Context-owned weights as a torch view [nnz, n_ops]."""
+        torch = _torch()
+        w, dt, no = ct.c_void_p(), ct.c_int(), ct.c_int()
+        self._check(self.lib.labfm_get_weights(self._ctx, ct.byref(w), ct.byref(dt), ct.byref(no)))
+        typestr = "<f8" if dt.value == 0 else "<f4"
+        if self.nnz == 0:
+            return torch.zeros((0, no.value), dtype=torch.float64 if dt.value == 0 else torch.float32,
+                               device=torch.device("cuda", self.device))
+        return torch.as_tensor(_DevView(w.value, (self.nnz, no.value), typestr), device=torch.device("cuda", self.device))
+
+    def apply(self, f, op_mask: int | None = None, out=None):
+        """out[s, i] = sum_j (f_j - f_i) w_ji^d for the selected operators (Eq. general_do)."""
+        torch = _torch()
+        fdt = _dtype_code(f)
+        pf = self._dev(f, f.dtype, "f", self.n)
+        mask = (1 << self.n_ops) - 1 if op_mask is None else int(op_mask)
+        nsel = bin(mask).count("1")
+        if out is None:
+            out = torch.empty((nsel, self.n), dtype=f.dtype, device=f.device)
+        po = self._dev(out, f.dtype, "out", nsel * self.n)
+        self._sync_stream()
+        self._check(self.lib.labfm_apply(self._ctx, mask, pf, fdt, po))
+        return out
+
+    def step(self, beta, u, dt: float, nsteps: int, frozen=None):
+        """nsteps of classical RK4 for du/dt = sum_d beta_d L^d(u) (Sec. 4.1); u is updated in place."""
+        torch = _torch()
+        b = np.zeros(MAX_OPS)
+        bb = np.asarray(beta, dtype=np.float64)
+        if bb.shape != (self.n_ops,):
+            raise ValueError(f"beta must have {self.n_ops} entries")
+        b[: self.n_ops] = bb
+        fdt = _dtype_code(u)
+        pu = self._dev(u, u.dtype, "u", self.n)
+        pz = None if frozen is None else self._dev(frozen, torch.uint8, "frozen", self.n)
+        self._sync_stream()
+        self._check(self.lib.labfm_step(self._ctx, b.ctypes.data_as(ct.c_void_p), pu, fdt, float(dt), int(nsteps), pz))
+        return u

@@ -1,0 +1,336 @@
+// Operator application (Eq. general_do) and the RK4 driver (Sec. 4.1).
+//
+// Both are streaming gather-sums over the CSR stencils: per stencil entry e of node i, read
+// col[e] and the weights w[e][*] once (HBM), gather f[col[e]] (stays in L2: the field is
+// small next to the weight stream and nodes are numbered in spatial order), and accumulate
+// (f_j - f_i) w.  A group of G lanes shares one node: the lanes read consecutive entries, so
+// every weight and index load of a warp is a contiguous, fully used segment; UNR entries per
+// lane are in flight before the first use.  The partial sums of a group are combined with
+// butterfly shuffles.
+#include <cmath>
+#include <type_traits>
+
+#include "labfm_internal.cuh"
+
+namespace labfm {
+namespace {
+
+constexpr int APPLY_THREADS = 256;
+constexpr int UNR = 4;
+
+template <class T> struct Acc { using type = double; };
+template <> struct Acc<float> { using type = float; };
+
+// Weights of entry e (NOPS of them) into wv[], converted to the accumulation type.
+template <int NOPS, class WT, class AT>
+__device__ __forceinline__ void load_w(const WT *__restrict__ w, int64_t e, AT *wv)
+{
+    const WT *p = w + e * NOPS;
+    if constexpr (NOPS == 4 && sizeof(WT) == 8) {
+        double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+        double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+        wv[0] = (AT)a.x; wv[1] = (AT)a.y; wv[2] = (AT)b.x; wv[3] = (AT)b.y;
+    } else if constexpr (NOPS == 4 && sizeof(WT) == 4) {
+        float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+        wv[0] = (AT)a.x; wv[1] = (AT)a.y; wv[2] = (AT)a.z; wv[3] = (AT)a.w;
+    } else if constexpr (NOPS == 2 && sizeof(WT) == 8) {
+        double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+        wv[0] = (AT)a.x; wv[1] = (AT)a.y;
+    } else {
+#pragma unroll
+        for (int d = 0; d < NOPS; d++) wv[d] = (AT)__ldcs(p + d);
+    }
+}
+
+// out[sel(d)][i] = sum_j (f_j - f_i) w_ji^d for the operators in mask.
+template <int NOPS, class FT, class WT>
+__global__ void __launch_bounds__(APPLY_THREADS) k_apply(int64_t n, const int64_t *__restrict__ row_ptr,
+                                                         const int32_t *__restrict__ col, const WT *__restrict__ w,
+                                                         const FT *__restrict__ f, FT *__restrict__ out, uint32_t mask,
+                                                         int G)
+{
+    using AT = typename std::conditional<std::is_same<FT, float>::value && std::is_same<WT, float>::value, float,
+                                         double>::type;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) / G;
+    const bool live = i < n;
+    int64_t rs = 0, re = 0;
+    AT fi = 0;
+    if (live) {
+        rs = row_ptr[i];
+        re = row_ptr[i + 1];
+        fi = (AT)__ldg(f + i);
+    }
+    AT acc[NOPS];
+#pragma unroll
+    for (int d = 0; d < NOPS; d++) acc[d] = 0;
+    for (int64_t base = rs; base < re; base += (int64_t)G * UNR) {
+        int cj[UNR];
+        AT wv[UNR][NOPS];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            int64_t e = base + (int64_t)u * G + lane;
+            if (e < re) {
+                cj[u] = __ldcs(col + e);
+                load_w<NOPS>(w, e, wv[u]);
+            } else {
+                cj[u] = -1;
+#pragma unroll
+                for (int d = 0; d < NOPS; d++) wv[u][d] = 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            if (cj[u] >= 0) {
+                AT df = (AT)__ldg(f + cj[u]) - fi;
+#pragma unroll
+                for (int d = 0; d < NOPS; d++) acc[d] = fma(df, wv[u][d], acc[d]);
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < NOPS; d++)
+        for (int o = G >> 1; o > 0; o >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
+    if (live) {
+#pragma unroll
+        for (int d = 0; d < NOPS; d++) {
+            if (lane == d && ((mask >> d) & 1u)) {
+                int row = __popc(mask & ((1u << d) - 1u));
+                out[(int64_t)row * n + i] = (FT)acc[d];
+            }
+        }
+    }
+}
+
+int lanes_for(int64_t n, int64_t nnz)
+{
+    double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+    int G = 4;
+    while (G < 32 && G * UNR < avg) G *= 2;
+    return G;
+}
+
+template <int NOPS, class FT, class WT>
+cudaError_t launch_apply_t(labfm_ctx *ctx, uint32_t mask, const void *f, void *out)
+{
+    int G = lanes_for(ctx->n, ctx->nnz);
+    if (G < NOPS) G = NOPS < 8 ? (NOPS <= 4 ? 4 : 8) : 8;  // lane d writes operator d
+    int64_t threads = ctx->n * G;
+    unsigned blocks = (unsigned)((threads + APPLY_THREADS - 1) / APPLY_THREADS);
+    k_apply<NOPS, FT, WT><<<blocks, APPLY_THREADS, 0, ctx->stream>>>(
+        ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(), (const WT *)ctx->w.ptr, (const FT *)f, (FT *)out,
+        mask, G);
+    return cudaGetLastError();
+}
+
+template <int NOPS>
+cudaError_t launch_apply_n(labfm_ctx *ctx, uint32_t mask, const void *f, int fdt, void *out)
+{
+    if (ctx->wdtype == LABFM_F64)
+        return fdt == LABFM_F64 ? launch_apply_t<NOPS, double, double>(ctx, mask, f, out)
+                                : launch_apply_t<NOPS, float, double>(ctx, mask, f, out);
+    return fdt == LABFM_F64 ? launch_apply_t<NOPS, double, float>(ctx, mask, f, out)
+                            : launch_apply_t<NOPS, float, float>(ctx, mask, f, out);
+}
+
+// ---------------------------------------------------------------------------------------------
+// RK4
+// ---------------------------------------------------------------------------------------------
+
+// wc[e] = sum_d beta_d w[e][d] (in double, stored in WT)
+template <class WT>
+__global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, WT *__restrict__ wc, double b0, double b1, double b2, double b3, double b4, double b5,
+                          double b6, double b7)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    const double b[8] = {b0, b1, b2, b3, b4, b5, b6, b7};
+    double s = 0.0;
+    for (int d = 0; d < n_ops; d++) s = fma(b[d], (double)w[e * n_ops + d], s);
+    wc[e] = (WT)s;
+}
+
+// One RK4 stage.  F_i = sum_j (src_j - src_i) wc_ji (0 on frozen nodes), then
+//   stage 0: acc = u + dt/6 F,  nxt = u + dt/2 F
+//   stage 1: acc += dt/3 F,     nxt = u + dt/2 F
+//   stage 2: acc += dt/3 F,     nxt = u + dt F
+//   stage 3: u = acc + dt/6 F
+template <class FT, class WT>
+__global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const int64_t *__restrict__ row_ptr,
+                                                             const int32_t *__restrict__ col, const WT *__restrict__ wc,
+                                                             const FT *__restrict__ src, FT *__restrict__ u,
+                                                             FT *__restrict__ acc_buf, FT *__restrict__ nxt,
+                                                             const uint8_t *__restrict__ frozen, int stage, double dt,
+                                                             int G)
+{
+    using AT = typename std::conditional<std::is_same<FT, float>::value && std::is_same<WT, float>::value, float,
+                                         double>::type;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) / G;
+    const bool live = i < n;
+    int64_t rs = 0, re = 0;
+    AT si = 0;
+    if (live) {
+        rs = row_ptr[i];
+        re = row_ptr[i + 1];
+        si = (AT)src[i];
+    }
+    AT acc = 0;
+    for (int64_t base = rs; base < re; base += (int64_t)G * UNR) {
+        int cj[UNR];
+        AT wv[UNR];
+#pragma unroll
+        for (int q = 0; q < UNR; q++) {
+            int64_t e = base + (int64_t)q * G + lane;
+            if (e < re) {
+                cj[q] = __ldcs(col + e);
+                wv[q] = (AT)__ldcs(wc + e);
+            } else {
+                cj[q] = -1;
+                wv[q] = 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < UNR; q++)
+            if (cj[q] >= 0) acc = fma((AT)src[cj[q]] - si, wv[q], acc);
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!live || lane != 0) return;
+    AT F = (frozen && frozen[i]) ? (AT)0 : acc;
+    AT h = (AT)dt;
+    AT ui = (AT)u[i];
+    switch (stage) {
+    case 0:
+        acc_buf[i] = (FT)(ui + h * (AT)(1.0 / 6.0) * F);
+        nxt[i] = (FT)(ui + h * (AT)0.5 * F);
+        break;
+    case 1:
+        acc_buf[i] = (FT)((AT)acc_buf[i] + h * (AT)(1.0 / 3.0) * F);
+        nxt[i] = (FT)(ui + h * (AT)0.5 * F);
+        break;
+    case 2:
+        acc_buf[i] = (FT)((AT)acc_buf[i] + h * (AT)(1.0 / 3.0) * F);
+        nxt[i] = (FT)(ui + h * F);
+        break;
+    default:
+        u[i] = (FT)((AT)acc_buf[i] + h * (AT)(1.0 / 6.0) * F);
+        break;
+    }
+}
+
+template <class FT, class WT>
+cudaError_t enqueue_steps(labfm_ctx *ctx, void *u, double dt, int64_t nsteps, const uint8_t *frozen, cudaStream_t s)
+{
+    int G = lanes_for(ctx->n, ctx->nnz);
+    int64_t threads = ctx->n * G;
+    unsigned blocks = (unsigned)((threads + APPLY_THREADS - 1) / APPLY_THREADS);
+    FT *uu = (FT *)u, *acc = ctx->rk_acc.as<FT>(), *sa = ctx->rk_stage_a.as<FT>(), *sb = ctx->rk_stage_b.as<FT>();
+    const WT *wc = (const WT *)ctx->wcomb.ptr;
+    const int64_t *rp = ctx->row_ptr.as<int64_t>();
+    const int32_t *cl = ctx->col.as<int32_t>();
+    for (int64_t st = 0; st < nsteps; st++) {
+        k_rk4_stage<FT, WT><<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, rp, cl, wc, uu, uu, acc, sa, frozen, 0, dt, G);
+        k_rk4_stage<FT, WT><<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, rp, cl, wc, sa, uu, acc, sb, frozen, 1, dt, G);
+        k_rk4_stage<FT, WT><<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, rp, cl, wc, sb, uu, acc, sa, frozen, 2, dt, G);
+        k_rk4_stage<FT, WT><<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, rp, cl, wc, sa, uu, acc, nullptr, frozen, 3, dt, G);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_steps_dt(labfm_ctx *ctx, int fdt, void *u, double dt, int64_t nsteps, const uint8_t *frozen,
+                             cudaStream_t s)
+{
+    if (ctx->wdtype == LABFM_F64)
+        return fdt == LABFM_F64 ? enqueue_steps<double, double>(ctx, u, dt, nsteps, frozen, s)
+                                : enqueue_steps<float, double>(ctx, u, dt, nsteps, frozen, s);
+    return fdt == LABFM_F64 ? enqueue_steps<double, float>(ctx, u, dt, nsteps, frozen, s)
+                            : enqueue_steps<float, float>(ctx, u, dt, nsteps, frozen, s);
+}
+
+}  // namespace
+
+cudaError_t launch_apply(labfm_ctx *ctx, uint32_t mask, const void *f, int fdt, void *out)
+{
+    switch (ctx->n_ops) {
+    case 1: return launch_apply_n<1>(ctx, mask, f, fdt, out);
+    case 2: return launch_apply_n<2>(ctx, mask, f, fdt, out);
+    case 3: return launch_apply_n<3>(ctx, mask, f, fdt, out);
+    case 4: return launch_apply_n<4>(ctx, mask, f, fdt, out);
+    case 5: return launch_apply_n<5>(ctx, mask, f, fdt, out);
+    case 6: return launch_apply_n<6>(ctx, mask, f, fdt, out);
+    case 7: return launch_apply_n<7>(ctx, mask, f, fdt, out);
+    default: return launch_apply_n<8>(ctx, mask, f, fdt, out);
+    }
+}
+
+labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int fdt, double dt, int64_t nsteps,
+                      const uint8_t *frozen)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ctx->n, nnz = ctx->nnz;
+    size_t wsz = ctx->wdtype == LABFM_F64 ? 8 : 4;
+    size_t fsz = fdt == LABFM_F64 ? 8 : 4;
+    // combined weight, cached while beta and the weights are unchanged
+    bool same_beta = ctx->wcomb_valid;
+    for (int d = 0; d < ctx->n_ops && same_beta; d++) same_beta = (ctx->beta_cached[d] == beta[d]);
+    if (!same_beta) {
+        void *old = ctx->wcomb.ptr;
+        LABFM_CUDA_TRY(ctx, ctx->wcomb.reserve(wsz * (nnz > 0 ? nnz : 1)));
+        if (old != ctx->wcomb.ptr) ctx->graph.release();
+        double b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int d = 0; d < ctx->n_ops; d++) b[d] = beta[d];
+        unsigned blocks = (unsigned)((nnz + 255) / 256);
+        if (nnz > 0) {
+            if (ctx->wdtype == LABFM_F64)
+                k_combine<double><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<double>(),
+                                                         ctx->wcomb.as<double>(), b[0], b[1], b[2], b[3], b[4], b[5],
+                                                         b[6], b[7]);
+            else
+                k_combine<float><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<float>(),
+                                                        ctx->wcomb.as<float>(), b[0], b[1], b[2], b[3], b[4], b[5],
+                                                        b[6], b[7]);
+            LABFM_CUDA_TRY(ctx, cudaGetLastError());
+        }
+        for (int d = 0; d < ctx->n_ops; d++) ctx->beta_cached[d] = beta[d];
+        ctx->wcomb_valid = true;
+    }
+    void *old_a = ctx->rk_acc.ptr, *old_b = ctx->rk_stage_a.ptr, *old_c = ctx->rk_stage_b.ptr;
+    LABFM_CUDA_TRY(ctx, ctx->rk_acc.reserve(fsz * n));
+    LABFM_CUDA_TRY(ctx, ctx->rk_stage_a.reserve(fsz * n));
+    LABFM_CUDA_TRY(ctx, ctx->rk_stage_b.reserve(fsz * n));
+    if (old_a != ctx->rk_acc.ptr || old_b != ctx->rk_stage_a.ptr || old_c != ctx->rk_stage_b.ptr) ctx->graph.release();
+
+    StepGraph &g = ctx->graph;
+    if (!(g.exec && g.u == u && g.frozen == frozen && g.dtype == fdt && g.dt == dt && g.nsteps == nsteps)) {
+        g.release();
+        if (!ctx->capture_stream) {
+            LABFM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        }
+        cudaGraph_t graph = nullptr;
+        LABFM_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_steps_dt(ctx, fdt, u, dt, nsteps, frozen, ctx->capture_stream);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(ctx, e, "RK4 stage capture");
+        }
+        LABFM_CUDA_TRY(ctx, e2);
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
+        g.u = u;
+        g.frozen = frozen;
+        g.dtype = fdt;
+        g.dt = dt;
+        g.nsteps = nsteps;
+    }
+    LABFM_CUDA_TRY(ctx, cudaGraphLaunch(g.exec, s));
+    return LABFM_OK;
+}
+
+}  // namespace labfm

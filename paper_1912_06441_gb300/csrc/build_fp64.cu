@@ -1,0 +1,460 @@
+// FP64 weight build (Sec. 2.1-2.2): per node, monomials X and ABFs W of every neighbour,
+// M = sum_j X_j (outer) W_j (Eq. disc_form), Gaussian elimination with partial pivoting of
+// M Psi = C^d for all operators at once (Eq. lsys), and w_j^d = W_j . Psi^d (Eq. w_abf).
+//
+// One CTA per node (persistent over a node list).  Neighbour data are staged in shared
+// memory in chunks of NB neighbours: Xs[j][m], Ws[j][n] (row stride LDX, a multiple of 4 so
+// that a thread's 4 consecutive W values are one 32-byte load).  The p x p assembly is tiled
+// 2 x 4 per thread in registers across chunks.  The augmented matrix [M | Chat] (Chat_alpha =
+// C_alpha h^-|alpha|) is eliminated in shared memory, one column per step.
+#include <cmath>
+#include <vector>
+
+#include "abf.cuh"
+
+namespace labfm {
+namespace {
+
+__constant__ RPolyTable c_rpoly = make_rpoly_table();
+__constant__ double c_invfact[KMAX + 1] = {1.0,       1.0,        0.5,         1.0 / 6.0,   1.0 / 24.0,
+                                           1.0 / 120, 1.0 / 720., 1.0 / 5040., 1.0 / 40320.};
+
+constexpr int BUILD_THREADS = 256;
+
+template <int K> struct Cfg {
+    static constexpr int P = p_of_k(K);
+    static constexpr int LDX = (P + 3) / 4 * 4;
+    static constexpr int NB = K >= 7 ? 72 : 64;
+    static constexpr int TM = 2, TN = 4;
+    static constexpr int RG = (P + TM - 1) / TM, CG = (P + TN - 1) / TN;
+    static_assert(RG * CG <= BUILD_THREADS, "assembly tile grid exceeds the CTA");
+    static constexpr int LDA = P + MAX_OPS + 1;  // augmented row stride (odd: fewer bank conflicts)
+    static constexpr size_t smem_bytes = sizeof(double) * ((size_t)2 * NB * LDX + (size_t)P * LDA);
+};
+
+struct BuildArgs {
+    int64_t n_list;           // nodes in this launch
+    const int32_t *list;      // node ids, or null: node = list index
+    const double *xy;         // [2n]
+    const double *h;          // [n]
+    const int64_t *row_ptr;
+    const int32_t *col;
+    int periodic;
+    double L[2], halfL[2];
+    int rbf;
+    int n_ops;
+    void *w;  // [nnz][n_ops]
+    int wdtype;
+    int32_t *node_status;     // may be null
+    unsigned long long *n_bad;
+    double C[MAX_OPS * PMAX];  // target vectors, row d = C^d (physical units)
+};
+
+// Monomials and ABFs of one scaled offset, written to X[0..P), W[0..P).
+template <int K>
+__device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__restrict__ X, double *__restrict__ W)
+{
+    constexpr int P = p_of_k(K);
+    double r = sqrt(x * x + y * y);
+    double ir = 1.0 / r;
+    double u = x * ir, v = y * ir;
+    double d1, d2, d3;
+    rbf_derivs(rbf, r, d1, d2, d3);
+    double xp[K + 1], yp[K + 1], up[K + 1], vp[K + 1], irp[K];
+    xp[0] = yp[0] = up[0] = vp[0] = irp[0] = 1.0;
+#pragma unroll
+    for (int t = 1; t <= K; t++) {
+        xp[t] = xp[t - 1] * x;
+        yp[t] = yp[t - 1] * y;
+        up[t] = up[t - 1] * u;
+        vp[t] = vp[t - 1] * v;
+    }
+#pragma unroll
+    for (int t = 1; t < K; t++) irp[t] = irp[t - 1] * ir;
+    double dr[P];  // d^alpha |r|
+#pragma unroll
+    for (int e = 0; e < P; e++) {
+        const int n = elem_degree(e), a = elem_a(e), b = n - a;
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t <= n; t++) s = fma(c_rpoly.c[e][t], up[t] * vp[n - t], s);
+        dr[e] = s * irp[n - 1];
+        X[e] = xp[a] * yp[b] * (c_invfact[a] * c_invfact[b]);
+    }
+    // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
+#pragma unroll
+    for (int e = 0; e < P; e++) W[e] = d1 * dr[e];
+    if constexpr (K >= 2) {
+        const double rxx = dr[2], rxy = dr[3], ryy = dr[4];
+        W[2] = fma(d2, u * u, W[2]);
+        W[3] = fma(d2, u * v, W[3]);
+        W[4] = fma(d2, v * v, W[4]);
+        if constexpr (K >= 3) {
+            W[5] = fma(d3, u * u * u, fma(d2, 3.0 * u * rxx, W[5]));
+            W[6] = fma(d3, u * u * v, fma(d2, v * rxx + 2.0 * u * rxy, W[6]));
+            W[7] = fma(d3, u * v * v, fma(d2, u * ryy + 2.0 * v * rxy, W[7]));
+            W[8] = fma(d3, v * v * v, fma(d2, 3.0 * v * ryy, W[8]));
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(BUILD_THREADS) k_build_fp64(BuildArgs A)
+{
+    using C = Cfg<K>;
+    constexpr int P = C::P, LDX = C::LDX, NB = C::NB, LDA = C::LDA, TM = C::TM, TN = C::TN;
+    extern __shared__ __align__(16) double smem[];
+    double *Xs = smem;                 // [NB][LDX]
+    double *Ws = Xs + NB * LDX;        // [NB][LDX]
+    double *Am = Ws + NB * LDX;        // [P][LDA]  augmented [M | Chat]
+    __shared__ int s_piv;
+    __shared__ double s_inv;
+    __shared__ int s_flag;  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
+
+    const int tid = threadIdx.x;
+    const int n_ops = A.n_ops;
+    const int W_ = P + n_ops;  // used columns of the augmented matrix
+    const int rg = tid / C::CG, cg = tid % C::CG;
+    const bool tile_active = tid < C::RG * C::CG;
+
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
+        const int64_t i = A.list ? (int64_t)A.list[li] : li;
+        const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
+        const int ni = (int)(re - rs);
+        if (ni < P) {
+            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += BUILD_THREADS) {
+                if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
+                else ((float *)A.w)[rs * n_ops + t] = 0.0f;
+            }
+            if (tid == 0) {
+                if (A.node_status) A.node_status[i] = LABFM_NODE_UNDERSAMPLED;
+                atomicAdd(A.n_bad, 1ull);
+            }
+            continue;
+        }
+        const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], hi = A.h[i];
+        const double ihi = 1.0 / hi;
+
+        double acc[TM][TN];
+#pragma unroll
+        for (int a = 0; a < TM; a++)
+#pragma unroll
+            for (int b = 0; b < TN; b++) acc[a][b] = 0.0;
+
+        const int nchunks = (ni + NB - 1) / NB;
+        for (int ch = 0; ch < nchunks; ch++) {
+            const int j0 = ch * NB;
+            const int nj = min(NB, ni - j0);
+            for (int t = tid; t < nj; t += BUILD_THREADS) {
+                int j = A.col[rs + j0 + t];
+                double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
+                if (A.periodic) {
+                    if (dx > A.halfL[0]) dx -= A.L[0];
+                    else if (dx < -A.halfL[0]) dx += A.L[0];
+                    if (dy > A.halfL[1]) dy -= A.L[1];
+                    else if (dy < -A.halfL[1]) dy += A.L[1];
+                }
+                double *X = Xs + t * LDX, *W = Ws + t * LDX;
+                eval_xw<K>(dx * ihi, dy * ihi, A.rbf, X, W);
+#pragma unroll
+                for (int e = P; e < LDX; e++) X[e] = W[e] = 0.0;
+            }
+            __syncthreads();
+            if (tile_active) {
+                for (int j = 0; j < nj; j++) {
+                    const double *X = Xs + j * LDX + rg * TM;
+                    const double *W = Ws + j * LDX + cg * TN;
+                    double xv[TM], wv[TN];
+#pragma unroll
+                    for (int a = 0; a < TM; a++) xv[a] = X[a];
+                    double2 w01 = *reinterpret_cast<const double2 *>(W);
+                    double2 w23 = *reinterpret_cast<const double2 *>(W + 2);
+                    wv[0] = w01.x;
+                    wv[1] = w01.y;
+                    wv[2] = w23.x;
+                    wv[3] = w23.y;
+#pragma unroll
+                    for (int a = 0; a < TM; a++)
+#pragma unroll
+                        for (int b = 0; b < TN; b++) acc[a][b] = fma(xv[a], wv[b], acc[a][b]);
+                }
+            }
+            if (ch + 1 < nchunks) __syncthreads();
+        }
+        // M into the augmented matrix, scaled targets into its right-hand columns
+        if (tid == 0) s_flag = 0;
+        __syncthreads();
+        if (tile_active) {
+            bool finite = true;
+#pragma unroll
+            for (int a = 0; a < TM; a++)
+#pragma unroll
+                for (int b = 0; b < TN; b++) {
+                    int m = rg * TM + a, c = cg * TN + b;
+                    if (m < P && c < P) {
+                        Am[m * LDA + c] = acc[a][b];
+                        finite &= isfinite(acc[a][b]);
+                    }
+                }
+            // a non-finite entry of M (a neighbour on top of node i: singular ABFs)
+            if (!finite) atomicOr(&s_flag, 4);
+        }
+        for (int t = tid; t < P * n_ops; t += BUILD_THREADS) {
+            int m = t / n_ops, d = t % n_ops;
+            int deg = elem_degree(m);
+            double s = 1.0;
+            for (int q = 0; q < deg; q++) s *= ihi;
+            Am[m * LDA + P + d] = A.C[d * PMAX + m] * s;
+        }
+        __syncthreads();
+        const bool bad_m = (s_flag & 4) != 0;
+
+        // Gaussian elimination with partial pivoting (first largest |pivot| wins)
+        for (int c = 0; c < P && !bad_m; c++) {
+            if (tid < 32) {
+                double best = -1.0;
+                int br = c;
+                for (int r = c + tid; r < P; r += 32) {
+                    double v = fabs(Am[r * LDA + c]);
+                    if (v > best) {
+                        best = v;
+                        br = r;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    int orr = __shfl_xor_sync(0xffffffffu, br, o);
+                    if (ob > best || (ob == best && orr < br)) {
+                        best = ob;
+                        br = orr;
+                    }
+                }
+                if (tid == 0) {
+                    s_piv = br;
+                    double pv = Am[br * LDA + c];
+                    if (!(best > 0.0) || !isfinite(best)) {
+                        s_flag |= 1;
+                        s_inv = 0.0;
+                    } else {
+                        s_inv = 1.0 / pv;
+                    }
+                }
+            }
+            __syncthreads();
+            const int pr = s_piv;
+            if (pr != c) {
+                for (int t = c + tid; t < W_; t += BUILD_THREADS) {
+                    double a = Am[c * LDA + t];
+                    Am[c * LDA + t] = Am[pr * LDA + t];
+                    Am[pr * LDA + t] = a;
+                }
+                __syncthreads();
+            }
+            const double inv = s_inv;
+            for (int r = c + 1 + tid; r < P; r += BUILD_THREADS) Am[r * LDA + c] *= inv;
+            __syncthreads();
+            const int nr = P - c - 1, nc = W_ - c - 1;
+            for (int t = tid; t < nr * nc; t += BUILD_THREADS) {
+                int r = c + 1 + t / nc, q = c + 1 + t % nc;
+                Am[r * LDA + q] = fma(-Am[r * LDA + c], Am[c * LDA + q], Am[r * LDA + q]);
+            }
+            __syncthreads();
+        }
+        // back substitution on the n_ops right-hand sides
+        for (int c = P - 1; c >= 0 && !bad_m; c--) {
+            if (tid < n_ops) Am[c * LDA + P + tid] = Am[c * LDA + P + tid] / Am[c * LDA + c];
+            __syncthreads();
+            for (int t = tid; t < c * n_ops; t += BUILD_THREADS) {
+                int r = t / n_ops, d = t % n_ops;
+                Am[r * LDA + P + d] = fma(-Am[r * LDA + c], Am[c * LDA + P + d], Am[r * LDA + P + d]);
+            }
+            __syncthreads();
+        }
+        const bool singular = (s_flag & 5) != 0;  // no weights from a failed elimination
+
+        // weights w_j^d = W_j . Psi^d
+        for (int ch = 0; ch < nchunks; ch++) {
+            const int j0 = ch * NB;
+            const int nj = min(NB, ni - j0);
+            if (nchunks > 1) {  // the staged W of earlier chunks were overwritten: recompute
+                __syncthreads();
+                for (int t = tid; t < nj; t += BUILD_THREADS) {
+                    int j = A.col[rs + j0 + t];
+                    double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
+                    if (A.periodic) {
+                        if (dx > A.halfL[0]) dx -= A.L[0];
+                        else if (dx < -A.halfL[0]) dx += A.L[0];
+                        if (dy > A.halfL[1]) dy -= A.L[1];
+                        else if (dy < -A.halfL[1]) dy += A.L[1];
+                    }
+                    eval_xw<K>(dx * ihi, dy * ihi, A.rbf, Xs + t * LDX, Ws + t * LDX);
+                }
+                __syncthreads();
+            }
+            for (int t = tid; t < nj * n_ops; t += BUILD_THREADS) {
+                int j = t / n_ops, d = t % n_ops;
+                double s = 0.0;
+                if (!singular) {
+                    const double *W = Ws + j * LDX;
+#pragma unroll 4
+                    for (int m = 0; m < P; m++) s = fma(W[m], Am[m * LDA + P + d], s);
+                    if (!isfinite(s)) {
+                        atomicOr(&s_flag, 2);
+                        s = 0.0;
+                    }
+                }
+                int64_t idx = (rs + j0 + j) * n_ops + d;
+                if (A.wdtype == LABFM_F64) ((double *)A.w)[idx] = s;
+                else ((float *)A.w)[idx] = (float)s;
+            }
+        }
+        __syncthreads();
+        const int flag = s_flag;
+        if (flag & 2) {  // a weight was not finite: the whole node is zeroed
+            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += BUILD_THREADS) {
+                if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
+                else ((float *)A.w)[rs * n_ops + t] = 0.0f;
+            }
+        }
+        if (tid == 0) {
+            int st = (flag & 4)   ? LABFM_NODE_NONFINITE
+                     : (flag & 1) ? LABFM_NODE_SINGULAR
+                     : (flag & 2) ? LABFM_NODE_NONFINITE
+                                  : LABFM_NODE_OK;
+            if (A.node_status) A.node_status[i] = st;
+            if (st != LABFM_NODE_OK) atomicAdd(A.n_bad, 1ull);
+        }
+        __syncthreads();  // shared state is reused by the next node
+    }
+}
+
+template <int K>
+static cudaError_t launch_k(const BuildArgs &a, int num_sms, cudaStream_t s)
+{
+    using C = Cfg<K>;
+    cudaError_t e = cudaFuncSetAttribute(k_build_fp64<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_fp64<K>, BUILD_THREADS, C::smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = std::min<int64_t>(a.n_list, (int64_t)num_sms * per_sm);
+    if (grid < 1) return cudaSuccess;
+    k_build_fp64<K><<<(unsigned)grid, BUILD_THREADS, C::smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_order(int k, const BuildArgs &a, int num_sms, cudaStream_t s)
+{
+    switch (k) {
+    case 1: return launch_k<1>(a, num_sms, s);
+    case 2: return launch_k<2>(a, num_sms, s);
+    case 3: return launch_k<3>(a, num_sms, s);
+    case 4: return launch_k<4>(a, num_sms, s);
+    case 5: return launch_k<5>(a, num_sms, s);
+    case 6: return launch_k<6>(a, num_sms, s);
+    case 7: return launch_k<7>(a, num_sms, s);
+    default: return launch_k<8>(a, num_sms, s);
+    }
+}
+
+// Bucket nodes by order: counts per order, then a stable list of node ids per order.
+__global__ void k_order_count(int64_t n, const int8_t *__restrict__ order, unsigned long long *__restrict__ cnt,
+                              unsigned long long *__restrict__ bad)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = order[i];
+    if (k < 1 || k > KMAX) {
+        atomicAdd(bad, 1ull);
+        return;
+    }
+    atomicAdd(&cnt[k], 1ull);
+}
+
+__global__ void k_order_scatter(int64_t n, const int8_t *__restrict__ order, const unsigned long long *__restrict__ base,
+                                unsigned long long *__restrict__ cursor, int32_t *__restrict__ list)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = order[i];
+    if (k < 1 || k > KMAX) return;
+    unsigned long long pos = base[k] + atomicAdd(&cursor[k], 1ull);
+    list[pos] = (int32_t)i;
+}
+
+}  // namespace
+
+labfm_status run_build_fp64(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops,
+                            const double *Cin, int weight_dtype, int32_t *node_status, int64_t *n_bad_out)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ctx->n;
+    size_t wbytes = (size_t)ctx->nnz * n_ops * (weight_dtype == LABFM_F64 ? 8 : 4);
+    LABFM_CUDA_TRY(ctx, ctx->w.reserve(wbytes > 0 ? wbytes : 8));
+    LABFM_CUDA_TRY(ctx, ctx->misc.reserve(4096));
+    unsigned long long *dmisc = ctx->misc.as<unsigned long long>();
+    // misc layout: [0] bad nodes, [1] bad orders, [2..10] order counts, [11..19] bases, [20..28] cursors
+    LABFM_CUDA_TRY(ctx, cudaMemsetAsync(dmisc, 0, 32 * sizeof(unsigned long long), s));
+
+    BuildArgs a{};
+    a.xy = ctx->node_xy.as<double>();
+    a.h = ctx->node_h.as<double>();
+    a.row_ptr = ctx->row_ptr.as<int64_t>();
+    a.col = ctx->col.as<int32_t>();
+    a.periodic = ctx->periodic;
+    for (int d = 0; d < 2; d++) {
+        a.L[d] = ctx->hi[d] - ctx->lo[d];
+        a.halfL[d] = 0.5 * a.L[d];
+    }
+    a.rbf = rbf;
+    a.n_ops = n_ops;
+    a.w = ctx->w.ptr;
+    a.wdtype = weight_dtype;
+    a.node_status = node_status;
+    a.n_bad = dmisc;
+    for (int t = 0; t < n_ops * PMAX; t++) a.C[t] = Cin[t];
+
+    unsigned long long *hs = (unsigned long long *)ctx->host_small;
+    if (!order) {
+        a.list = nullptr;
+        a.n_list = n;
+        LABFM_CUDA_TRY(ctx, launch_order(uniform_order, a, ctx->num_sms, s));
+    } else {
+        int nb = (int)((n + 255) / 256);
+        k_order_count<<<nb, 256, 0, s>>>(n, order, dmisc + 2, dmisc + 1);
+        LABFM_CUDA_TRY(ctx, cudaGetLastError());
+        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        if (hs[1] != 0) return fail(ctx, LABFM_ERR_ARG, "order[] has entries outside 1..8");
+        unsigned long long cnt[KMAX + 1], base[KMAX + 1];
+        unsigned long long acc = 0;
+        for (int k = 0; k <= KMAX; k++) {
+            cnt[k] = hs[2 + k];
+            base[k] = acc;
+            acc += cnt[k];
+        }
+        LABFM_CUDA_TRY(ctx, ctx->status_tmp.reserve(sizeof(int32_t) * (n > 0 ? n : 1)));
+        int32_t *list = ctx->status_tmp.as<int32_t>();
+        for (int k = 0; k <= KMAX; k++) hs[k] = base[k];
+        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(dmisc + 11, hs, sizeof(base), cudaMemcpyHostToDevice, s));
+        k_order_scatter<<<nb, 256, 0, s>>>(n, order, dmisc + 11, dmisc + 20, list);
+        LABFM_CUDA_TRY(ctx, cudaGetLastError());
+        for (int k = KMAX; k >= 1; k--) {
+            if (!cnt[k]) continue;
+            a.list = list + base[k];
+            a.n_list = (int64_t)cnt[k];
+            LABFM_CUDA_TRY(ctx, launch_order(k, a, ctx->num_sms, s));
+        }
+    }
+    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    int64_t nbad = (int64_t)hs[0];
+    if (n_bad_out) *n_bad_out = nbad;
+    if (nbad) return fail(ctx, LABFM_ERR_SINGULAR, std::to_string(nbad) + " node(s) flagged");
+    return LABFM_OK;
+}
+
+}  // namespace labfm

@@ -1,0 +1,100 @@
+// Internal declarations shared by the translation units of liblabfm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "labfm.h"
+
+namespace labfm {
+
+constexpr int KMAX = LABFM_MAX_ORDER;
+constexpr int PMAX = LABFM_PMAX;
+constexpr int MAX_OPS = LABFM_MAX_OPS;
+
+__host__ __device__ constexpr int p_of_k(int k) { return (k * k + 3 * k) / 2; }
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t need);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Cached CUDA graph of an RK4 run.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void *u = nullptr;
+    const void *frozen = nullptr;
+    int dtype = -1;
+    double dt = 0;
+    int64_t nsteps = 0;
+    void release();
+};
+
+}  // namespace labfm
+
+struct labfm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+
+    // stencils
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int periodic = 0;
+    double lo[2] = {0, 0}, hi[2] = {0, 0};
+    labfm::DevBuf node_xy, node_h;  // context copies of the node positions and h
+    labfm::DevBuf row_ptr, col;
+    // scratch of the neighbour search
+    labfm::DevBuf cell_of, cell_count, cell_start, cell_nodes, counts, scan_tmp, misc;
+
+    // weights
+    bool have_weights = false;
+    int n_ops = 0;
+    int wdtype = LABFM_F64;
+    labfm::DevBuf w;
+    labfm::DevBuf status_tmp;
+
+    // RK4
+    labfm::DevBuf wcomb, rk_acc, rk_stage_a, rk_stage_b;
+    double beta_cached[LABFM_MAX_OPS] = {0};
+    int wcomb_dtype = -1;
+    bool wcomb_valid = false;
+    labfm::StepGraph graph;
+    cudaStream_t capture_stream = nullptr;  // private stream used only to record the RK4 graph
+
+    // pinned host word for status read-back
+    void *host_small = nullptr;
+};
+
+namespace labfm {
+
+labfm_status fail(labfm_ctx *ctx, labfm_status st, const std::string &msg);
+labfm_status cuda_fail(labfm_ctx *ctx, cudaError_t e, const char *where);
+
+// Exclusive prefix sum of in[0..n) (int64) into out[0..n]; out[n] = total.  `tmp` is scratch.
+cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf &tmp, cudaStream_t s);
+cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, DevBuf &tmp, cudaStream_t s);
+
+// Kernel launchers (each returns the launch error).
+labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const double *h, int periodic,
+                            const double lo[2], const double hi[2], int64_t *nnz_out);
+labfm_status run_build_fp64(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops,
+                            const double *C, int weight_dtype, int32_t *node_status, int64_t *n_bad_out);
+cudaError_t launch_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int field_dtype, void *out);
+labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int field_dtype, double dt, int64_t nsteps,
+                      const uint8_t *frozen);
+
+}  // namespace labfm
+
+#define LABFM_CUDA_TRY(ctx, expr)                                   \
+    do {                                                            \
+        cudaError_t e_ = (expr);                                    \
+        if (e_ != cudaSuccess) return labfm::cuda_fail(ctx, e_, #expr); \
+    } while (0)

@@ -1,0 +1,272 @@
+// Stencil search (Sec. 2: all j != i with |r_ji| < 2 h_i) on a uniform cell grid.
+//
+// Cells have side >= 2 h_max, so every neighbour of a node lies in its own cell or one of
+// the 8 cells around it (with wrap-around in a periodic box).  Nodes are counting-sorted by
+// cell; one thread per node (in cell order, so a warp sweeps the same few cells) counts its
+// neighbours, a prefix sum gives the CSR row pointers, a second sweep writes the column
+// indices, and each row is sorted ascending.  The distance test is evaluated in IEEE double
+// with explicitly rounded operations (no fused multiply-add), so the result does not depend
+// on the compiler's contraction choices.
+#include <cmath>
+#include <cstring>
+
+#include "labfm_internal.cuh"
+
+namespace labfm {
+namespace {
+
+constexpr int NB_THREADS = 256;
+
+struct Grid {
+    double lo[2], L[2], halfL[2], inv_cs[2];
+    int nc[2];
+    int periodic;
+};
+
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+
+// Validate nodes and find max h.  misc[0] = bits of max h, misc[1] = number of bad nodes.
+__global__ void k_check(int64_t n, const double *__restrict__ xy, const double *__restrict__ h, double lo0, double lo1,
+                        double hi0, double hi1, unsigned long long *__restrict__ misc)
+{
+    __shared__ unsigned long long s_max[NB_THREADS / 32];
+    __shared__ unsigned int s_bad[NB_THREADS / 32];
+    unsigned long long mx = 0;
+    unsigned int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double x = xy[2 * i], y = xy[2 * i + 1], hv = h[i];
+        bool ok = isfinite(x) && isfinite(y) && isfinite(hv) && hv > 0.0 && x >= lo0 && x <= hi0 && y >= lo1 &&
+                  y <= hi1;
+        if (!ok) bad++;
+        else mx = max(mx, dbits(hv));  // positive doubles order like their bit patterns
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_max[w] = mx;
+        s_bad[w] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 1; t < NB_THREADS / 32; t++) {
+            mx = max(mx, s_max[t]);
+            bad += s_bad[t];
+        }
+        atomicMax(&misc[0], mx);
+        if (bad) atomicAdd(&misc[1], (unsigned long long)bad);
+    }
+}
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double inv_cs, int nc)
+{
+    double t = __dmul_rn(__dsub_rn(x, lo), inv_cs);
+    int c = (int)floor(t);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void k_cell_assign(int64_t n, const double *__restrict__ xy, Grid g, int32_t *__restrict__ cell_of,
+                              int32_t *__restrict__ cell_count)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cx = cell_coord(xy[2 * i], g.lo[0], g.inv_cs[0], g.nc[0]);
+    int cy = cell_coord(xy[2 * i + 1], g.lo[1], g.inv_cs[1], g.nc[1]);
+    int c = cy * g.nc[0] + cx;
+    cell_of[i] = c;
+    atomicAdd(&cell_count[c], 1);
+}
+
+__global__ void k_cell_scatter(int64_t n, const double *__restrict__ xy, const int32_t *__restrict__ cell_of,
+                               const int64_t *__restrict__ cell_start, int32_t *__restrict__ cursor,
+                               int32_t *__restrict__ cell_nodes, double2 *__restrict__ cell_xy)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cell_of[i];
+    int64_t pos = cell_start[c] + atomicAdd(&cursor[c], 1);
+    cell_nodes[pos] = (int32_t)i;
+    cell_xy[pos] = make_double2(xy[2 * i], xy[2 * i + 1]);
+}
+
+// The up-to-3 distinct cell coordinates around c along one axis.
+__device__ __forceinline__ int axis_cells(int c, int nc, int periodic, int out[3])
+{
+    int m = 0;
+    for (int d = -1; d <= 1; d++) {
+        int v = c + d;
+        if (periodic) {
+            v = v < 0 ? v + nc : (v >= nc ? v - nc : v);
+        } else if (v < 0 || v >= nc) {
+            continue;
+        }
+        bool dup = false;
+        for (int t = 0; t < m; t++) dup |= (out[t] == v);
+        if (!dup) out[m++] = v;
+    }
+    return m;
+}
+
+// One sweep over the candidate cells of node i.  WRITE = false: count; true: write col[].
+template <bool WRITE>
+__global__ void k_sweep(int64_t n, const double *__restrict__ xy, const double *__restrict__ h, Grid g,
+                        const int32_t *__restrict__ cell_of, const int64_t *__restrict__ cell_start,
+                        const int32_t *__restrict__ cell_nodes, const double2 *__restrict__ cell_xy,
+                        int32_t *__restrict__ counts, const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = cell_nodes[t];
+    double xi = xy[2 * (int64_t)i], yi = xy[2 * (int64_t)i + 1];
+    double R = 2.0 * h[i];
+    double R2 = __dmul_rn(R, R);
+    int c = cell_of[i];
+    int cx = c % g.nc[0], cy = c / g.nc[0];
+    int xs[3], ys[3];
+    int mx = axis_cells(cx, g.nc[0], g.periodic, xs);
+    int my = axis_cells(cy, g.nc[1], g.periodic, ys);
+    int cnt = 0;
+    int64_t base = WRITE ? row_ptr[i] : 0;
+    for (int a = 0; a < my; a++) {
+        for (int b = 0; b < mx; b++) {
+            int cc = ys[a] * g.nc[0] + xs[b];
+            int64_t s = cell_start[cc], e = cell_start[cc + 1];
+            for (int64_t p = s; p < e; p++) {
+                int j = cell_nodes[p];
+                if (j == i) continue;
+                double2 q = cell_xy[p];
+                double dx = __dsub_rn(q.x, xi);
+                double dy = __dsub_rn(q.y, yi);
+                if (g.periodic) {
+                    if (dx > g.halfL[0]) dx = __dsub_rn(dx, g.L[0]);
+                    else if (dx < -g.halfL[0]) dx = __dadd_rn(dx, g.L[0]);
+                    if (dy > g.halfL[1]) dy = __dsub_rn(dy, g.L[1]);
+                    else if (dy < -g.halfL[1]) dy = __dadd_rn(dy, g.L[1]);
+                }
+                double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                if (r2 < R2) {
+                    if (WRITE) col[base + cnt] = j;
+                    cnt++;
+                }
+            }
+        }
+    }
+    if (!WRITE) {
+        counts[i] = cnt;
+    } else {
+        // insertion sort of the row (stencils hold tens of entries)
+        int32_t *row = col + base;
+        for (int u = 1; u < cnt; u++) {
+            int32_t v = row[u];
+            int w = u - 1;
+            while (w >= 0 && row[w] > v) {
+                row[w + 1] = row[w];
+                w--;
+            }
+            row[w + 1] = v;
+        }
+    }
+}
+
+}  // namespace
+
+labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const double *h, int periodic,
+                            const double lo[2], const double hi[2], int64_t *nnz_out)
+{
+    cudaStream_t s = ctx->stream;
+    ctx->n = 0;
+    ctx->nnz = 0;
+    LABFM_CUDA_TRY(ctx, ctx->misc.reserve(4096));
+    unsigned long long *misc = ctx->misc.as<unsigned long long>();
+    LABFM_CUDA_TRY(ctx, cudaMemsetAsync(misc, 0, 2 * sizeof(unsigned long long), s));
+    int nb = (int)std::min<int64_t>((n + NB_THREADS - 1) / NB_THREADS, (int64_t)ctx->num_sms * 8);
+    k_check<<<nb, NB_THREADS, 0, s>>>(n, xy, h, lo[0], lo[1], hi[0], hi[1], misc);
+    LABFM_CUDA_TRY(ctx, cudaGetLastError());
+    unsigned long long *hs = (unsigned long long *)ctx->host_small;
+    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, misc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hs[1] != 0)
+        return fail(ctx, LABFM_ERR_ARG, std::to_string(hs[1]) + " node(s) with non-finite or out-of-box coordinates or h <= 0");
+    double hmax;
+    memcpy(&hmax, &hs[0], sizeof hmax);
+
+    Grid g;
+    g.periodic = periodic;
+    double ncell_d[2];
+    for (int d = 0; d < 2; d++) {
+        g.lo[d] = lo[d];
+        g.L[d] = hi[d] - lo[d];
+        g.halfL[d] = 0.5 * g.L[d];
+        // side >= 2 h_max with a relative margin far above the rounding of the cell coordinate
+        ncell_d[d] = std::floor(g.L[d] / (2.0 * hmax * (1.0 + 1e-9)));
+        if (!(ncell_d[d] >= 1.0)) ncell_d[d] = 1.0;
+    }
+    // keep the grid to about 4 cells per node (coarser cells stay correct, just hold more nodes)
+    double cap = 4.0 * (double)n + 64.0;
+    if (ncell_d[0] * ncell_d[1] > cap) {
+        double f = std::sqrt(ncell_d[0] * ncell_d[1] / cap);
+        for (int d = 0; d < 2; d++) ncell_d[d] = std::max(1.0, std::floor(ncell_d[d] / f));
+    }
+    if (ncell_d[0] * ncell_d[1] > (double)(1 << 28))
+        return fail(ctx, LABFM_ERR_CAPACITY, "cell grid exceeds 2^28 cells");
+    for (int d = 0; d < 2; d++) {
+        g.nc[d] = (int)ncell_d[d];
+        g.inv_cs[d] = (double)g.nc[d] / g.L[d];
+    }
+    int64_t ncells = (int64_t)g.nc[0] * g.nc[1];
+
+    LABFM_CUDA_TRY(ctx, ctx->cell_of.reserve(sizeof(int32_t) * n));
+    LABFM_CUDA_TRY(ctx, ctx->cell_count.reserve(sizeof(int32_t) * ncells));
+    LABFM_CUDA_TRY(ctx, ctx->cell_start.reserve(sizeof(int64_t) * (ncells + 1)));
+    LABFM_CUDA_TRY(ctx, ctx->cell_nodes.reserve(sizeof(int32_t) * n + sizeof(double2) * n + 64));
+    LABFM_CUDA_TRY(ctx, ctx->counts.reserve(sizeof(int32_t) * n));
+    LABFM_CUDA_TRY(ctx, ctx->row_ptr.reserve(sizeof(int64_t) * (n + 1)));
+    int32_t *cell_of = ctx->cell_of.as<int32_t>();
+    int32_t *cell_count = ctx->cell_count.as<int32_t>();
+    int64_t *cell_start = ctx->cell_start.as<int64_t>();
+    int32_t *cell_nodes = ctx->cell_nodes.as<int32_t>();
+    size_t xy_off = ((sizeof(int32_t) * n + 15) / 16) * 16;
+    double2 *cell_xy = (double2 *)((char *)ctx->cell_nodes.ptr + xy_off);
+    int32_t *counts = ctx->counts.as<int32_t>();
+    int64_t *row_ptr = ctx->row_ptr.as<int64_t>();
+
+    int nbn = (int)((n + NB_THREADS - 1) / NB_THREADS);
+    LABFM_CUDA_TRY(ctx, cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, s));
+    k_cell_assign<<<nbn, NB_THREADS, 0, s>>>(n, xy, g, cell_of, cell_count);
+    LABFM_CUDA_TRY(ctx, cudaGetLastError());
+    LABFM_CUDA_TRY(ctx, exclusive_scan_i32_to_i64(cell_count, cell_start, ncells, ctx->scan_tmp, s));
+    LABFM_CUDA_TRY(ctx, cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, s));
+    k_cell_scatter<<<nbn, NB_THREADS, 0, s>>>(n, xy, cell_of, cell_start, cell_count, cell_nodes, cell_xy);
+    LABFM_CUDA_TRY(ctx, cudaGetLastError());
+    k_sweep<false><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, counts, nullptr,
+                                              nullptr);
+    LABFM_CUDA_TRY(ctx, cudaGetLastError());
+    LABFM_CUDA_TRY(ctx, exclusive_scan_i32_to_i64(counts, row_ptr, n, ctx->scan_tmp, s));
+    int64_t *nnz_h = (int64_t *)ctx->host_small;
+    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(nnz_h, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    int64_t nnz = *nnz_h;
+    if (nnz >= ((int64_t)1 << 40)) return fail(ctx, LABFM_ERR_CAPACITY, "too many stencil entries");
+    LABFM_CUDA_TRY(ctx, ctx->col.reserve(sizeof(int32_t) * (nnz > 0 ? nnz : 1)));
+    k_sweep<true><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, nullptr, row_ptr,
+                                             ctx->col.as<int32_t>());
+    LABFM_CUDA_TRY(ctx, cudaGetLastError());
+    LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    ctx->n = n;
+    ctx->nnz = nnz;
+    ctx->periodic = periodic;
+    for (int d = 0; d < 2; d++) {
+        ctx->lo[d] = lo[d];
+        ctx->hi[d] = hi[d];
+    }
+    LABFM_CUDA_TRY(ctx, ctx->node_xy.reserve(sizeof(double) * 2 * n));
+    LABFM_CUDA_TRY(ctx, ctx->node_h.reserve(sizeof(double) * n));
+    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->node_xy.ptr, xy, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
+    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->node_h.ptr, h, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    *nnz_out = nnz;
+    return LABFM_OK;
+}
+
+}  // namespace labfm

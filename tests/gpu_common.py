@@ -1,0 +1,89 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI, slice its CSR
+output, and compare against the CPU oracle with tolerances tied to the oracle's own FP64
+rounding floor (FP64 oracle vs long-double oracle on the same inputs)."""
+import numpy as np
+
+import labfm_synth as S
+import oracle
+
+# k -> h/s used by the order-k parity cases (each above the critical h/dr of Sec. 2.2)
+HS = {1: 1.2, 2: 1.2, 3: 1.3, 4: 1.4, 5: 1.6, 6: 1.8, 7: 2.0, 8: 2.2}
+OPS = {1: ("dx", "dy"), 2: ("dx", "dy", "lap"), 3: ("dx", "dy", "lap"), 4: ("dx", "dy", "lap", "lap2"),
+       5: ("dx", "dy", "lap", "lap2"), 6: ("dx", "dy", "lap", "lap3"), 7: ("dx", "dy", "lap", "lap3"),
+       8: ("dx", "dy", "lap", "lap4")}
+
+# Absolute floors of the weight/derivative tolerance (the benchmark spec's 1e-11 where FP64 allows it)
+TOL_FLOOR_MAX = 1e-11
+TOL_FLOOR_MEDIAN = 1e-12
+# The GPU's rounding error is of the same kind as the FP64 oracle's (same algorithm, other
+# summation order and FMA use); this factor bounds the ratio of the two error distributions.
+FLOOR_FACTOR = 30.0
+
+
+def c_matrix(k, ops):
+    return np.stack([S.op_c_vector(o, k) for o in ops])
+
+
+def gpu_run(ns, k, ops, rbf="wendland_c2", weight_dtype="f64", order=None):
+    import torch
+
+    from paper_1912_06441_gb300 import Labfm
+
+    dev = torch.device("cuda", 0)
+    L = Labfm(0)
+    xy = torch.from_numpy(np.ascontiguousarray(ns.xy)).to(dev)
+    h = torch.from_numpy(np.ascontiguousarray(ns.h)).to(dev)
+    L.build_neighbours(xy, h, ns.periodic, ns.lo, ns.hi)
+    status = torch.full((ns.n,), -1, dtype=torch.int32, device=dev)
+    od = None if order is None else torch.from_numpy(np.ascontiguousarray(order, dtype=np.int8)).to(dev)
+    nbad = L.build_weights(c_matrix(k, ops), order=od, uniform_order=k, rbf=rbf, weight_dtype=weight_dtype,
+                           node_status=status)
+    rp, col = L.get_neighbours()
+    w = L.get_weights()
+    torch.cuda.synchronize()
+    return L, rp.cpu().numpy(), col.cpu().numpy(), w.cpu().numpy().astype(np.float64), status.cpu().numpy(), nbad
+
+
+def rows_of(rp, col, q):
+    """CSR of the rows q of (rp, col)."""
+    lens = rp[q + 1] - rp[q]
+    sub_rp = np.zeros(len(q) + 1, dtype=np.int64)
+    sub_rp[1:] = np.cumsum(lens)
+    idx = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in q]) if len(q) else np.zeros(0, np.int64)
+    return sub_rp, col[idx], idx
+
+
+def node_rel_err(a, b, rp):
+    """Per node and operator: ||a - b|| / ||b|| over the node's stencil entries."""
+    nq = len(rp) - 1
+    out = np.zeros((nq, a.shape[1]))
+    for t in range(nq):
+        s = slice(rp[t], rp[t + 1])
+        den = np.linalg.norm(b[s], axis=0)
+        den[den == 0] = 1.0
+        out[t] = np.linalg.norm(a[s] - b[s], axis=0) / den
+    return out
+
+
+def oracle_refs(ns, k, ops, q, rp_q, col_q, rbf="wendland_c2", order=None):
+    C = c_matrix(k, ops)
+    kw = dict(queries=q, rbf=rbf, lo=ns.lo, hi=ns.hi)
+    if order is None:
+        kw["k"] = k
+    else:
+        kw["order"] = order
+    r64 = oracle.build_weights(ns.xy, ns.h, ns.periodic, rp_q, col_q, C, **kw)
+    rld = oracle.build_weights(ns.xy, ns.h, ns.periodic, rp_q, col_q, C, precision="ld", **kw)
+    return r64, rld
+
+
+def assert_weights_parity(w_gpu_q, r64, rld, rp_q, label=""):
+    """GPU weights vs the long-double oracle, bounded by the FP64 oracle's own error."""
+    ok = (r64["status"] == 0) & (rld["status"] == 0)
+    e_gpu = node_rel_err(w_gpu_q, rld["w"], rp_q)[ok]
+    e_64 = node_rel_err(r64["w"], rld["w"], rp_q)[ok]
+    tol_max = max(TOL_FLOOR_MAX, FLOOR_FACTOR * e_64.max())
+    tol_med = max(TOL_FLOOR_MEDIAN, FLOOR_FACTOR * np.median(e_64))
+    assert e_gpu.max() <= tol_max, (label, "max", e_gpu.max(), tol_max, e_64.max())
+    assert np.median(e_gpu) <= tol_med, (label, "median", np.median(e_gpu), tol_med, np.median(e_64))
+    return e_gpu.max(), e_64.max()
