@@ -31,7 +31,8 @@ import labfm_synth as S  # noqa: E402
 METRIC = "order-8 weight build Mnodes/s; apply GB/s vs HBM; mixed vs FP64 at ≤1e-8 err"
 N_SIDE, HS, K, JITTER = 512, 2.2, 8, 0.3
 OPS = ("dx", "dy", "lap", "lap4")
-WORKLOAD = (f"2D periodic jittered lattice {N_SIDE}x{N_SIDE} (+-{JITTER}s), h={HS}s, Wendland C2, order {K} "
+def workload_name():
+    return (f"2D periodic jittered lattice {N_SIDE}x{N_SIDE} (+-{JITTER}s), h={HS}s, Wendland C2, order {K} "
             f"(p=44), FP64 weights for dx, dy, lap, lap4; apply to 16 Fourier modes (k<=32); 1 RK4 step")
 C_ADV = (1.0, 0.5)
 NU = 1e-3
@@ -185,6 +186,80 @@ def cpu_baseline(ns, field, C, sample=1024, seed=9):
             "seconds": t}
 
 
+def kernel_source_hash():
+    import hashlib
+
+    hsh = hashlib.sha256()
+    for f in ("build_fp64.cu", "abf.cuh"):
+        with open(os.path.join(ROOT, "paper_1912_06441_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
+def build_traffic(n):
+    """DRAM bytes per launch of the build kernel from the committed ncu capture, scaled by
+    node count; None if the kernel source changed since the capture."""
+    prof = os.path.join(ROOT, "profiles", "build_fp64_traffic.json")
+    try:
+        with open(prof) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    if rec.get("source_sha256") != kernel_source_hash():
+        return None
+    return rec["dram_bytes_per_node"] * n
+
+
+def _time(torch, fn, reps=3):
+    best = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def extra_measurements(torch, P, dev, local_rank, ns, field, hbm):
+    """Outside the timed step: the order-6 FP64 build of the same node count (h = 1.8 s,
+    nabla^6 for the hyperviscosity operator) and the FP32-weight / FP32-field apply."""
+    out = {}
+    n = ns.n
+    L6 = P.Labfm(local_rank)
+    ns6 = S.jittered_lattice(N_SIDE, 1.8, 6, jitter=JITTER, seed=2)
+    xy6 = torch.from_numpy(ns6.xy).to(dev)
+    h6 = torch.from_numpy(ns6.h).to(dev)
+    L6.build_neighbours(xy6, h6, True)
+    C6 = np.stack([S.op_c_vector(o, 6) for o in ("dx", "dy", "lap", "lap3")])
+    L6.build_weights(C6, uniform_order=6)
+    ms6 = _time(torch, lambda: L6.build_weights(C6, uniform_order=6))
+    out["order6_build_fp64"] = {"ms": ms6, "mnodes_per_s": n / (ms6 * 1e-3) / 1e6, "nnz": L6.nnz,
+                                "tflops_algorithmic": build_flops_per_node(6, L6.nnz / n, 4) * n / (ms6 * 1e-3) / 1e12}
+    L6.close()
+    L32 = P.Labfm(local_rank)
+    xy = torch.from_numpy(ns.xy).to(dev)
+    h = torch.from_numpy(ns.h).to(dev)
+    L32.build_neighbours(xy, h, True)
+    C = np.stack([S.op_c_vector(o, K) for o in OPS])
+    L32.build_weights(C, uniform_order=K, weight_dtype="f32")
+    f32 = torch.from_numpy(field.value(ns.xy).astype(np.float32)).to(dev)
+    o32 = torch.empty((len(OPS), n), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ts = []
+    for _ in range(5):
+        flush.zero_()
+        ts.append(_time(torch, lambda: L32.apply(f32, out=o32), reps=1))
+    ms = float(np.median(ts))
+    by = apply_bytes(n, L32.nnz, len(OPS), wbytes=4, fbytes=4)
+    out["apply_f32"] = {"kernel": "k_apply<4,float,float>", "ms": ms, "achieved_gbs": by / (ms * 1e-3) / 1e9,
+                        "frac_of_hbm": by / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": by,
+                        "derivatives_per_s": len(OPS) * n / (ms * 1e-3)}
+    L32.close()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -200,7 +275,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mnodes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean([x["seconds"] for x in vals])) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_nodes": args.ref_sample},
+            "config": {"workload": workload_name(), "sample_nodes": args.ref_sample},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "Mnodes/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -310,19 +385,12 @@ def run_labfm(args, rank, world, local_rank):
     abytes = apply_bytes(n, nnz, len(OPS))
     a_ach = abytes / (apply_ms * 1e-3) / 1e9
     hbm, hbm_src = hbm_peak()
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "build_fp64_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as fh:
-                traffic = json.load(fh).get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = build_traffic(n)
     line = {
         "metric": METRIC, "value": value, "unit": "Mnodes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": n, "nnz": nnz, "order": K, "ops": list(OPS),
+        "config": {"workload": workload_name(), "nodes": n, "nnz": nnz, "order": K, "ops": list(OPS),
                    "l2": "256 MB buffer written between timed steps (inside the timed region)",
                    "parallelism": f"replicas x{world}"},
         "phases_ms": {"neighbours": float(np.mean(phase[:, 0])), "build_fp64": build_ms, "apply": apply_ms,
@@ -343,6 +411,7 @@ def run_labfm(args, rank, world, local_rank):
         "gpu_launches": args.steps * (nbr_launches(n, ncells_of(HS / N_SIDE)) + 1 + 1 + 1 + 4),
         "clocks": clk,
     }
+    line["extra"] = extra_measurements(torch, P, dev, local_rank, ns, field, hbm)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ns, field, C, sample=args.cpu_sample)
     print(json.dumps(line), flush=True)
@@ -350,6 +419,7 @@ def run_labfm(args, rank, world, local_rank):
 
 
 def main():
+    global N_SIDE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -358,7 +428,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1024)
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-side", type=int, default=512,
+                    help="lattice side (default 512; smaller sizes are for profiler captures only)")
     args = ap.parse_args()
+    N_SIDE = args.n_side
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

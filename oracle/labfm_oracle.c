@@ -499,10 +499,11 @@ void orc_apply(const int64_t *queries, int64_t nq, const int64_t *row_ptr, const
 /* ---------------------------------------------------------------------------
  * Classical RK4 (Sec. 4.1) for du/dt = F(u), F(u)_i = sum_d beta_d L_i^d(u),
  * over all n nodes (row_ptr/col/w cover every node).  Nodes with frozen[i]
- * set keep their value (Dirichlet nodes, Sec. 4.1).
+ * set keep their value (Dirichlet nodes, Sec. 4.1): a fixed boundary value has
+ * du/dt = 0, so F_i = 0 there in every stage.
  * ------------------------------------------------------------------------- */
 static void rhs_eval(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w, int n_ops,
-                     const double *beta, const real *u, real *F)
+                     const double *beta, const real *u, real *F, const uint8_t *frozen)
 {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
@@ -514,7 +515,7 @@ static void rhs_eval(int64_t n, const int64_t *row_ptr, const int32_t *col, cons
             for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) sd += (u[col[e]] - u[i]) * (real)w[e * n_ops + d];
             s += (real)beta[d] * sd;
         }
-        F[i] = s;
+        F[i] = (frozen && frozen[i]) ? 0 : s;
     }
 }
 
@@ -531,15 +532,14 @@ int orc_rk4(int64_t n, const int64_t *row_ptr, const int32_t *col, const double 
     for (int64_t i = 0; i < n; i++) u[i] = (real)u_io[i];
     real hdt = (real)dt / 2, fdt = (real)dt;
     for (int64_t s = 0; s < nsteps; s++) {
-        rhs_eval(n, row_ptr, col, w, n_ops, beta, u, k1);
+        rhs_eval(n, row_ptr, col, w, n_ops, beta, u, k1, frozen);
         for (int64_t i = 0; i < n; i++) ut[i] = u[i] + hdt * k1[i];
-        rhs_eval(n, row_ptr, col, w, n_ops, beta, ut, k2);
+        rhs_eval(n, row_ptr, col, w, n_ops, beta, ut, k2, frozen);
         for (int64_t i = 0; i < n; i++) ut[i] = u[i] + hdt * k2[i];
-        rhs_eval(n, row_ptr, col, w, n_ops, beta, ut, k3);
+        rhs_eval(n, row_ptr, col, w, n_ops, beta, ut, k3, frozen);
         for (int64_t i = 0; i < n; i++) ut[i] = u[i] + fdt * k3[i];
-        rhs_eval(n, row_ptr, col, w, n_ops, beta, ut, k4);
-        for (int64_t i = 0; i < n; i++)
-            if (!(frozen && frozen[i])) u[i] = u[i] + fdt / 6 * (k1[i] + 2 * k2[i] + 2 * k3[i] + k4[i]);
+        rhs_eval(n, row_ptr, col, w, n_ops, beta, ut, k4, frozen);
+        for (int64_t i = 0; i < n; i++) u[i] = u[i] + fdt / 6 * (k1[i] + 2 * k2[i] + 2 * k3[i] + k4[i]);
     }
     for (int64_t i = 0; i < n; i++) u_io[i] = (double)u[i];
     free(u); free(ut); free(k1); free(k2); free(k3); free(k4);

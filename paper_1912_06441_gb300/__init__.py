@@ -81,7 +81,7 @@ class _DevView:
     """__cuda_array_interface__ wrapper so torch can view a context-owned device buffer."""
 
     def __init__(self, ptr, shape, typestr):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 3, "strides": None, "stream": None}
 
 
@@ -140,7 +140,7 @@ class Labfm:
             raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
         if not t.is_contiguous():
             raise ValueError(f"{name} must be contiguous")
-        if numel is not None and t.numel() != numel:
+        if numel is not None and self.n > 0 and t.numel() != numel:
             raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
         return ct.c_void_p(t.data_ptr())
 

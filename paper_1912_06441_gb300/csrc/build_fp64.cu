@@ -50,56 +50,63 @@ struct BuildArgs {
     double C[MAX_OPS * PMAX];  // target vectors, row d = C^d (physical units)
 };
 
-// Monomials and ABFs of one scaled offset, written to X[0..P), W[0..P).
+// Monomials and ABFs of one scaled offset (x, y), written to X[0..P), W[0..P).
+// In polar form q = |(x, y)|, (u, v) = (x, y)/q, degree n = a + b:
+//   X_(a,b) = q^n u^a v^b / (a! b!)          d^(a,b)|r| = q^(1-n) P_(a,b)(u, v)
+// and both use the same n+1 products u^t v^(n-t), formed once per degree.  Results go
+// straight to shared memory to keep the register footprint small.
 template <int K>
 __device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__restrict__ X, double *__restrict__ W)
 {
-    constexpr int P = p_of_k(K);
-    double r = sqrt(x * x + y * y);
-    double ir = 1.0 / r;
-    double u = x * ir, v = y * ir;
+    double q = sqrt(x * x + y * y);
+    double iq = 1.0 / q;
+    double u = x * iq, v = y * iq;
     double d1, d2, d3;
-    rbf_derivs(rbf, r, d1, d2, d3);
-    double xp[K + 1], yp[K + 1], up[K + 1], vp[K + 1], irp[K];
-    xp[0] = yp[0] = up[0] = vp[0] = irp[0] = 1.0;
+    rbf_derivs(rbf, q, d1, d2, d3);
+    double up[K + 1], vp[K + 1];
+    up[0] = vp[0] = 1.0;
 #pragma unroll
     for (int t = 1; t <= K; t++) {
-        xp[t] = xp[t - 1] * x;
-        yp[t] = yp[t - 1] * y;
         up[t] = up[t - 1] * u;
         vp[t] = vp[t - 1] * v;
     }
+    double qn = 1.0;      // q^n
+    double iqn = 1.0;     // q^(1-n)
+    double rxx = 0.0, rxy = 0.0, ryy = 0.0;
 #pragma unroll
-    for (int t = 1; t < K; t++) irp[t] = irp[t - 1] * ir;
-    double dr[P];  // d^alpha |r|
+    for (int n = 1; n <= K; n++) {
+        qn *= q;
+        if (n > 1) iqn *= iq;
+        double mono[K + 1];
 #pragma unroll
-    for (int e = 0; e < P; e++) {
-        const int n = elem_degree(e), a = elem_a(e), b = n - a;
-        double s = 0.0;
+        for (int t = 0; t <= n; t++) mono[t] = up[t] * vp[n - t];
 #pragma unroll
-        for (int t = 0; t <= n; t++) s = fma(c_rpoly.c[e][t], up[t] * vp[n - t], s);
-        dr[e] = s * irp[n - 1];
-        X[e] = xp[a] * yp[b] * (c_invfact[a] * c_invfact[b]);
-    }
-    // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
+        for (int a = n; a >= 0; a--) {
+            const int e = p_of_k(n - 1) + (n - a);
+            X[e] = qn * mono[a] * (c_invfact[a] * c_invfact[n - a]);
+            double s = 0.0;
 #pragma unroll
-    for (int e = 0; e < P; e++) W[e] = d1 * dr[e];
-    if constexpr (K >= 2) {
-        const double rxx = dr[2], rxy = dr[3], ryy = dr[4];
-        W[2] = fma(d2, u * u, W[2]);
-        W[3] = fma(d2, u * v, W[3]);
-        W[4] = fma(d2, v * v, W[4]);
-        if constexpr (K >= 3) {
-            W[5] = fma(d3, u * u * u, fma(d2, 3.0 * u * rxx, W[5]));
-            W[6] = fma(d3, u * u * v, fma(d2, v * rxx + 2.0 * u * rxy, W[6]));
-            W[7] = fma(d3, u * v * v, fma(d2, u * ryy + 2.0 * v * rxy, W[7]));
-            W[8] = fma(d3, v * v * v, fma(d2, 3.0 * v * ryy, W[8]));
+            for (int t = 0; t <= n; t++) s = fma(c_rpoly.c[e][t], mono[t], s);
+            const double dr = s * iqn;
+            double wv = d1 * dr;
+            // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
+            if (n == 2) {
+                if (a == 2) { rxx = dr; wv = fma(d2, u * u, wv); }
+                if (a == 1) { rxy = dr; wv = fma(d2, u * v, wv); }
+                if (a == 0) { ryy = dr; wv = fma(d2, v * v, wv); }
+            } else if (n == 3) {
+                if (a == 3) wv = fma(d3, u * u * u, fma(d2, 3.0 * u * rxx, wv));
+                if (a == 2) wv = fma(d3, u * u * v, fma(d2, v * rxx + 2.0 * u * rxy, wv));
+                if (a == 1) wv = fma(d3, u * v * v, fma(d2, u * ryy + 2.0 * v * rxy, wv));
+                if (a == 0) wv = fma(d3, v * v * v, fma(d2, 3.0 * v * ryy, wv));
+            }
+            W[e] = wv;
         }
     }
 }
 
 template <int K>
-__global__ void __launch_bounds__(BUILD_THREADS) k_build_fp64(BuildArgs A)
+__global__ void __launch_bounds__(BUILD_THREADS, 3) k_build_fp64(BuildArgs A)
 {
     using C = Cfg<K>;
     constexpr int P = C::P, LDX = C::LDX, NB = C::NB, LDA = C::LDA, TM = C::TM, TN = C::TN;
@@ -109,6 +116,8 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_fp64(BuildArgs A)
     double *Am = Ws + NB * LDX;        // [P][LDA]  augmented [M | Chat]
     __shared__ int s_piv;
     __shared__ double s_inv;
+    __shared__ double s_invpiv[P];  // 1 / pivot of each column, reused by the back substitution
+    __shared__ double s_hpow[KMAX + 1];  // h^-n
     __shared__ int s_flag;  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
 
     const int tid = threadIdx.x;
@@ -134,6 +143,13 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_fp64(BuildArgs A)
         }
         const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], hi = A.h[i];
         const double ihi = 1.0 / hi;
+        if (tid == 0) {
+            double s = 1.0;
+            for (int t = 0; t <= K; t++) {
+                s_hpow[t] = s;
+                s *= ihi;
+            }
+        }
 
         double acc[TM][TN];
 #pragma unroll
@@ -201,10 +217,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_fp64(BuildArgs A)
         }
         for (int t = tid; t < P * n_ops; t += BUILD_THREADS) {
             int m = t / n_ops, d = t % n_ops;
-            int deg = elem_degree(m);
-            double s = 1.0;
-            for (int q = 0; q < deg; q++) s *= ihi;
-            Am[m * LDA + P + d] = A.C[d * PMAX + m] * s;
+            Am[m * LDA + P + d] = A.C[d * PMAX + m] * s_hpow[elem_degree(m)];
         }
         __syncthreads();
         const bool bad_m = (s_flag & 4) != 0;
@@ -239,6 +252,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_fp64(BuildArgs A)
                     } else {
                         s_inv = 1.0 / pv;
                     }
+                    s_invpiv[c] = s_inv;
                 }
             }
             __syncthreads();
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_build_fp64(BuildArgs A)
         }
         // back substitution on the n_ops right-hand sides
         for (int c = P - 1; c >= 0 && !bad_m; c--) {
-            if (tid < n_ops) Am[c * LDA + P + tid] = Am[c * LDA + P + tid] / Am[c * LDA + c];
+            if (tid < n_ops) Am[c * LDA + P + tid] *= s_invpiv[c];
             __syncthreads();
             for (int t = tid; t < c * n_ops; t += BUILD_THREADS) {
                 int r = t / n_ops, d = t % n_ops;

@@ -496,8 +496,13 @@ def test_rk4_linear_system_is_taylor_polynomial():
     ref = np.linalg.matrix_power(P, 3) @ u0
     got = oracle.rk4(rp, col, r["w"], beta, u0, dt, 3)
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
-    # frozen nodes keep their value
+    # frozen (Dirichlet) nodes keep their value: du/dt = 0 there, i.e. their rows of A vanish,
+    # in every stage -- the step is then the Taylor polynomial of the row-zeroed matrix
     fz = np.zeros(n, dtype=np.uint8)
     fz[::5] = 1
     got2 = oracle.rk4(rp, col, r["w"], beta, u0, dt, 3, frozen=fz)
     assert np.array_equal(got2[::5], u0[::5])
+    Zf = Z.copy()
+    Zf[fz.astype(bool)] = 0.0
+    Pf = np.eye(n) + Zf + Zf @ Zf / 2 + Zf @ Zf @ Zf / 6 + Zf @ Zf @ Zf @ Zf / 24
+    np.testing.assert_allclose(got2, np.linalg.matrix_power(Pf, 3) @ u0, rtol=0, atol=1e-13)
