@@ -222,22 +222,51 @@ def _time(torch, fn, reps=3):
     return best
 
 
+def deriv_errors(d, ref):
+    """Per operator: |d - ref| relative to max |ref| (median, 99th percentile, max over nodes)
+    and the normalised L2 norm of Sec. 3.1."""
+    d = d.astype(np.float64)
+    ref = ref.astype(np.float64)
+    sc = np.abs(ref).max(axis=1, keepdims=True)
+    e = np.abs(d - ref) / sc
+    return {"l2": (np.linalg.norm(d - ref, axis=1) / np.linalg.norm(ref, axis=1)).tolist(),
+            "median": np.median(e, axis=1).tolist(), "p99": np.percentile(e, 99, axis=1).tolist(),
+            "max": e.max(axis=1).tolist()}
+
+
+def mixed_vs_fp64(torch, P, dev, local_rank, nsx, k, ops, field):
+    """Mixed-precision and FP64 builds of the same node set: build time and the error of the
+    mixed derivatives against the FP64 ones (both on the GPU), per operator."""
+    n = nsx.n
+    L = P.Labfm(local_rank)
+    L.build_neighbours(torch.from_numpy(nsx.xy).to(dev), torch.from_numpy(nsx.h).to(dev), True)
+    C = np.stack([S.op_c_vector(o, k) for o in ops])
+    f = torch.from_numpy(field.value(nsx.xy)).to(dev)
+    res = {}
+    ders = {}
+    for prec in ("fp64", "mixed"):
+        L.build_weights(C, uniform_order=k, precision=prec)
+        ms = _time(torch, lambda: L.build_weights(C, uniform_order=k, precision=prec))
+        ders[prec] = L.apply(f).cpu().numpy()
+        res[prec] = {"ms": ms, "mnodes_per_s": n / (ms * 1e-3) / 1e6}
+    res["speedup_mixed_over_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    res["ops"] = list(ops)
+    res["deriv_err_mixed_vs_fp64"] = deriv_errors(ders["mixed"], ders["fp64"])
+    res["nref"] = 2 if k >= 6 else 1
+    L.close()
+    return res
+
+
 def extra_measurements(torch, P, dev, local_rank, ns, field, hbm):
-    """Outside the timed step: the order-6 FP64 build of the same node count (h = 1.8 s,
-    nabla^6 for the hyperviscosity operator) and the FP32-weight / FP32-field apply."""
+    """Outside the timed step: FP64 and mixed-precision builds at order 8 and order 6
+    (h = 1.8 s, nabla^6 for the hyperviscosity operator) with the mixed-vs-FP64 derivative
+    errors, and the FP32-weight / FP32-field apply."""
     out = {}
     n = ns.n
-    L6 = P.Labfm(local_rank)
+    out["order8_mixed_vs_fp64"] = mixed_vs_fp64(torch, P, dev, local_rank, ns, K, OPS, field)
     ns6 = S.jittered_lattice(N_SIDE, 1.8, 6, jitter=JITTER, seed=2)
-    xy6 = torch.from_numpy(ns6.xy).to(dev)
-    h6 = torch.from_numpy(ns6.h).to(dev)
-    L6.build_neighbours(xy6, h6, True)
-    C6 = np.stack([S.op_c_vector(o, 6) for o in ("dx", "dy", "lap", "lap3")])
-    L6.build_weights(C6, uniform_order=6)
-    ms6 = _time(torch, lambda: L6.build_weights(C6, uniform_order=6))
-    out["order6_build_fp64"] = {"ms": ms6, "mnodes_per_s": n / (ms6 * 1e-3) / 1e6, "nnz": L6.nnz,
-                                "tflops_algorithmic": build_flops_per_node(6, L6.nnz / n, 4) * n / (ms6 * 1e-3) / 1e12}
-    L6.close()
+    out["order6_mixed_vs_fp64"] = mixed_vs_fp64(torch, P, dev, local_rank, ns6, 6, ("dx", "dy", "lap", "lap3"),
+                                                field)
     L32 = P.Labfm(local_rank)
     xy = torch.from_numpy(ns.xy).to(dev)
     h = torch.from_numpy(ns.h).to(dev)

@@ -57,8 +57,15 @@ enum {
 
 /* Arithmetic of the moment-matrix assembly (Eq. disc_form) and solve (Eq. lsys). */
 enum {
-    LABFM_PREC_FP64 = 0 /* everything in IEEE double */
+    LABFM_PREC_FP64 = 0, /* everything in IEEE double */
+    /* X and W in double; M, its partially pivoted LU, Psi and W . Psi in double-float
+     * (pairs of FP32, ~48 bits, on the FP32 pipes); then iterative refinement on the
+     * polynomial-reproduction residual C - sum_j X_j w_j computed in double (the moment
+     * conditions of Sec. 2.1).  Default: 1 refinement step for k <= 5, 2 for k >= 6. */
+    LABFM_PREC_MIXED = 1
 };
+/* LABFM_PREC_MIXED with exactly n refinement steps, n = 0..4 */
+#define LABFM_PREC_MIXED_REFINE(n) (LABFM_PREC_MIXED | (((n) + 1) << 8))
 
 /* Storage type of weights and fields. */
 enum { LABFM_F64 = 0, LABFM_F32 = 1 };

@@ -19,7 +19,17 @@ from .build import LIB as _LIB_PATH, build_library
 __all__ = ["Labfm", "LabfmError", "load_library", "RBF", "PREC", "DTYPE", "NODE", "C_FUNCTIONS"]
 
 RBF = {"wendland_c2": 0, "quadratic": 1, "cone": 2, "wendland_c6": 3, "gaussian": 4}
-PREC = {"fp64": 0}
+PREC = {"fp64": 0, "mixed": 1}
+
+
+def precision_code(precision: str, refine: int | None = None) -> int:
+    """C ABI precision value: LABFM_PREC_FP64, LABFM_PREC_MIXED or LABFM_PREC_MIXED_REFINE(refine)."""
+    code = PREC[precision]
+    if refine is not None:
+        if precision != "mixed" or not 0 <= refine <= 4:
+            raise ValueError("refine applies to precision='mixed', 0..4 steps")
+        code |= (refine + 1) << 8
+    return code
 DTYPE = {"f64": 0, "f32": 1}
 NODE = {"ok": 0, "singular": 1, "undersampled": 2, "nonfinite": 3}
 STATUS = {0: "LABFM_OK", 1: "LABFM_ERR_ARG", 2: "LABFM_ERR_CUDA", 3: "LABFM_ERR_NOMEM", 4: "LABFM_ERR_CAPACITY",
@@ -183,7 +193,8 @@ class Labfm:
         return row_ptr, col
 
     def build_weights(self, C, order=None, uniform_order: int = 4, rbf: str = "wendland_c2",
-                      precision: str = "fp64", weight_dtype: str = "f64", node_status=None) -> int:
+                      precision: str = "fp64", weight_dtype: str = "f64", node_status=None,
+                      refine: int | None = None) -> int:
         """Weights w_ji^d for the target vectors C (rows, D ordering, Sec. 2); returns #flagged nodes.
 
         Raises LabfmError(LABFM_ERR_SINGULAR) only if ``node_status`` is None and a node was
@@ -201,7 +212,8 @@ class Labfm:
         self._sync_stream()
         nbad = ct.c_int64()
         st = self.lib.labfm_build_weights(self._ctx, po, int(uniform_order), RBF[rbf], n_ops,
-                                          Cp.ctypes.data_as(ct.c_void_p), PREC[precision], DTYPE[weight_dtype], ps,
+                                          Cp.ctypes.data_as(ct.c_void_p), precision_code(precision, refine),
+                                          DTYPE[weight_dtype], ps,
                                           ct.byref(nbad))
         if st == 5 and node_status is not None:
             st = 0

@@ -132,4 +132,67 @@ __device__ __forceinline__ void rbf_derivs(int rbf, double q, double &d1, double
     }
 }
 
+namespace {
+
+__constant__ RPolyTable c_rpoly = make_rpoly_table();
+__constant__ double c_invfact[KMAX + 1] = {1.0,       1.0,        0.5,         1.0 / 6.0,   1.0 / 24.0,
+                                           1.0 / 120, 1.0 / 720., 1.0 / 5040., 1.0 / 40320.};
+
+// Monomials and ABFs of one scaled offset (x, y), written to X[0..P), W[0..P).
+// In polar form q = |(x, y)|, (u, v) = (x, y)/q, degree n = a + b:
+//   X_(a,b) = q^n u^a v^b / (a! b!)          d^(a,b)|r| = q^(1-n) P_(a,b)(u, v)
+// and both use the same n+1 products u^t v^(n-t), formed once per degree.  Results go
+// straight to shared memory to keep the register footprint small.
+template <int K>
+__device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__restrict__ X, double *__restrict__ W)
+{
+    double q = sqrt(x * x + y * y);
+    double iq = 1.0 / q;
+    double u = x * iq, v = y * iq;
+    double d1, d2, d3;
+    rbf_derivs(rbf, q, d1, d2, d3);
+    double up[K + 1], vp[K + 1];
+    up[0] = vp[0] = 1.0;
+#pragma unroll
+    for (int t = 1; t <= K; t++) {
+        up[t] = up[t - 1] * u;
+        vp[t] = vp[t - 1] * v;
+    }
+    double qn = 1.0;      // q^n
+    double iqn = 1.0;     // q^(1-n)
+    double rxx = 0.0, rxy = 0.0, ryy = 0.0;
+#pragma unroll
+    for (int n = 1; n <= K; n++) {
+        qn *= q;
+        if (n > 1) iqn *= iq;
+        double mono[K + 1];
+#pragma unroll
+        for (int t = 0; t <= n; t++) mono[t] = up[t] * vp[n - t];
+#pragma unroll
+        for (int a = n; a >= 0; a--) {
+            const int e = p_of_k(n - 1) + (n - a);
+            X[e] = qn * mono[a] * (c_invfact[a] * c_invfact[n - a]);
+            double s = 0.0;
+#pragma unroll
+            for (int t = 0; t <= n; t++) s = fma(c_rpoly.c[e][t], mono[t], s);
+            const double dr = s * iqn;
+            double wv = d1 * dr;
+            // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
+            if (n == 2) {
+                if (a == 2) { rxx = dr; wv = fma(d2, u * u, wv); }
+                if (a == 1) { rxy = dr; wv = fma(d2, u * v, wv); }
+                if (a == 0) { ryy = dr; wv = fma(d2, v * v, wv); }
+            } else if (n == 3) {
+                if (a == 3) wv = fma(d3, u * u * u, fma(d2, 3.0 * u * rxx, wv));
+                if (a == 2) wv = fma(d3, u * u * v, fma(d2, v * rxx + 2.0 * u * rxy, wv));
+                if (a == 1) wv = fma(d3, u * v * v, fma(d2, u * ryy + 2.0 * v * rxy, wv));
+                if (a == 0) wv = fma(d3, v * v * v, fma(d2, 3.0 * v * ryy, wv));
+            }
+            W[e] = wv;
+        }
+    }
+}
+
+}  // namespace
+
 }  // namespace labfm

@@ -266,13 +266,18 @@ labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int unifor
     if (!C) return fail(ctx, LABFM_ERR_ARG, "C is null");
     for (int t = 0; t < n_ops * LABFM_PMAX; t++)
         if (!std::isfinite(C[t])) return fail(ctx, LABFM_ERR_ARG, "C has a non-finite entry");
-    if (precision != LABFM_PREC_FP64) return fail(ctx, LABFM_ERR_ARG, "unknown precision");
+    {
+        int base = precision & 0xff, forced = (precision >> 8) & 0xf, rest = precision >> 12;
+        bool ok = rest == 0 && (base == LABFM_PREC_FP64 ? forced == 0 : (base == LABFM_PREC_MIXED && forced <= 5));
+        if (!ok) return fail(ctx, LABFM_ERR_ARG, "unknown precision");
+    }
     if (weight_dtype != LABFM_F64 && weight_dtype != LABFM_F32) return fail(ctx, LABFM_ERR_ARG, "bad weight_dtype");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, LABFM_ERR_CUDA, "cudaSetDevice failed");
     ctx->have_weights = false;
     ctx->wcomb_valid = false;
     ctx->graph.release();
-    labfm_status st = run_build_fp64(ctx, order, uniform_order, rbf, n_ops, C, weight_dtype, node_status, n_bad_out);
+    labfm_status st =
+        run_build(ctx, order, uniform_order, rbf, n_ops, C, precision, weight_dtype, node_status, n_bad_out);
     if (st == LABFM_OK || st == LABFM_ERR_SINGULAR) {
         ctx->have_weights = true;
         ctx->n_ops = n_ops;

@@ -15,10 +15,6 @@
 namespace labfm {
 namespace {
 
-__constant__ RPolyTable c_rpoly = make_rpoly_table();
-__constant__ double c_invfact[KMAX + 1] = {1.0,       1.0,        0.5,         1.0 / 6.0,   1.0 / 24.0,
-                                           1.0 / 120, 1.0 / 720., 1.0 / 5040., 1.0 / 40320.};
-
 constexpr int BUILD_THREADS = 256;
 
 template <int K> struct Cfg {
@@ -49,61 +45,6 @@ struct BuildArgs {
     unsigned long long *n_bad;
     double C[MAX_OPS * PMAX];  // target vectors, row d = C^d (physical units)
 };
-
-// Monomials and ABFs of one scaled offset (x, y), written to X[0..P), W[0..P).
-// In polar form q = |(x, y)|, (u, v) = (x, y)/q, degree n = a + b:
-//   X_(a,b) = q^n u^a v^b / (a! b!)          d^(a,b)|r| = q^(1-n) P_(a,b)(u, v)
-// and both use the same n+1 products u^t v^(n-t), formed once per degree.  Results go
-// straight to shared memory to keep the register footprint small.
-template <int K>
-__device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__restrict__ X, double *__restrict__ W)
-{
-    double q = sqrt(x * x + y * y);
-    double iq = 1.0 / q;
-    double u = x * iq, v = y * iq;
-    double d1, d2, d3;
-    rbf_derivs(rbf, q, d1, d2, d3);
-    double up[K + 1], vp[K + 1];
-    up[0] = vp[0] = 1.0;
-#pragma unroll
-    for (int t = 1; t <= K; t++) {
-        up[t] = up[t - 1] * u;
-        vp[t] = vp[t - 1] * v;
-    }
-    double qn = 1.0;      // q^n
-    double iqn = 1.0;     // q^(1-n)
-    double rxx = 0.0, rxy = 0.0, ryy = 0.0;
-#pragma unroll
-    for (int n = 1; n <= K; n++) {
-        qn *= q;
-        if (n > 1) iqn *= iq;
-        double mono[K + 1];
-#pragma unroll
-        for (int t = 0; t <= n; t++) mono[t] = up[t] * vp[n - t];
-#pragma unroll
-        for (int a = n; a >= 0; a--) {
-            const int e = p_of_k(n - 1) + (n - a);
-            X[e] = qn * mono[a] * (c_invfact[a] * c_invfact[n - a]);
-            double s = 0.0;
-#pragma unroll
-            for (int t = 0; t <= n; t++) s = fma(c_rpoly.c[e][t], mono[t], s);
-            const double dr = s * iqn;
-            double wv = d1 * dr;
-            // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
-            if (n == 2) {
-                if (a == 2) { rxx = dr; wv = fma(d2, u * u, wv); }
-                if (a == 1) { rxy = dr; wv = fma(d2, u * v, wv); }
-                if (a == 0) { ryy = dr; wv = fma(d2, v * v, wv); }
-            } else if (n == 3) {
-                if (a == 3) wv = fma(d3, u * u * u, fma(d2, 3.0 * u * rxx, wv));
-                if (a == 2) wv = fma(d3, u * u * v, fma(d2, v * rxx + 2.0 * u * rxy, wv));
-                if (a == 1) wv = fma(d3, u * v * v, fma(d2, u * ryy + 2.0 * v * rxy, wv));
-                if (a == 0) wv = fma(d3, v * v * v, fma(d2, 3.0 * v * ryy, wv));
-            }
-            W[e] = wv;
-        }
-    }
-}
 
 template <int K>
 __global__ void __launch_bounds__(BUILD_THREADS, 3) k_build_fp64(BuildArgs A)
@@ -401,13 +342,22 @@ __global__ void k_order_scatter(int64_t n, const int8_t *__restrict__ order, con
 
 }  // namespace
 
-labfm_status run_build_fp64(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops,
-                            const double *Cin, int weight_dtype, int32_t *node_status, int64_t *n_bad_out)
+static int precision_nref(int precision, int k)
+{
+    int forced = (precision >> 8) & 0xf;  // LABFM_PREC_MIXED_REFINE(n) stores n + 1 here
+    if (forced) return forced - 1;
+    return k >= 6 ? 2 : 1;
+}
+
+labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops, const double *Cin,
+                       int precision, int weight_dtype, int32_t *node_status, int64_t *n_bad_out)
 {
     cudaStream_t s = ctx->stream;
     const int64_t n = ctx->n;
+    const bool mixed = (precision & 0xff) == LABFM_PREC_MIXED;
     size_t wbytes = (size_t)ctx->nnz * n_ops * (weight_dtype == LABFM_F64 ? 8 : 4);
     LABFM_CUDA_TRY(ctx, ctx->w.reserve(wbytes > 0 ? wbytes : 8));
+    if (mixed) LABFM_CUDA_TRY(ctx, ctx->wtilde.reserve((size_t)ctx->nnz * n_ops * 8 + 8));
     LABFM_CUDA_TRY(ctx, ctx->misc.reserve(4096));
     unsigned long long *dmisc = ctx->misc.as<unsigned long long>();
     // misc layout: [0] bad nodes, [1] bad orders, [2..10] order counts, [11..19] bases, [20..28] cursors
@@ -431,11 +381,48 @@ labfm_status run_build_fp64(labfm_ctx *ctx, const int8_t *order, int uniform_ord
     a.n_bad = dmisc;
     for (int t = 0; t < n_ops * PMAX; t++) a.C[t] = Cin[t];
 
+    MixedArgsPublic m{};
+    if (mixed) {
+        m.xy = a.xy;
+        m.h = a.h;
+        m.row_ptr = a.row_ptr;
+        m.col = a.col;
+        m.periodic = a.periodic;
+        for (int d = 0; d < 2; d++) {
+            m.L[d] = a.L[d];
+            m.halfL[d] = a.halfL[d];
+        }
+        m.rbf = rbf;
+        m.n_ops = n_ops;
+        m.w = a.w;
+        m.wdtype = weight_dtype;
+        m.wt = ctx->wtilde.as<double>();
+        m.node_status = node_status;
+        m.n_bad = dmisc;
+        m.num_sms = ctx->num_sms;
+        for (int t = 0; t < n_ops * PMAX; t++) m.C[t] = Cin[t];
+        for (int d = 0; d < n_ops; d++) {
+            int l = 0;
+            for (int e = 0; e < PMAX; e++)
+                if (Cin[d * PMAX + e] != 0.0) l = std::max(l, (int)elem_degree(e));
+            m.lmax[d] = l;
+        }
+    }
+    auto launch = [&](int k, const int32_t *list, int64_t n_list) -> cudaError_t {
+        if (!mixed) {
+            a.list = list;
+            a.n_list = n_list;
+            return launch_order(k, a, ctx->num_sms, s);
+        }
+        m.list = list;
+        m.n_list = n_list;
+        m.nref = precision_nref(precision, k);
+        return launch_build_mixed(k, m, s);
+    };
+
     unsigned long long *hs = (unsigned long long *)ctx->host_small;
     if (!order) {
-        a.list = nullptr;
-        a.n_list = n;
-        LABFM_CUDA_TRY(ctx, launch_order(uniform_order, a, ctx->num_sms, s));
+        LABFM_CUDA_TRY(ctx, launch(uniform_order, nullptr, n));
     } else {
         int nb = (int)((n + 255) / 256);
         k_order_count<<<nb, 256, 0, s>>>(n, order, dmisc + 2, dmisc + 1);
@@ -458,9 +445,7 @@ labfm_status run_build_fp64(labfm_ctx *ctx, const int8_t *order, int uniform_ord
         LABFM_CUDA_TRY(ctx, cudaGetLastError());
         for (int k = KMAX; k >= 1; k--) {
             if (!cnt[k]) continue;
-            a.list = list + base[k];
-            a.n_list = (int64_t)cnt[k];
-            LABFM_CUDA_TRY(ctx, launch_order(k, a, ctx->num_sms, s));
+            LABFM_CUDA_TRY(ctx, launch(k, list + base[k], (int64_t)cnt[k]));
         }
     }
     LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));

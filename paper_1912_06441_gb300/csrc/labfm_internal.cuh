@@ -60,6 +60,7 @@ struct labfm_ctx {
     int wdtype = LABFM_F64;
     labfm::DevBuf w;
     labfm::DevBuf status_tmp;
+    labfm::DevBuf wtilde;  // scratch of the mixed-precision build: unscaled weights in double
 
     // RK4
     labfm::DevBuf wcomb, rk_acc, rk_stage_a, rk_stage_b;
@@ -82,11 +83,32 @@ labfm_status cuda_fail(labfm_ctx *ctx, cudaError_t e, const char *where);
 cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf &tmp, cudaStream_t s);
 cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, DevBuf &tmp, cudaStream_t s);
 
+// Arguments of the mixed-precision build kernel (see build_mixed.cu).
+struct MixedArgsPublic {
+    int64_t n_list;
+    const int32_t *list;
+    const double *xy, *h;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    int periodic;
+    double L[2], halfL[2];
+    int rbf, n_ops, nref;
+    void *w;
+    int wdtype;
+    double *wt;
+    int32_t *node_status;
+    unsigned long long *n_bad;
+    int lmax[MAX_OPS];
+    double C[MAX_OPS * PMAX];
+    int num_sms;
+};
+cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s);
+
 // Kernel launchers (each returns the launch error).
 labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const double *h, int periodic,
                             const double lo[2], const double hi[2], int64_t *nnz_out);
-labfm_status run_build_fp64(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops,
-                            const double *C, int weight_dtype, int32_t *node_status, int64_t *n_bad_out);
+labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops, const double *C,
+                       int precision, int weight_dtype, int32_t *node_status, int64_t *n_bad_out);
 cudaError_t launch_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int field_dtype, void *out);
 labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int field_dtype, double dt, int64_t nsteps,
                       const uint8_t *frozen);

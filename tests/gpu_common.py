@@ -24,7 +24,7 @@ def c_matrix(k, ops):
     return np.stack([S.op_c_vector(o, k) for o in ops])
 
 
-def gpu_run(ns, k, ops, rbf="wendland_c2", weight_dtype="f64", order=None):
+def gpu_run(ns, k, ops, rbf="wendland_c2", weight_dtype="f64", order=None, precision="fp64", refine=None):
     import torch
 
     from paper_1912_06441_gb300 import Labfm
@@ -37,7 +37,7 @@ def gpu_run(ns, k, ops, rbf="wendland_c2", weight_dtype="f64", order=None):
     status = torch.full((ns.n,), -1, dtype=torch.int32, device=dev)
     od = None if order is None else torch.from_numpy(np.ascontiguousarray(order, dtype=np.int8)).to(dev)
     nbad = L.build_weights(c_matrix(k, ops), order=od, uniform_order=k, rbf=rbf, weight_dtype=weight_dtype,
-                           node_status=status)
+                           node_status=status, precision=precision, refine=refine)
     rp, col = L.get_neighbours()
     w = L.get_weights()
     torch.cuda.synchronize()
