@@ -252,7 +252,7 @@ def mixed_vs_fp64(torch, P, dev, local_rank, nsx, k, ops, field):
     res["speedup_mixed_over_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
     res["ops"] = list(ops)
     res["deriv_err_mixed_vs_fp64"] = deriv_errors(ders["mixed"], ders["fp64"])
-    res["nref"] = 2 if k >= 6 else 1
+    res["nref"] = 1
     L.close()
     return res
 

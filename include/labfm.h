@@ -61,7 +61,7 @@ enum {
     /* X and W in double; M, its partially pivoted LU, Psi and W . Psi in double-float
      * (pairs of FP32, ~48 bits, on the FP32 pipes); then iterative refinement on the
      * polynomial-reproduction residual C - sum_j X_j w_j computed in double (the moment
-     * conditions of Sec. 2.1).  Default: 1 refinement step for k <= 5, 2 for k >= 6. */
+     * conditions of Sec. 2.1).  Default: 1 refinement step. */
     LABFM_PREC_MIXED = 1
 };
 /* LABFM_PREC_MIXED with exactly n refinement steps, n = 0..4 */

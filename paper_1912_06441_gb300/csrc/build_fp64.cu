@@ -346,7 +346,8 @@ static int precision_nref(int precision, int k)
 {
     int forced = (precision >> 8) & 0xf;  // LABFM_PREC_MIXED_REFINE(n) stores n + 1 here
     if (forced) return forced - 1;
-    return k >= 6 ? 2 : 1;
+    (void)k;
+    return 1;  // one step reaches the FP64 floor at every order (measured up to k = 8)
 }
 
 labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops, const double *Cin,
@@ -417,6 +418,14 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         m.list = list;
         m.n_list = n_list;
         m.nref = precision_nref(precision, k);
+        // per-node matrices of one batch: at most 2^18 nodes (4.2 GB at k = 8)
+        m.batch_nodes = std::max<int64_t>(1, std::min<int64_t>(n_list, (int64_t)1 << 18));
+        cudaError_t e = ctx->mscratch.reserve(mixed_scratch_bytes_per_node(k) * (size_t)m.batch_nodes + 256);
+        if (e != cudaSuccess) return e;
+        m.scratch = ctx->mscratch.ptr;
+        e = ctx->mrecs.reserve(mixed_record_bytes() * (size_t)ctx->nnz + 256);
+        if (e != cudaSuccess) return e;
+        m.recs = ctx->mrecs.ptr;
         return launch_build_mixed(k, m, s);
     };
 

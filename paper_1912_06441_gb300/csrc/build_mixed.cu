@@ -1,15 +1,19 @@
 // Mixed-precision weight build.  Same method as build_fp64.cu (Eqs. disc_form, lsys, w_abf),
-// with the arithmetic placed where GB300 has throughput:
-//   - X and W of each neighbour are evaluated in FP64 (X stays in FP64 for the residual);
-//   - M = sum_j X_j (outer) W_j and the partial-pivoting LU of M run in double-float
-//     (pairs of FP32 on the FP32 pipes, ~48 bits), giving Psi~ and w~ = W . Psi~;
-//   - then `nref` steps of iterative refinement on the polynomial-reproduction residual
-//         r = C~ - sum_j X_j w~_j        (computed in FP64; Sec. 2.1: the moments of w must
-//                                         equal the targets C)
-//         w~ <- w~ + W . (LU^-1 r)       (correction solve in double-float).
-// The targets are scaled per operator d by h^(l_d - |alpha|), l_d = highest degree with a
-// non-zero entry of C^d, so that Psi~ stays within float range; the stored weight is
-// w = h^-l_d w~, the same similarity transform as the FP64 build (exact in exact arithmetic).
+// with the arithmetic placed where GB300 has throughput: its FP32 pipes issue ~64x the FP64
+// rate, so the bulk runs in double-float (pairs of FP32, ~48 bits; df64.cuh) and FP64 is kept
+// for the polynomial-reproduction residual.  Three kernels per batch of nodes, handing off
+// through global scratch:
+//   A  k_mixed_assemble (CTA per node): X and W of every neighbour in double-float, then
+//      M = sum_j X_j (outer) W_j in double-float register tiles  -> M (global).
+//   B  k_mixed_invert (64 threads per node, a row per thread in shared memory): Gauss-Jordan
+//      inversion of M with partial pivoting (interchanges undone on the columns) -> M^-1.
+//   C  k_mixed_weights (CTA per node): Psi~ = M^-1 C~, w~ = W . Psi~, then `nref` refinement
+//      steps on the residual of the moment conditions of Sec. 2.1
+//          r = C~ - sum_j X_j w~_j   (FP64)        w~ <- w~ + W . (M^-1 r)
+//      and the physical weights w = h^-l_d w~.
+// Targets are scaled per operator d by h^(l_d - |alpha|), l_d = highest degree with a non-zero
+// entry of C^d, so that Psi~ stays within float range; w = h^-l_d w~ is the same similarity
+// transform as the FP64 build (exact in exact arithmetic).
 #include <cmath>
 
 #include "abf.cuh"
@@ -19,22 +23,54 @@ namespace labfm {
 namespace {
 
 constexpr int MIX_THREADS = 256;
+constexpr int PARTS = 3;            // threads per neighbour in the X/W evaluation
+constexpr int NREC = 8;             // per-neighbour record: q, 1/q, u, v, W0', W0'', W0'''
 
 template <int K> struct MCfg {
     static constexpr int P = p_of_k(K);
     static constexpr int LDX = (P + 3) / 4 * 4;
     static constexpr int NB = K >= 7 ? 72 : 64;
+    static_assert(NB * PARTS <= MIX_THREADS, "one evaluation pass per chunk");
     static constexpr int TM = 2, TN = 4;
     static constexpr int RG = (P + TM - 1) / TM, CG = (P + TN - 1) / TN;
     static_assert(RG * CG <= MIX_THREADS, "assembly tile grid exceeds the CTA");
-    static constexpr int LDA = P + MAX_OPS + 1;
-    // Xd (double) + Xf (df) + Wf (df, first written as double) + Af (df) + residual (double)
-    static constexpr size_t smem_bytes = 8 * ((size_t)3 * NB * LDX + (size_t)P * LDA + (size_t)P * MAX_OPS);
+    // kernel A: Xf, Wf (df) + neighbour records
+    static constexpr size_t smemA = 8 * ((size_t)2 * NB * LDX + (size_t)NB * NREC);
+    // kernel C: Xd (double), Wf (df), M^-1 (df), records, Psi/rhs (df) and residual (double)
+    static constexpr size_t smemC =
+        8 * ((size_t)2 * NB * LDX + (size_t)P * P + (size_t)NB * NREC + (size_t)2 * P * MAX_OPS + (size_t)NB * MAX_OPS);
 };
 
+struct DfTables {
+    df invfact2[KMAX + 1][KMAX + 1];  // 1 / (a! b!) as a double-float
+    float rpoly[PMAX][KMAX + 1];      // the |r|-derivative polynomials (integers, exact in float)
+};
+
+constexpr DfTables make_df_tables()
+{
+    DfTables T{};
+    const RPolyTable R = make_rpoly_table();
+    for (int e = 0; e < PMAX; e++)
+        for (int t = 0; t <= KMAX; t++) T.rpoly[e][t] = static_cast<float>(R.c[e][t]);
+    double f[KMAX + 1] = {1, 1, 2, 6, 24, 120, 720, 5040, 40320};
+    for (int a = 0; a <= KMAX; a++)
+        for (int b = 0; b <= KMAX; b++) {
+            double x = 1.0 / (f[a] * f[b]);
+            float h = static_cast<float>(x);
+            float l = static_cast<float>(x - static_cast<double>(h));
+            T.invfact2[a][b] = df{h, l};
+        }
+    return T;
+}
+
+__constant__ DfTables c_dft = make_df_tables();
+
+struct Rec;
+
 struct MixedArgs {
-    int64_t n_list;
-    const int32_t *list;
+    int64_t n_list;       // nodes in this batch
+    const int32_t *list;  // node ids, or null: node = list index + list_base
+    int64_t list_base;
     const double *xy;
     const double *h;
     const int64_t *row_ptr;
@@ -44,105 +80,241 @@ struct MixedArgs {
     int rbf;
     int n_ops;
     int nref;
-    void *w;        // [nnz][n_ops] output
+    void *w;            // [nnz][n_ops] output
     int wdtype;
-    double *wt;     // [nnz][n_ops] scratch: unscaled weights w~ in double
+    double *wt;         // [nnz][n_ops] scratch: unscaled weights w~ in double
+    df *Mg;             // [n_list][P][P] scratch: M, then M^-1
+    int *flag;          // [n_list] scratch: per-node failure bits
+    Rec *recs;          // [nnz] per-entry preamble (k_mixed_records)
     int32_t *node_status;
     unsigned long long *n_bad;
-    int lmax[MAX_OPS];  // l_d
+    int lmax[MAX_OPS];
     double C[MAX_OPS * PMAX];
 };
 
-template <int K>
-__device__ __forceinline__ void stage_chunk(const MixedArgs &A, int64_t rs, int j0, int nj, double xi, double yi,
-                                            double ihi, double *Xd, df *Xf, df *Wf)
+__device__ __forceinline__ int64_t node_of(const MixedArgs &A, int64_t li)
 {
-    using C = MCfg<K>;
-    constexpr int P = C::P, LDX = C::LDX;
-    for (int t = threadIdx.x; t < nj; t += MIX_THREADS) {
-        int j = A.col[rs + j0 + t];
-        double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
-        if (A.periodic) {
-            if (dx > A.halfL[0]) dx -= A.L[0];
-            else if (dx < -A.halfL[0]) dx += A.L[0];
-            if (dy > A.halfL[1]) dy -= A.L[1];
-            else if (dy < -A.halfL[1]) dy += A.L[1];
+    return A.list ? (int64_t)A.list[li] : A.list_base + li;
+}
+
+// Degrees handled by evaluation part `part` (each part carries a similar (n+1)^2 workload):
+// part 0: 8, 3, 1   part 1: 7, 4, 2   part 2: 6, 5
+__device__ __forceinline__ bool part_has_degree(int part, int n)
+{
+    switch (part) {
+    case 0: return n == 8 || n == 3 || n == 1;
+    case 1: return n == 7 || n == 4 || n == 2;
+    default: return n == 6 || n == 5;
+    }
+}
+
+// X (when Xf != null) and W in double-float for the degrees of `part` of one neighbour, from
+// its record (polar form q, (u, v) as in abf.cuh's eval_xw).
+template <int K>
+__device__ __forceinline__ void eval_xw_part(const df *__restrict__ rec, int part, df *__restrict__ Xf,
+                                             df *__restrict__ Wf)
+{
+    const df q = rec[0], iq = rec[1], u = rec[2], v = rec[3], d1 = rec[4], d2 = rec[5], d3 = rec[6];
+    df up[K + 1], vp[K + 1];
+    up[0] = vp[0] = df{1.0f, 0.0f};
+#pragma unroll
+    for (int t = 1; t <= K; t++) {
+        up[t] = df_mul(up[t - 1], u);
+        vp[t] = df_mul(vp[t - 1], v);
+    }
+    df qn = df{1.0f, 0.0f}, iqn = df{1.0f, 0.0f};
+#pragma unroll
+    for (int n = 1; n <= K; n++) {
+        if (n > 1) {
+            qn = df_mul(qn, q);
+            iqn = df_mul(iqn, iq);
+        } else {
+            qn = q;
         }
-        double *X = Xd + t * LDX;
-        double *Wd = reinterpret_cast<double *>(Wf + t * LDX);
-        eval_xw<K>(dx * ihi, dy * ihi, A.rbf, X, Wd);
-#pragma unroll 4
-        for (int e = 0; e < LDX; e++) {
-            double xv = e < P ? X[e] : 0.0;
-            double wv = e < P ? Wd[e] : 0.0;
-            if (e >= P) X[e] = 0.0;
-            Xf[t * LDX + e] = df_from_double(xv);
-            Wf[t * LDX + e] = df_from_double(wv);  // in place: same 8 bytes
+        if (!part_has_degree(part, n)) continue;
+        df mono[K + 1];
+#pragma unroll
+        for (int t = 0; t <= n; t++) mono[t] = df_mul(up[t], vp[n - t]);
+        // second derivatives of |r| for the chain rule of the degree-3 elements
+        df rxx = df{0.0f, 0.0f}, rxy = rxx, ryy = rxx;
+        if (n == 3) {
+            rxx = df_mul(vp[2], iq);
+            rxy = df_neg(df_mul(df_mul(u, v), iq));
+            ryy = df_mul(up[2], iq);
+        }
+#pragma unroll
+        for (int a = n; a >= 0; a--) {
+            const int b = n - a;
+            const int e = p_of_k(n - 1) + b;
+            if (Xf) Xf[e] = df_mul(df_mul(qn, mono[a]), c_dft.invfact2[a][b]);
+            df s = df{0.0f, 0.0f};
+#pragma unroll
+            for (int t = 0; t <= n; t++) {
+                const float c = c_dft.rpoly[e][t];
+                if (c != 0.0f) s = df_fma(df{c, 0.0f}, mono[t], s);
+            }
+            const df dr = df_mul(s, iqn);
+            df wv = df_mul(d1, dr);
+            // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
+            if (n == 2) {
+                wv = df_fma(d2, a == 2 ? up[2] : (a == 1 ? df_mul(u, v) : vp[2]), wv);
+            } else if (n == 3) {
+                if (a == 3) wv = df_fma(d3, up[3], df_fma(d2, df_mul(df{3.0f, 0.0f}, df_mul(u, rxx)), wv));
+                if (a == 2)
+                    wv = df_fma(d3, df_mul(up[2], v),
+                                df_fma(d2, df_add(df_mul(v, rxx), df_mul(df{2.0f, 0.0f}, df_mul(u, rxy))), wv));
+                if (a == 1)
+                    wv = df_fma(d3, df_mul(u, vp[2]),
+                                df_fma(d2, df_add(df_mul(u, ryy), df_mul(df{2.0f, 0.0f}, df_mul(v, rxy))), wv));
+                if (a == 0) wv = df_fma(d3, vp[3], df_fma(d2, df_mul(df{3.0f, 0.0f}, df_mul(v, ryy)), wv));
+            }
+            Wf[e] = wv;
         }
     }
 }
 
+// FP64 preamble of one stencil entry, converted once to double-float (kernel k_mixed_records):
+// the scaled offset (x, y) in double, and q, 1/q, u, v and the first three radial derivatives
+// of W0 in double-float.
+struct Rec {
+    double x, y;
+    df v[7];
+};
+static_assert(sizeof(Rec) == 72, "record layout");
+
+// One warp per node: every stencil entry's preamble (the only FP64 work of the X/W evaluation).
+__global__ void __launch_bounds__(256) k_mixed_records(MixedArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    Rec *recs = A.recs;
+    for (int64_t li = wg; li < A.n_list; li += nw) {
+        const int64_t i = A.list ? (int64_t)A.list[li] : A.list_base + li;
+        const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
+        const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1];
+        const double ihi = 1.0 / A.h[i];
+        for (int64_t e = rs + lane; e < re; e += 32) {
+            const int j = A.col[e];
+            double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
+            if (A.periodic) {
+                if (dx > A.halfL[0]) dx -= A.L[0];
+                else if (dx < -A.halfL[0]) dx += A.L[0];
+                if (dy > A.halfL[1]) dy -= A.L[1];
+                else if (dy < -A.halfL[1]) dy += A.L[1];
+            }
+            const double x = dx * ihi, y = dy * ihi;
+            const double qd = sqrt(x * x + y * y);
+            const double iqd = 1.0 / qd;
+            double d1, d2, d3;
+            rbf_derivs(A.rbf, qd, d1, d2, d3);
+            Rec r;
+            r.x = x;
+            r.y = y;
+            r.v[0] = df_from_double(qd);
+            r.v[1] = df_from_double(iqd);
+            r.v[2] = df_from_double(x * iqd);
+            r.v[3] = df_from_double(y * iqd);
+            r.v[4] = df_from_double(d1);
+            r.v[5] = df_from_double(d2);
+            r.v[6] = df_from_double(d3);
+            recs[e] = r;
+        }
+    }
+}
+
+// Stage neighbours j0 .. j0+nj-1 of node i from their records: X in FP64 (when Xd != null, one
+// thread per neighbour), then X (when Xf != null) and W in double-float (PARTS threads per
+// neighbour, a warp on one part).  Ends synchronised.
 template <int K>
-__global__ void __launch_bounds__(MIX_THREADS, 2) k_build_mixed(MixedArgs A)
+__device__ __forceinline__ void stage_chunk(const MixedArgs &A, int64_t rs, int j0, int nj, double *Xd, df *Xf,
+                                            df *Wf, df *Nrec)
 {
     using C = MCfg<K>;
-    constexpr int P = C::P, LDX = C::LDX, NB = C::NB, LDA = C::LDA, TM = C::TM, TN = C::TN;
-    extern __shared__ __align__(16) double smem_d[];
-    double *Xd = smem_d;                                          // [NB][LDX]
-    df *Xf = reinterpret_cast<df *>(Xd + NB * LDX);               // [NB][LDX]
-    df *Wf = Xf + NB * LDX;                                       // [NB][LDX]
-    df *Af = Wf + NB * LDX;                                       // [P][LDA]
-    double *Rd = reinterpret_cast<double *>(Af + P * LDA);        // [P][MAX_OPS] residual
-    __shared__ int s_pivrow[P];
-    __shared__ df s_invp[P];
-    __shared__ double s_hneg[KMAX + 1], s_hpos[KMAX + 1];
-    __shared__ int s_flag;
+    constexpr int P = C::P, LDX = C::LDX;
+    static_assert(LDX - P >= 0, "padding");
+    // records -> shared memory (coalesced: an entry's 72 bytes as nine 8-byte words)
+    const double *src = reinterpret_cast<const double *>(A.recs + rs + j0);
+    for (int t = threadIdx.x; t < nj * 9; t += MIX_THREADS) {
+        const int jj = t / 9, w = t - jj * 9;
+        if (w >= 2) reinterpret_cast<double *>(Nrec + jj * NREC)[w - 2] = src[t];
+    }
+    __syncthreads();
+    if (Xd) {
+        for (int t = threadIdx.x; t < nj; t += MIX_THREADS) {
+            const double x = src[t * 9], y = src[t * 9 + 1];
+            double xp[K + 1], yp[K + 1];
+            xp[0] = yp[0] = 1.0;
+#pragma unroll
+            for (int q = 1; q <= K; q++) {
+                xp[q] = xp[q - 1] * x;
+                yp[q] = yp[q - 1] * y;
+            }
+            double *X = Xd + t * LDX;
+#pragma unroll
+            for (int e = 0; e < P; e++) {
+                const int a = elem_a(e), b = elem_degree(e) - a;
+                X[e] = xp[a] * yp[b] * (c_invfact[a] * c_invfact[b]);
+            }
+#pragma unroll
+            for (int e = P; e < LDX; e++) X[e] = 0.0;
+        }
+    }
+    for (int t = threadIdx.x; t < nj * PARTS; t += MIX_THREADS) {
+        const int part = t / nj, jj = t - part * nj;
+        eval_xw_part<K>(Nrec + jj * NREC, part, Xf ? Xf + jj * LDX : nullptr, Wf + jj * LDX);
+    }
+    // the padding columns the tiles read
+    for (int t = threadIdx.x; t < nj * (LDX - P); t += MIX_THREADS) {
+        const int jj = t / (LDX - P), e = P + t % (LDX - P);
+        if (Xf) Xf[jj * LDX + e] = df{0.0f, 0.0f};
+        Wf[jj * LDX + e] = df{0.0f, 0.0f};
+    }
+    __syncthreads();
+}
 
-    const int tid = threadIdx.x;
+__device__ __forceinline__ void mark_undersampled(const MixedArgs &A, int64_t li, int64_t i, int64_t rs, int ni)
+{
     const int n_ops = A.n_ops;
-    const int W_ = P + n_ops;
+    for (int64_t t = threadIdx.x; t < (int64_t)ni * n_ops; t += blockDim.x) {
+        if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
+        else ((float *)A.w)[rs * n_ops + t] = 0.0f;
+    }
+    if (threadIdx.x == 0) A.flag[li] = 8;
+}
+
+// ------------------------------------------------------------------------------------------
+// A: X, W and M in double-float
+// ------------------------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_assemble(MixedArgs A)
+{
+    using C = MCfg<K>;
+    constexpr int P = C::P, LDX = C::LDX, NB = C::NB, TM = C::TM, TN = C::TN;
+    extern __shared__ __align__(16) double smem_d[];
+    df *Xf = reinterpret_cast<df *>(smem_d);  // [NB][LDX]
+    df *Wf = Xf + NB * LDX;                   // [NB][LDX]
+    df *Nrec = Wf + NB * LDX;                 // [NB][NREC]
+    const int tid = threadIdx.x;
     const int rg = tid / C::CG, cg = tid % C::CG;
     const bool tile_active = tid < C::RG * C::CG;
 
     for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
-        const int64_t i = A.list ? (int64_t)A.list[li] : li;
+        const int64_t i = node_of(A, li);
         const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
         const int ni = (int)(re - rs);
         if (ni < P) {
-            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
-                if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
-                else ((float *)A.w)[rs * n_ops + t] = 0.0f;
-            }
-            if (tid == 0) {
-                if (A.node_status) A.node_status[i] = LABFM_NODE_UNDERSAMPLED;
-                atomicAdd(A.n_bad, 1ull);
-            }
+            mark_undersampled(A, li, i, rs, ni);
             continue;
         }
-        const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], hi = A.h[i];
-        const double ihi = 1.0 / hi;
-        if (tid == 0) {
-            double s = 1.0, t = 1.0;
-            for (int q = 0; q <= KMAX; q++) {
-                s_hneg[q] = s;
-                s_hpos[q] = t;
-                s *= ihi;
-                t *= hi;
-            }
-            s_flag = 0;
-        }
-
-        // ---- assembly of M in double-float, 2 x 4 register tiles ----
         df acc[TM][TN];
 #pragma unroll
         for (int a = 0; a < TM; a++)
 #pragma unroll
             for (int b = 0; b < TN; b++) acc[a][b] = df{0.0f, 0.0f};
-        const int nchunks = (ni + NB - 1) / NB;
-        for (int ch = 0; ch < nchunks; ch++) {
-            const int j0 = ch * NB, nj = min(NB, ni - j0);
-            stage_chunk<K>(A, rs, j0, nj, xi, yi, ihi, Xd, Xf, Wf);
-            __syncthreads();
+        for (int j0 = 0; j0 < ni; j0 += NB) {
+            const int nj = min(NB, ni - j0);
+            stage_chunk<K>(A, rs, j0, nj, nullptr, Xf, Wf, Nrec);
             if (tile_active) {
                 for (int j = 0; j < nj; j++) {
                     const df *X = Xf + j * LDX + rg * TM;
@@ -164,7 +336,11 @@ __global__ void __launch_bounds__(MIX_THREADS, 2) k_build_mixed(MixedArgs A)
             }
             __syncthreads();
         }
+        __shared__ int s_bad;
+        if (tid == 0) s_bad = 0;
+        __syncthreads();
         if (tile_active) {
+            df *Mg = A.Mg + li * (int64_t)P * P;
             bool finite = true;
 #pragma unroll
             for (int a = 0; a < TM; a++)
@@ -172,171 +348,278 @@ __global__ void __launch_bounds__(MIX_THREADS, 2) k_build_mixed(MixedArgs A)
                 for (int b = 0; b < TN; b++) {
                     int m = rg * TM + a, c = cg * TN + b;
                     if (m < P && c < P) {
-                        Af[m * LDA + c] = acc[a][b];
+                        Mg[m * P + c] = acc[a][b];
                         finite &= df_isfinite(acc[a][b]);
                     }
                 }
-            if (!finite) atomicOr(&s_flag, 4);
+            if (!finite) s_bad = 4;  // a neighbour on top of node i: singular ABFs
         }
+        __syncthreads();
+        if (tid == 0) A.flag[li] = s_bad;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// B: Gauss-Jordan inversion with partial pivoting; one CTA of 64 threads per node, thread t
+// updates row t of the working matrix in shared memory.  Per pivot column c:
+//   1. argmax of |M[r][c]| over r >= c (warp shuffles, then the two warps through shared memory);
+//   2. rows c and argmax are exchanged (threads over columns);
+//   3. every row r != c: f = M[r][c] / p, M[r][q] -= f M[c][q] (q != c), M[r][c] = -f;
+//      row c: M[c][q] /= p (q != c), M[c][c] = 1 / p.
+// The column loop is unrolled (compile-time offsets, so loads are issued ahead of the
+// dependent stores); the pivot loop is not, which keeps the code small.  The row interchanges
+// are undone on the columns when the result is written out.
+// ------------------------------------------------------------------------------------------
+constexpr int INV_THREADS = 64;
+
+template <int K>
+__global__ void __launch_bounds__(INV_THREADS) k_mixed_invert(MixedArgs A)
+{
+    using C = MCfg<K>;
+    constexpr int P = C::P;
+    constexpr int LDM = P + 1;  // row stride (df) of the working matrix
+    static_assert(P <= INV_THREADS, "one row per thread");
+    __shared__ df s_m[P * LDM];
+    __shared__ df s_prow[P];
+    __shared__ float s_best[2];
+    __shared__ int s_br[2];
+    __shared__ int s_src[P];
+    __shared__ signed char s_piv[P];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const bool own = t < P;
+
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
+        if (A.flag[li] != 0) continue;  // uniform per CTA
+        const df *Mg = A.Mg + li * (int64_t)P * P;
+        for (int u = t; u < P * P; u += INV_THREADS) {
+            const int r = u / P;
+            s_m[r * LDM + (u - r * P)] = Mg[u];
+        }
+        __syncthreads();
+        bool zero = false;
+        for (int c = 0; c < P; c++) {
+            float best = (own && t >= c) ? fabsf(s_m[t * LDM + c].hi) : -1.0f;
+            int br = t;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ob > best || (ob == best && orr < br)) {
+                    best = ob;
+                    br = orr;
+                }
+            }
+            if (lane == 0) {
+                s_best[warp] = best;
+                s_br[warp] = br;
+            }
+            __syncthreads();
+            if (s_best[1] > s_best[0]) {
+                best = s_best[1];
+                br = s_br[1];
+            } else {
+                best = s_best[0];
+                br = s_br[0];
+            }
+            if (!(best > 0.0f) || !isfinite(best)) {
+                zero = true;
+                break;
+            }
+            if (t == 0) s_piv[c] = (signed char)br;
+            // exchange rows c and br, and publish the pivot row
+            if (t < P) {
+                const df a = s_m[c * LDM + t], b = s_m[br * LDM + t];
+                s_prow[t] = b;
+                if (br != c) {
+                    s_m[c * LDM + t] = b;
+                    s_m[br * LDM + t] = a;
+                }
+            }
+            __syncthreads();
+            const df inv = df_recip(s_prow[c]);
+            if (own) {
+                df *row = s_m + t * LDM;
+                if (t == c) {
+#pragma unroll
+                    for (int q = 0; q < P; q++) row[q] = df_mul(row[q], inv);
+                    row[c] = inv;
+                } else {
+                    const df f = df_mul(row[c], inv);
+#pragma unroll
+                    for (int q = 0; q < P; q++) row[q] = df_fms(f, s_prow[q], row[q]);
+                    row[c] = df_neg(f);
+                }
+            }
+            __syncthreads();
+        }
+        if (zero) {
+            if (t == 0) A.flag[li] = 1;
+            __syncthreads();
+            continue;
+        }
+        // column order of the result: undo the interchanges, last first
+        if (t == 0) {
+            for (int q = 0; q < P; q++) s_src[q] = q;
+            for (int c = P - 1; c >= 0; c--) {
+                const int pr = s_piv[c];
+                const int a = s_src[c];
+                s_src[c] = s_src[pr];
+                s_src[pr] = a;
+            }
+        }
+        __syncthreads();
+        df *Mo = A.Mg + li * (int64_t)P * P;
+        for (int u = t; u < P * P; u += INV_THREADS) {
+            const int r = u / P, q = u - r * P;
+            Mo[u] = s_m[r * LDM + s_src[q]];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// C: Psi~ = M^-1 C~, w~ = W . Psi~, FP64 residual refinement, physical weights
+// ------------------------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(MIX_THREADS, 2) k_mixed_weights(MixedArgs A)
+{
+    using C = MCfg<K>;
+    constexpr int P = C::P, LDX = C::LDX, NB = C::NB;
+    extern __shared__ __align__(16) double smem_d[];
+    double *Xd = smem_d;                                     // [NB][LDX]
+    df *Wf = reinterpret_cast<df *>(Xd + NB * LDX);          // [NB][LDX]
+    df *Mi = Wf + NB * LDX;                                  // [P][P] M^-1
+    df *Nrec = Mi + P * P;                                   // [NB][NREC]
+    df *Rhs = Nrec + NB * NREC;                              // [P][MAX_OPS] right-hand sides
+    df *Psi = Rhs + P * MAX_OPS;                             // [P][MAX_OPS]
+    double *Wt = reinterpret_cast<double *>(Psi + P * MAX_OPS);  // [NB][MAX_OPS] w~ of the chunk
+    __shared__ double s_hneg[KMAX + 1], s_hpos[KMAX + 1];
+    __shared__ double s_res[PMAX * MAX_OPS];
+    __shared__ int s_flag;
+    const int tid = threadIdx.x;
+    const int n_ops = A.n_ops;
+
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
+        const int64_t i = node_of(A, li);
+        const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
+        const int ni = (int)(re - rs);
+        const int fl = A.flag[li];
+        if (fl & 8) {  // undersampled: weights already zeroed by kernel A
+            if (tid == 0) {
+                if (A.node_status) A.node_status[i] = LABFM_NODE_UNDERSAMPLED;
+                atomicAdd(A.n_bad, 1ull);
+            }
+            continue;
+        }
+        if (fl != 0) {
+            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
+                if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
+                else ((float *)A.w)[rs * n_ops + t] = 0.0f;
+            }
+            if (tid == 0) {
+                if (A.node_status) A.node_status[i] = (fl & 4) ? LABFM_NODE_NONFINITE : LABFM_NODE_SINGULAR;
+                atomicAdd(A.n_bad, 1ull);
+            }
+            continue;
+        }
+        const double hi = A.h[i];
+        const double ihi = 1.0 / hi;
+        if (tid == 0) {
+            double s = 1.0, t = 1.0;
+            for (int q = 0; q <= KMAX; q++) {
+                s_hneg[q] = s;
+                s_hpos[q] = t;
+                s *= ihi;
+                t *= hi;
+            }
+            s_flag = 0;
+        }
+        const df *Mg = A.Mg + li * (int64_t)P * P;
+        for (int t = tid; t < P * P; t += MIX_THREADS) Mi[t] = Mg[t];
+        __syncthreads();
         // scaled targets C~_alpha = C_alpha h^(l_d - |alpha|)
         for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
             int m = t / n_ops, d = t % n_ops;
-            int deg = elem_degree(m);
-            int l = A.lmax[d];
+            int deg = elem_degree(m), l = A.lmax[d];
             double sc = l >= deg ? s_hpos[l - deg] : s_hneg[deg - l];
-            Af[m * LDA + P + d] = df_from_double(A.C[d * PMAX + m] * sc);
+            s_res[m * MAX_OPS + d] = A.C[d * PMAX + m] * sc;
+            Rhs[m * MAX_OPS + d] = df_from_double(s_res[m * MAX_OPS + d]);
         }
-        __syncthreads();
-        const bool bad_m = (s_flag & 4) != 0;
+        const int nchunks = (ni + NB - 1) / NB;
+        if (nchunks == 1) stage_chunk<K>(A, rs, 0, ni, Xd, nullptr, Wf, Nrec);
+        else __syncthreads();
 
-        // ---- LU with partial pivoting (whole-row swaps, so the factors can be reused) ----
-        for (int c = 0; c < P && !bad_m; c++) {
-            if (tid < 32) {
-                float best = -1.0f;
-                int br = c;
-                for (int r = c + tid; r < P; r += 32) {
-                    float v = df_abs_hi(Af[r * LDA + c]);
-                    if (v > best) {
-                        best = v;
-                        br = r;
-                    }
+        for (int it = 0; it <= A.nref; it++) {
+            // Psi (or its correction) = M^-1 Rhs, thread per (m, d)
+            for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
+                int m = t / n_ops, d = t % n_ops;
+                df s0 = df{0.0f, 0.0f}, s1 = s0;
+                const df *row = Mi + m * P;
+                int q = 0;
+                for (; q + 1 < P; q += 2) {
+                    s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
+                    s1 = df_fma(row[q + 1], Rhs[(q + 1) * MAX_OPS + d], s1);
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                    if (ob > best || (ob == best && orr < br)) {
-                        best = ob;
-                        br = orr;
-                    }
-                }
-                if (tid == 0) {
-                    s_pivrow[c] = br;
-                    df pv = Af[br * LDA + c];
-                    if (!(best > 0.0f) || !isfinite(best)) {
-                        s_flag |= 1;
-                        s_invp[c] = df{0.0f, 0.0f};
-                    } else {
-                        s_invp[c] = df_recip(pv);
-                    }
-                }
+                if (q < P) s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
+                Psi[m * MAX_OPS + d] = df_add(s0, s1);
             }
             __syncthreads();
-            const int pr = s_pivrow[c];
-            if (pr != c) {
-                for (int t = tid; t < W_; t += MIX_THREADS) {
-                    df a = Af[c * LDA + t];
-                    Af[c * LDA + t] = Af[pr * LDA + t];
-                    Af[pr * LDA + t] = a;
-                }
-                __syncthreads();
+            // w~ (+)= W . Psi over the chunks; the residual r = C~ - sum_j X_j w~_j accumulates
+            for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
+                int m = t / n_ops, d = t % n_ops;
+                int deg = elem_degree(m), l = A.lmax[d];
+                double sc = l >= deg ? s_hpos[l - deg] : s_hneg[deg - l];
+                s_res[m * MAX_OPS + d] = A.C[d * PMAX + m] * sc;
             }
-            const df inv = s_invp[c];
-            for (int r = c + 1 + tid; r < P; r += MIX_THREADS) Af[r * LDA + c] = df_mul(Af[r * LDA + c], inv);
-            __syncthreads();
-            const int nr = P - c - 1, nc = W_ - c - 1;
-            for (int t = tid; t < nr * nc; t += MIX_THREADS) {
-                int r = c + 1 + t / nc, q = c + 1 + t % nc;
-                Af[r * LDA + q] = df_fms(Af[r * LDA + c], Af[c * LDA + q], Af[r * LDA + q]);
-            }
-            __syncthreads();
-        }
-        // back substitution: Psi~ in columns P..P+n_ops
-        for (int c = P - 1; c >= 0 && !bad_m; c--) {
-            if (tid < n_ops) Af[c * LDA + P + tid] = df_mul(Af[c * LDA + P + tid], s_invp[c]);
-            __syncthreads();
-            for (int t = tid; t < c * n_ops; t += MIX_THREADS) {
-                int r = t / n_ops, d = t % n_ops;
-                Af[r * LDA + P + d] = df_fms(Af[r * LDA + c], Af[c * LDA + P + d], Af[r * LDA + P + d]);
-            }
-            __syncthreads();
-        }
-        const bool failed = (s_flag & 5) != 0;
-
-        // ---- w~ = W . Psi~ (double-float), then refinement steps ----
-        for (int it = 0; it <= A.nref && !failed; it++) {
-            // (it == 0: Psi~ in the RHS columns;  it > 0: correction dPsi in the RHS columns)
             for (int ch = 0; ch < nchunks; ch++) {
                 const int j0 = ch * NB, nj = min(NB, ni - j0);
-                if (nchunks > 1) {
-                    stage_chunk<K>(A, rs, j0, nj, xi, yi, ihi, Xd, Xf, Wf);
-                    __syncthreads();
-                }
+                if (nchunks > 1) stage_chunk<K>(A, rs, j0, nj, Xd, nullptr, Wf, Nrec);
                 for (int t = tid; t < nj * n_ops; t += MIX_THREADS) {
                     int j = t / n_ops, d = t % n_ops;
-                    df s = df{0.0f, 0.0f};
+                    df s0 = df{0.0f, 0.0f}, s1 = s0;
                     const df *W = Wf + j * LDX;
-#pragma unroll 4
-                    for (int m = 0; m < P; m++) s = df_fma(W[m], Af[m * LDA + P + d], s);
-                    int64_t idx = (rs + j0 + j) * n_ops + d;
-                    double v = df_to_double(s);
-                    A.wt[idx] = it == 0 ? v : A.wt[idx] + v;
+                    int m = 0;
+                    for (; m + 1 < P; m += 2) {
+                        s0 = df_fma(W[m], Psi[m * MAX_OPS + d], s0);
+                        s1 = df_fma(W[m + 1], Psi[(m + 1) * MAX_OPS + d], s1);
+                    }
+                    if (m < P) s0 = df_fma(W[m], Psi[m * MAX_OPS + d], s0);
+                    const double v = df_to_double(df_add(s0, s1));
+                    const int64_t idx = (rs + j0 + j) * n_ops + d;
+                    const double wv = it == 0 ? v : A.wt[idx] + v;
+                    A.wt[idx] = wv;
+                    Wt[j * MAX_OPS + d] = wv;
+                }
+                __syncthreads();
+                if (it < A.nref) {
+                    for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
+                        int m = t / n_ops, d = t % n_ops;
+                        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                        int j = 0;
+                        for (; j + 3 < nj; j += 4) {
+                            s0 = fma(Xd[j * LDX + m], Wt[j * MAX_OPS + d], s0);
+                            s1 = fma(Xd[(j + 1) * LDX + m], Wt[(j + 1) * MAX_OPS + d], s1);
+                            s2 = fma(Xd[(j + 2) * LDX + m], Wt[(j + 2) * MAX_OPS + d], s2);
+                            s3 = fma(Xd[(j + 3) * LDX + m], Wt[(j + 3) * MAX_OPS + d], s3);
+                        }
+                        for (; j < nj; j++) s0 = fma(Xd[j * LDX + m], Wt[j * MAX_OPS + d], s0);
+                        s_res[m * MAX_OPS + d] -= (s0 + s1) + (s2 + s3);
+                    }
                 }
                 __syncthreads();
             }
             if (it == A.nref) break;
-            // residual r = C~ - sum_j X_j w~_j in FP64 (thread per (alpha, d))
             for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
                 int m = t / n_ops, d = t % n_ops;
-                int deg = elem_degree(m);
-                int l = A.lmax[d];
-                double sc = l >= deg ? s_hpos[l - deg] : s_hneg[deg - l];
-                Rd[m * MAX_OPS + d] = A.C[d * PMAX + m] * sc;
-            }
-            for (int ch = 0; ch < nchunks; ch++) {
-                const int j0 = ch * NB, nj = min(NB, ni - j0);
-                if (nchunks > 1) {
-                    __syncthreads();
-                    stage_chunk<K>(A, rs, j0, nj, xi, yi, ihi, Xd, Xf, Wf);
-                }
-                __syncthreads();
-                for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
-                    int m = t / n_ops, d = t % n_ops;
-                    double s = Rd[m * MAX_OPS + d];
-                    for (int j = 0; j < nj; j++) s = fma(-Xd[j * LDX + m], A.wt[(rs + j0 + j) * n_ops + d], s);
-                    Rd[m * MAX_OPS + d] = s;
-                }
+                Rhs[m * MAX_OPS + d] = df_from_double(s_res[m * MAX_OPS + d]);
             }
             __syncthreads();
-            // correction solve with the stored factors: row swaps, unit-lower L, then U
-            for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
-                int m = t / n_ops, d = t % n_ops;
-                Af[m * LDA + P + d] = df_from_double(Rd[m * MAX_OPS + d]);
-            }
-            __syncthreads();
-            if (tid < n_ops) {
-                for (int c = 0; c < P; c++) {
-                    int pr = s_pivrow[c];
-                    if (pr != c) {
-                        df a = Af[c * LDA + P + tid];
-                        Af[c * LDA + P + tid] = Af[pr * LDA + P + tid];
-                        Af[pr * LDA + P + tid] = a;
-                    }
-                }
-            }
-            __syncthreads();
-            for (int c = 0; c < P - 1; c++) {
-                for (int t = tid; t < (P - c - 1) * n_ops; t += MIX_THREADS) {
-                    int r = c + 1 + t / n_ops, d = t % n_ops;
-                    Af[r * LDA + P + d] = df_fms(Af[r * LDA + c], Af[c * LDA + P + d], Af[r * LDA + P + d]);
-                }
-                __syncthreads();
-            }
-            for (int c = P - 1; c >= 0; c--) {
-                if (tid < n_ops) Af[c * LDA + P + tid] = df_mul(Af[c * LDA + P + tid], s_invp[c]);
-                __syncthreads();
-                for (int t = tid; t < c * n_ops; t += MIX_THREADS) {
-                    int r = t / n_ops, d = t % n_ops;
-                    Af[r * LDA + P + d] = df_fms(Af[r * LDA + c], Af[c * LDA + P + d], Af[r * LDA + P + d]);
-                }
-                __syncthreads();
-            }
         }
 
-        // ---- physical weights w = h^-l_d w~ ----
+        // physical weights w = h^-l_d w~
         for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
             int d = (int)(t % n_ops);
-            double v = failed ? 0.0 : A.wt[rs * n_ops + t] * s_hneg[A.lmax[d]];
+            double v = A.wt[rs * n_ops + t] * s_hneg[A.lmax[d]];
             if (!isfinite(v)) {
                 atomicOr(&s_flag, 2);
                 v = 0.0;
@@ -345,18 +628,14 @@ __global__ void __launch_bounds__(MIX_THREADS, 2) k_build_mixed(MixedArgs A)
             else ((float *)A.w)[rs * n_ops + t] = (float)v;
         }
         __syncthreads();
-        const int flag = s_flag;
-        if ((flag & 2) && !failed) {
+        if (s_flag & 2) {
             for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
                 if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
                 else ((float *)A.w)[rs * n_ops + t] = 0.0f;
             }
         }
         if (tid == 0) {
-            int st = (flag & 4)   ? LABFM_NODE_NONFINITE
-                     : (flag & 1) ? LABFM_NODE_SINGULAR
-                     : (flag & 2) ? LABFM_NODE_NONFINITE
-                                  : LABFM_NODE_OK;
+            const int st = (s_flag & 2) ? LABFM_NODE_NONFINITE : LABFM_NODE_OK;
             if (A.node_status) A.node_status[i] = st;
             if (st != LABFM_NODE_OK) atomicAdd(A.n_bad, 1ull);
         }
@@ -364,30 +643,52 @@ __global__ void __launch_bounds__(MIX_THREADS, 2) k_build_mixed(MixedArgs A)
     }
 }
 
+template <class KernelT>
+cudaError_t launch_persistent(KernelT kern, const MixedArgs &a, int threads, size_t smem, int64_t units, int num_sms,
+                              cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = std::min<int64_t>(units, (int64_t)num_sms * per_sm);
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, cudaStream_t s)
 {
     using C = MCfg<K>;
-    cudaError_t e = cudaFuncSetAttribute(k_build_mixed<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::smem_bytes);
+    {
+        int64_t blocks = std::min<int64_t>((a.n_list + 7) / 8, (int64_t)num_sms * 16);
+        if (blocks > 0) k_mixed_records<<<(unsigned)blocks, 256, 0, s>>>(a);
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
+    cudaError_t e = launch_persistent(k_mixed_assemble<K>, a, MIX_THREADS, C::smemA, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_mixed<K>, MIX_THREADS, C::smem_bytes);
+    e = launch_persistent(k_mixed_invert<K>, a, INV_THREADS, 0, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = std::min<int64_t>(a.n_list, (int64_t)num_sms * per_sm);
-    if (grid < 1) return cudaSuccess;
-    k_build_mixed<K><<<(unsigned)grid, MIX_THREADS, C::smem_bytes, s>>>(a);
-    return cudaGetLastError();
+    return launch_persistent(k_mixed_weights<K>, a, MIX_THREADS, C::smemC, a.n_list, num_sms, s);
 }
 
 }  // namespace
 
+size_t mixed_record_bytes() { return sizeof(Rec); }
+
+size_t mixed_scratch_bytes_per_node(int k)
+{
+    const int p = p_of_k(k);
+    return sizeof(df) * (size_t)p * p + sizeof(int);
+}
+
 cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
 {
     MixedArgs a{};
-    a.n_list = p.n_list;
-    a.list = p.list;
     a.xy = p.xy;
     a.h = p.h;
     a.row_ptr = p.row_ptr;
@@ -405,18 +706,32 @@ cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
     a.wt = p.wt;
     a.node_status = p.node_status;
     a.n_bad = p.n_bad;
+    a.recs = reinterpret_cast<Rec *>(p.recs);
     for (int d = 0; d < MAX_OPS; d++) a.lmax[d] = p.lmax[d];
     for (int t = 0; t < MAX_OPS * PMAX; t++) a.C[t] = p.C[t];
-    switch (k) {
-    case 1: return launch_mixed_k<1>(a, p.num_sms, s);
-    case 2: return launch_mixed_k<2>(a, p.num_sms, s);
-    case 3: return launch_mixed_k<3>(a, p.num_sms, s);
-    case 4: return launch_mixed_k<4>(a, p.num_sms, s);
-    case 5: return launch_mixed_k<5>(a, p.num_sms, s);
-    case 6: return launch_mixed_k<6>(a, p.num_sms, s);
-    case 7: return launch_mixed_k<7>(a, p.num_sms, s);
-    default: return launch_mixed_k<8>(a, p.num_sms, s);
+    const int pk = p_of_k(k);
+    // scratch holds batch_nodes matrices; the node list is processed batch by batch
+    const int64_t batch = p.batch_nodes;
+    for (int64_t b0 = 0; b0 < p.n_list; b0 += batch) {
+        a.n_list = std::min<int64_t>(batch, p.n_list - b0);
+        a.list = p.list ? p.list + b0 : nullptr;
+        a.list_base = p.list ? 0 : b0;
+        a.Mg = reinterpret_cast<df *>(p.scratch);
+        a.flag = reinterpret_cast<int *>(reinterpret_cast<char *>(p.scratch) + sizeof(df) * (size_t)pk * pk * batch);
+        cudaError_t e;
+        switch (k) {
+        case 1: e = launch_mixed_k<1>(a, p.num_sms, s); break;
+        case 2: e = launch_mixed_k<2>(a, p.num_sms, s); break;
+        case 3: e = launch_mixed_k<3>(a, p.num_sms, s); break;
+        case 4: e = launch_mixed_k<4>(a, p.num_sms, s); break;
+        case 5: e = launch_mixed_k<5>(a, p.num_sms, s); break;
+        case 6: e = launch_mixed_k<6>(a, p.num_sms, s); break;
+        case 7: e = launch_mixed_k<7>(a, p.num_sms, s); break;
+        default: e = launch_mixed_k<8>(a, p.num_sms, s); break;
+        }
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 }  // namespace labfm

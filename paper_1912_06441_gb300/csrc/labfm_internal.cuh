@@ -61,6 +61,8 @@ struct labfm_ctx {
     labfm::DevBuf w;
     labfm::DevBuf status_tmp;
     labfm::DevBuf wtilde;  // scratch of the mixed-precision build: unscaled weights in double
+    labfm::DevBuf mscratch;  // scratch of the mixed-precision build: per-node matrices of one batch
+    labfm::DevBuf mrecs;     // scratch of the mixed-precision build: per-entry preamble records
 
     // RK4
     labfm::DevBuf wcomb, rk_acc, rk_stage_a, rk_stage_b;
@@ -101,8 +103,13 @@ struct MixedArgsPublic {
     int lmax[MAX_OPS];
     double C[MAX_OPS * PMAX];
     int num_sms;
+    int64_t batch_nodes;  // nodes per batch; `scratch` holds batch_nodes * mixed_scratch_bytes_per_node(k)
+    void *scratch;
+    void *recs;  // [nnz] per-entry records, mixed_record_bytes() each
 };
 cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s);
+size_t mixed_scratch_bytes_per_node(int k);
+size_t mixed_record_bytes();
 
 // Kernel launchers (each returns the launch error).
 labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const double *h, int periodic,
