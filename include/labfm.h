@@ -178,6 +178,44 @@ labfm_status labfm_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int fi
 labfm_status labfm_step(labfm_ctx *ctx, const double *beta, void *u, int field_dtype, double dt,
                         int64_t nsteps, const uint8_t *frozen);
 
+/*
+ * Stencil search that allocates nothing.  (The paper has no counterpart: this is an interface
+ * for callers that cannot allocate device memory.)
+ *
+ * Some callers cannot call cudaMalloc: their device memory is owned entirely by another
+ * allocator (a framework's caching pool, a fixed per-process budget on a shared GPU), or they
+ * must not allocate once running (a latency-critical loop, where cudaMalloc may synchronise
+ * the device).  This entry point computes the same stencils as labfm_build_neighbours
+ * (identical predicate, identical CSR arrays, rows ascending in j) without a context and
+ * without allocating: its scratch (the cell grid) lives in a fixed array of about 10 MB in the
+ * library's device memory, which every GPU that loads the library holds until the process
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   device          CUDA device to run on (made current for the call, then restored)
+ *   stream          cudaStream_t the work is enqueued on (NULL = legacy default stream)
+ *   n               number of nodes, 1 <= n <= LABFM_NOALLOC_MAX_NODES
+ *   xy, h           device double[2n] (interleaved) and double[n], as in labfm_build_neighbours
+ *   periodic, box_lo, box_hi   as in labfm_build_neighbours
+ *   row_ptr         device int64[n+1], caller-owned, written
+ *   col             device int32[col_capacity], caller-owned, written (may be NULL if 0)
+ *   col_capacity    entries available in col
+ *   nnz_out         host, receives the number of stencil entries (also on LABFM_ERR_CAPACITY,
+ *                   so the caller can size col and call again)
+ * Returns LABFM_ERR_ARG for bad arguments (as labfm_build_neighbours), LABFM_ERR_CAPACITY if
+ * n > LABFM_NOALLOC_MAX_NODES or nnz > col_capacity (row_ptr is then valid, col untouched),
+ * LABFM_ERR_CUDA on a CUDA error.  The call synchronises `stream` before returning.
+ *
+ * The first call on a device looks up the device address of the fixed array (once per
+ * device); make that first call before any stream capture begins.  All calls share the one
+ * array per device: calls whose GPU work overlaps (on different streams or host threads) race
+ * on it and must be serialised by the caller.  The array keeps the previous call's contents;
+ * every call clears what it needs cleared.
+ */
+#define LABFM_NOALLOC_MAX_NODES 262144
+labfm_status labfm_build_neighbours_noalloc(int device, void *stream, int64_t n, const double *xy, const double *h,
+                                            int periodic, const double box_lo[2], const double box_hi[2],
+                                            int64_t *row_ptr, int32_t *col, int64_t col_capacity, int64_t *nnz_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,9 @@ MAX_OPS = 8
 
 # every symbol include/labfm.h declares
 C_FUNCTIONS = ["labfm_create", "labfm_destroy", "labfm_last_error", "labfm_set_stream", "labfm_build_neighbours",
-               "labfm_get_neighbours", "labfm_build_weights", "labfm_get_weights", "labfm_apply", "labfm_step"]
+               "labfm_get_neighbours", "labfm_build_weights", "labfm_get_weights", "labfm_apply", "labfm_step",
+               "labfm_build_neighbours_noalloc"]
+NOALLOC_MAX_NODES = 262144  # LABFM_NOALLOC_MAX_NODES
 
 _lib = None
 
@@ -82,6 +84,8 @@ def load_library(path: str | None = None, build_if_missing: bool = False):
     lib.labfm_apply.restype = I
     lib.labfm_step.argtypes = [P, P, P, I, D, I64, P]
     lib.labfm_step.restype = I
+    lib.labfm_build_neighbours_noalloc.argtypes = [I, P, I64, P, P, I, P, P, P, P, I64, ct.POINTER(I64)]
+    lib.labfm_build_neighbours_noalloc.restype = I
     if path is None:
         _lib = lib
     return lib

@@ -172,6 +172,20 @@ cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n
     return cudaGetLastError();
 }
 
+size_t scan_workspace_elems(int64_t n) { return scan_tmp_elems(n); }
+
+cudaError_t exclusive_scan_i32_to_i64_ws(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, size_t tmp_elems,
+                                         cudaStream_t s)
+{
+    if (scan_tmp_elems(n) > tmp_elems) return cudaErrorInvalidValue;
+    if (n > 0) {
+        cudaError_t e = scan_rec<int32_t>(in, out, n, tmp, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_scan_total<<<1, 1, 0, s>>>(out, nullptr, in, n, out + n);
+    return cudaGetLastError();
+}
+
 }  // namespace labfm
 
 using namespace labfm;

@@ -84,6 +84,10 @@ labfm_status cuda_fail(labfm_ctx *ctx, cudaError_t e, const char *where);
 // Exclusive prefix sum of in[0..n) (int64) into out[0..n]; out[n] = total.  `tmp` is scratch.
 cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf &tmp, cudaStream_t s);
 cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, DevBuf &tmp, cudaStream_t s);
+// The same scan on a caller-provided workspace of tmp_elems int64 (at least scan_workspace_elems(n)).
+size_t scan_workspace_elems(int64_t n);
+cudaError_t exclusive_scan_i32_to_i64_ws(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, size_t tmp_elems,
+                                         cudaStream_t s);
 
 // Arguments of the mixed-precision build kernel (see build_mixed.cu).
 struct MixedArgsPublic {

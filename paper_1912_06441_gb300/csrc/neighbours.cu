@@ -270,3 +270,151 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
 }
 
 }  // namespace labfm
+
+// ---------------------------------------------------------------------------------------------
+// labfm_build_neighbours_noalloc: the same kernels on a fixed scratch array instead of
+// context-owned allocations.
+// ---------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int64_t NA_MAXN = LABFM_NOALLOC_MAX_NODES;
+constexpr int64_t NA_MAXC = LABFM_NOALLOC_MAX_NODES;  // cells of the search grid
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t NA_OFF_MISC = 0;
+constexpr size_t NA_OFF_CELL_OF = na_align(NA_OFF_MISC + 64);
+constexpr size_t NA_OFF_CELL_COUNT = na_align(NA_OFF_CELL_OF + 4 * NA_MAXN);
+constexpr size_t NA_OFF_CELL_START = na_align(NA_OFF_CELL_COUNT + 4 * NA_MAXC);
+constexpr size_t NA_OFF_CELL_NODES = na_align(NA_OFF_CELL_START + 8 * (NA_MAXC + 1));
+constexpr size_t NA_OFF_CELL_XY = na_align(NA_OFF_CELL_NODES + 4 * NA_MAXN);
+constexpr size_t NA_OFF_COUNTS = na_align(NA_OFF_CELL_XY + 16 * NA_MAXN);
+constexpr size_t NA_OFF_SCAN = na_align(NA_OFF_COUNTS + 4 * NA_MAXN);
+constexpr size_t NA_SCAN_ELEMS = 4096;
+constexpr size_t NA_BYTES = na_align(NA_OFF_SCAN + 8 * NA_SCAN_ELEMS);  // about 10 MB
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_na_mutex;
+void *g_na_ptr[NA_MAX_DEVICES] = {};  // device address of the scratch array, per device
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// The scratch of labfm_build_neighbours_noalloc (one copy per device that loads the library).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+extern "C" labfm_status labfm_build_neighbours_noalloc(int device, void *stream, int64_t n, const double *xy,
+                                                       const double *h, int periodic, const double box_lo[2],
+                                                       const double box_hi[2], int64_t *row_ptr, int32_t *col,
+                                                       int64_t col_capacity, int64_t *nnz_out)
+{
+    using namespace labfm;
+    if (n < 1 || !xy || !h || !box_lo || !box_hi || !row_ptr || !nnz_out || col_capacity < 0 ||
+        (col_capacity > 0 && !col))
+        return LABFM_ERR_ARG;
+    if (n > NA_MAXN) return LABFM_ERR_CAPACITY;
+    for (int d = 0; d < 2; d++)
+        if (!std::isfinite(box_lo[d]) || !std::isfinite(box_hi[d]) || !(box_hi[d] > box_lo[d])) return LABFM_ERR_ARG;
+    if (device < 0 || device >= NA_MAX_DEVICES) return LABFM_ERR_ARG;
+    DeviceGuard guard;
+    if (cudaGetDevice(&guard.prev) != cudaSuccess) return LABFM_ERR_CUDA;
+    if (guard.prev != device) {
+        if (cudaSetDevice(device) != cudaSuccess) return LABFM_ERR_CUDA;
+        guard.changed = true;
+    }
+    char *base;
+    {
+        std::lock_guard<std::mutex> lock(g_na_mutex);
+        if (!g_na_ptr[device]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LABFM_ERR_CUDA;
+            g_na_ptr[device] = p;
+        }
+        base = static_cast<char *>(g_na_ptr[device]);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *misc = reinterpret_cast<unsigned long long *>(base + NA_OFF_MISC);
+    int32_t *cell_of = reinterpret_cast<int32_t *>(base + NA_OFF_CELL_OF);
+    int32_t *cell_count = reinterpret_cast<int32_t *>(base + NA_OFF_CELL_COUNT);
+    int64_t *cell_start = reinterpret_cast<int64_t *>(base + NA_OFF_CELL_START);
+    int32_t *cell_nodes = reinterpret_cast<int32_t *>(base + NA_OFF_CELL_NODES);
+    double2 *cell_xy = reinterpret_cast<double2 *>(base + NA_OFF_CELL_XY);
+    int32_t *counts = reinterpret_cast<int32_t *>(base + NA_OFF_COUNTS);
+    int64_t *scan_tmp = reinterpret_cast<int64_t *>(base + NA_OFF_SCAN);
+
+#define NA_TRY(expr)                                     \
+    do {                                                 \
+        if ((expr) != cudaSuccess) return LABFM_ERR_CUDA; \
+    } while (0)
+
+    int num_sms = 0;
+    NA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
+    // node check and h_max (the counters start at zero on every call)
+    NA_TRY(cudaMemsetAsync(misc, 0, 2 * sizeof(unsigned long long), s));
+    int nb = (int)std::min<int64_t>((n + NB_THREADS - 1) / NB_THREADS, (int64_t)num_sms * 8);
+    k_check<<<nb, NB_THREADS, 0, s>>>(n, xy, h, box_lo[0], box_lo[1], box_hi[0], box_hi[1], misc);
+    NA_TRY(cudaGetLastError());
+    unsigned long long hs[2];
+    NA_TRY(cudaMemcpyAsync(hs, misc, sizeof hs, cudaMemcpyDeviceToHost, s));
+    NA_TRY(cudaStreamSynchronize(s));
+    if (hs[1] != 0) return LABFM_ERR_ARG;
+    double hmax;
+    memcpy(&hmax, &hs[0], sizeof hmax);
+
+    // the same grid rule as labfm_build_neighbours, capped at the scratch's cell count
+    Grid g;
+    g.periodic = periodic ? 1 : 0;
+    double ncell_d[2];
+    for (int d = 0; d < 2; d++) {
+        g.lo[d] = box_lo[d];
+        g.L[d] = box_hi[d] - box_lo[d];
+        g.halfL[d] = 0.5 * g.L[d];
+        ncell_d[d] = std::floor(g.L[d] / (2.0 * hmax * (1.0 + 1e-9)));
+        if (!(ncell_d[d] >= 1.0)) ncell_d[d] = 1.0;
+    }
+    double cap = std::min(4.0 * (double)n + 64.0, (double)NA_MAXC);
+    if (ncell_d[0] * ncell_d[1] > cap) {
+        double f = std::sqrt(ncell_d[0] * ncell_d[1] / cap);
+        for (int d = 0; d < 2; d++) ncell_d[d] = std::max(1.0, std::floor(ncell_d[d] / f));
+    }
+    for (int d = 0; d < 2; d++) {
+        g.nc[d] = (int)ncell_d[d];
+        g.inv_cs[d] = (double)g.nc[d] / g.L[d];
+    }
+    const int64_t ncells = (int64_t)g.nc[0] * g.nc[1];
+    if (ncells > NA_MAXC) return LABFM_ERR_CAPACITY;
+
+    int nbn = (int)((n + NB_THREADS - 1) / NB_THREADS);
+    NA_TRY(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, s));
+    k_cell_assign<<<nbn, NB_THREADS, 0, s>>>(n, xy, g, cell_of, cell_count);
+    NA_TRY(cudaGetLastError());
+    NA_TRY(exclusive_scan_i32_to_i64_ws(cell_count, cell_start, ncells, scan_tmp, NA_SCAN_ELEMS, s));
+    NA_TRY(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, s));
+    k_cell_scatter<<<nbn, NB_THREADS, 0, s>>>(n, xy, cell_of, cell_start, cell_count, cell_nodes, cell_xy);
+    NA_TRY(cudaGetLastError());
+    k_sweep<false><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, counts, nullptr,
+                                              nullptr);
+    NA_TRY(cudaGetLastError());
+    NA_TRY(exclusive_scan_i32_to_i64_ws(counts, row_ptr, n, scan_tmp, NA_SCAN_ELEMS, s));
+    int64_t nnz = 0;
+    NA_TRY(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof nnz, cudaMemcpyDeviceToHost, s));
+    NA_TRY(cudaStreamSynchronize(s));
+    *nnz_out = nnz;
+    if (nnz > col_capacity) return LABFM_ERR_CAPACITY;
+    if (nnz > 0) {
+        k_sweep<true><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, nullptr,
+                                                 row_ptr, col);
+        NA_TRY(cudaGetLastError());
+    }
+    NA_TRY(cudaStreamSynchronize(s));
+#undef NA_TRY
+    return LABFM_OK;
+}
