@@ -30,6 +30,7 @@ import labfm_synth as S  # noqa: E402
 
 METRIC = "order-8 weight build Mnodes/s; apply GB/s vs HBM; mixed vs FP64 at ≤1e-8 err"
 N_SIDE, HS, K, JITTER = 512, 2.2, 8, 0.3
+SKIP_LARGE = False  # --skip-large: leave out the 4.2M-node RK4 and 1M-node wall workloads
 OPS = ("dx", "dy", "lap", "lap4")
 def workload_name():
     return (f"2D periodic jittered lattice {N_SIDE}x{N_SIDE} (+-{JITTER}s), h={HS}s, Wendland C2, order {K} "
@@ -286,7 +287,118 @@ def extra_measurements(torch, P, dev, local_rank, ns, field, hbm):
                         "frac_of_hbm": by / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": by,
                         "derivatives_per_s": len(OPS) * n / (ms * 1e-3)}
     L32.close()
+    if not SKIP_LARGE:
+        out["rk4_2048"] = rk4_large(torch, P, dev, local_rank)
+        out["walls_1m_variable_order"] = walls_variable_order(torch, P, dev, local_rank)
     return out
+
+
+RK4_JITTER = 0.2       # noise of the time-stepping node set (inside the stable range of Sec. 3.3)
+RK4_RBF = "quadratic"  # the kernel of the PDE tests of Sec. 4
+RK4_ABF = "dw0"        # dW0/dr-only ABFs: the form the stability results of Sec. 3.3 belong to
+
+
+def spectral_radius(torch, L, beta, iters=80):
+    """Largest |lambda| of u -> sum_d beta_d L^d(u) by power iteration through labfm_apply."""
+    dev = torch.device("cuda", L.device)
+    g = torch.Generator(device=dev).manual_seed(0)
+    v = torch.randn(L.n, dtype=torch.float64, device=dev, generator=g)
+    v /= v.norm()
+    b = torch.tensor(beta, dtype=torch.float64, device=dev)[:, None]
+    rho = 0.0
+    for _ in range(iters):
+        wv = (b * L.apply(v)).sum(0)
+        rho = float(wv.norm())
+        v = wv / rho
+    return rho
+
+
+def rk4_large(torch, P, dev, local_rank, n_side=2048, nsteps=1000):
+    """The time-stepping workload: 2048^2 jittered periodic nodes (+-0.2 s), order 8, quadratic
+    ABFs in the dW0/dr-only form, weights built once, then nsteps of RK4 for
+    u_t + c.grad u = nu lap u - alpha nabla^8 u (c = (1, 0.5), nu = 1e-3, alpha = 1e-3 h^8)
+    replayed from one CUDA graph; FP32 fields with FP64 weights and with FP32 weights; error
+    against the exact advected, decayed mode."""
+    ns = S.jittered_lattice(n_side, HS, K, jitter=RK4_JITTER, seed=5)
+    n = ns.n
+    C = np.stack([S.op_c_vector(o, K) for o in OPS])
+    h = ns.h[0]
+    beta = [-C_ADV[0], -C_ADV[1], NU, -HV * h ** 8]
+    res = {"nodes": n, "steps": nsteps, "jitter": RK4_JITTER, "rbf": RK4_RBF, "abf_form": RK4_ABF}
+    xy = torch.from_numpy(ns.xy).to(dev)
+    hh = torch.from_numpy(ns.h).to(dev)
+    u0 = S.sincos_field().value(ns.xy)
+    dt = None
+    for wdt in ("f64", "f32"):
+        L = P.Labfm(local_rank)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.build_neighbours(xy, hh, True)
+        nbad = L.build_weights(C, uniform_order=K, rbf=RK4_RBF, abf_form=RK4_ABF, weight_dtype=wdt,
+                               node_status=torch.zeros(n, dtype=torch.int32, device=dev))
+        e1.record()
+        e1.synchronize()
+        if dt is None:
+            # advective CFL 0.5, and 0.8 x the RK4 stability radius on the real axis against the
+            # spectral radius of the right-hand side (FP64 weights)
+            rho = spectral_radius(torch, L, beta)
+            s = 1.0 / n_side
+            dt = min(0.5 * s / float(np.hypot(*C_ADV)), 0.8 * 2.785 / rho)
+            res["spectral_radius"] = rho
+            res["dt"] = dt
+        u = torch.from_numpy(u0.astype(np.float32)).to(dev)
+        L.step(beta, u, dt, nsteps)  # warm: tunes the stage launch shape and records the graph
+        u.copy_(torch.from_numpy(u0.astype(np.float32)).to(dev))
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        L.step(beta, u, dt, nsteps)
+        t1.record()
+        t1.synchronize()
+        ms = t0.elapsed_time(t1)
+        T = dt * nsteps
+        x, y = ns.xy[:, 0], ns.xy[:, 1]
+        exact = np.exp(-8 * np.pi ** 2 * NU * T) * np.sin(2 * np.pi * (x - C_ADV[0] * T)) * \
+            np.cos(2 * np.pi * (y - C_ADV[1] * T))
+        got = u.cpu().numpy().astype(np.float64)
+        wb = 8 if wdt == "f64" else 4
+        stage_bytes = L.nnz * (4 + wb) + n * (8 + 4 + 4 * 3)  # col + combined weight; row_ptr, u, src, acc, next
+        sub = (np.arange(n) // n_side % 8 == 0) & (np.arange(n) % n_side % 8 == 0)  # the 256^2 subsample
+        res[f"weights_{wdt}"] = {
+            "build_ms": e0.elapsed_time(e1), "flagged_nodes": int(nbad), "T": T,
+            "ms_per_step": ms / nsteps, "steps_per_s": nsteps / (ms * 1e-3),
+            "stage_gbs": 4 * stage_bytes / (ms / nsteps * 1e-3) / 1e9,
+            "l2_err_vs_exact": float(np.linalg.norm(got - exact) / np.linalg.norm(exact)),
+            "l2_err_vs_exact_256_subsample": float(np.linalg.norm(got[sub] - exact[sub]) /
+                                                   np.linalg.norm(exact[sub])),
+            "max_abs_u": float(np.abs(got).max())}
+        del u
+        L.close()
+        torch.cuda.empty_cache()
+    res["nnz"] = int(L.nnz)
+    return res
+
+
+def walls_variable_order(torch, P, dev, local_rank, n_side=1000):
+    """Non-periodic unit square with walls, spacing varying 4x, per-node order 2..8 (capped at 4
+    near walls): the bucketed build (one launch per order) in FP64 and mixed precision."""
+    ns = S.variable_wall_nodes(n_side, seed=4)
+    n = ns.n
+    L = P.Labfm(local_rank)
+    L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), False)
+    order = torch.from_numpy(ns.order.astype(np.int8)).to(dev)
+    C = np.stack([S.op_c_vector(o, 8) for o in ("dx", "dy", "lap")])
+    status = torch.zeros(n, dtype=torch.int32, device=dev)
+    res = {"nodes": n, "nnz": int(L.nnz), "order_counts": {int(k): int(v) for k, v in
+                                                           zip(*np.unique(ns.order, return_counts=True))}}
+    for prec in ("fp64", "mixed"):
+        L.build_weights(C, order=order, precision=prec, node_status=status)
+        ms = _time(torch, lambda: L.build_weights(C, order=order, precision=prec, node_status=status), reps=2)
+        st = status.cpu().numpy()
+        res[prec] = {"ms": ms, "mnodes_per_s": n / (ms * 1e-3) / 1e6,
+                     "flagged_nodes": int((st != 0).sum())}
+    L.close()
+    return res
 
 
 def run_reference(args, rank, world):
@@ -448,7 +560,7 @@ def run_labfm(args, rank, world, local_rank):
 
 
 def main():
-    global N_SIDE
+    global N_SIDE, SKIP_LARGE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -457,10 +569,13 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1024)
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-large", action="store_true",
+                    help="leave out the 2048^2 RK4 and 1000^2 wall workloads (profiler captures)")
     ap.add_argument("--n-side", type=int, default=512,
                     help="lattice side (default 512; smaller sizes are for profiler captures only)")
     args = ap.parse_args()
     N_SIDE = args.n_side
+    SKIP_LARGE = args.skip_large or args.n_side != 512
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -54,6 +54,18 @@ enum {
     LABFM_RBF_WENDLAND_C6 = 3, /* 78/(28 pi) (1 - q/2)^8 (4q^3 + 6.25q^2 + 4q + 1), Appendix A.2 */
     LABFM_RBF_GAUSSIAN = 4     /* 9/pi exp(-9 q^2), Appendix A.3 */
 };
+#define LABFM_RBF_MASK 0xff
+
+/* ABF form, OR-ed into the rbf argument of labfm_build_weights.
+ * Default (0): the elements 1-9 (|alpha| <= 3) are the full chain rule of D(W0(|r|)) with
+ * dW0/dr, d2W0/dr2 and d3W0/dr3, as printed in Appendix A; the elements >= 10 keep only
+ * dW0/dr d^alpha|r| (Appendix A, truncation rule).
+ * LABFM_ABF_DW0_ONLY: every element is dW0/dr d^alpha|r|, i.e. the higher RBF derivatives are
+ * dropped for the elements 1-9 too.  Appendix A's truncation sentence names only elements >= 10,
+ * but the stability results of Sec. 3.3 (the Laplacian's noise limits, a purely imaginary
+ * convective spectrum on a regular lattice whenever dW0/dr vanishes at q = 2) are reproduced
+ * by this form and not by the default one; explicit time stepping needs it. */
+#define LABFM_ABF_DW0_ONLY 0x100
 
 /* Arithmetic of the moment-matrix assembly (Eq. disc_form) and solve (Eq. lsys). */
 enum {
@@ -131,7 +143,7 @@ labfm_status labfm_get_neighbours(labfm_ctx *ctx, const int64_t **row_ptr, const
  * and C^d is scaled by h_i^-|alpha| (an exact similarity transform of M_i).
  *   order        device int8[n] per-node order k_i in 1..8, or NULL to use uniform_order
  *   uniform_order  1..8 when order == NULL
- *   rbf          LABFM_RBF_*
+ *   rbf          LABFM_RBF_*, optionally OR-ed with LABFM_ABF_DW0_ONLY
  *   n_ops        number of operators, 1..LABFM_MAX_OPS
  *   C            host double[n_ops * 44]: row d is C^d in the derivative ordering D of
  *                Sec. 2 (d/dx, d/dy, d2/dx2, d2/dxdy, d2/dy2, d3/dx3, ...), physical units;
@@ -158,7 +170,13 @@ labfm_status labfm_get_weights(labfm_ctx *ctx, const void **w, int *dtype, int *
  *   f           device [n] of field_dtype (LABFM_F64 or LABFM_F32)
  *   out         device [n_selected][n] of field_dtype, row-major by operator
  * Accumulation is in double for LABFM_F64 fields and in float for LABFM_F32 fields.
- * Asynchronous.  LABFM_ERR_STATE before labfm_build_weights.
+ * f and out must not overlap.
+ * Launch shape: G lanes share a node and each lane keeps UNR stencil entries in flight,
+ * (G, UNR) in {4, 8, 16, 32} x {2, 4, 8}.  The first call per (n_ops, field dtype, weight
+ * dtype, floor(log2 n), mean stencil size) on a context (n >= 4096, stream not capturing)
+ * times each shape once, writing out repeatedly, waits for the timings, and keeps the fastest
+ * for the life of the context; later calls are asynchronous.
+ * LABFM_ERR_STATE before labfm_build_weights.
  */
 labfm_status labfm_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int field_dtype, void *out);
 
@@ -169,7 +187,10 @@ labfm_status labfm_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int fi
  * stencil entry, w_ji = sum_d beta_d w_ji^d (L^d is linear in w), cached while beta
  * and the weights are unchanged.  Nodes with frozen[i] != 0 keep their value
  * (Dirichlet nodes, Sec. 4.1).  The nsteps x 4 stage launches are recorded once into a
- * CUDA graph and replayed.
+ * CUDA graph and replayed; it is recorded again when an argument other than beta, the
+ * stencil count or size, the weight type or a context buffer changes.  The stage's launch
+ * shape is tuned as for labfm_apply, on first-stage launches that read u and write only
+ * context-owned buffers (u is not changed by the tuning).
  *   beta    host double[n_ops]
  *   u       device [n] of field_dtype, updated in place
  *   frozen  device uint8[n] or NULL

@@ -146,7 +146,7 @@ def variable_wall_nodes(n_side: int, seed: int = 4, jitter: float = 0.3,
     y = eta_n - stretch * np.sin(tw * eta_n) / tw
     sx = (1.0 - stretch * np.cos(tw * xi_n)) / (m - 1)
     sy = (1.0 - stretch * np.cos(tw * eta_n)) / (m - 1)
-    s = np.minimum(sx, sy)
+    s = np.sqrt(sx * sy)  # area-equivalent spacing: pi (2h)^2 / (sx sy) neighbours = 4 pi (h/s)^2
     n = m * m
     u = uniform01(seed, 2 * n)
     on_x_wall = (ii.ravel() == 0) | (ii.ravel() == m - 1)

@@ -24,6 +24,10 @@ _LOCK = threading.Lock()
 _LIBS: dict = {}
 
 RBF = {"wendland_c2": 0, "quadratic": 1, "cone": 2, "wendland_c6": 3, "gaussian": 4}
+# ABF forms (Appendix A): "chain" keeps the second- and third-derivative chain-rule terms of W0 in
+# the elements 1-9 (only elements >= 10 are truncated to dW0/dr d^alpha|r|); "dw0" truncates every
+# element to dW0/dr d^alpha|r|.
+ABF_FORM = {"chain": 0, "dw0": 0x100}
 PMAX = 44
 ST_OK, ST_SINGULAR, ST_UNDERSAMPLED, ST_NONFINITE = 0, 1, 2, 3
 
@@ -137,7 +141,7 @@ def neighbours(xy, h, periodic, lo=(0.0, 0.0), hi=(1.0, 1.0), queries=None, prec
 
 def build_weights(xy, h, periodic, row_ptr, col, C, k=None, order=None, rbf="wendland_c2",
                   lo=(0.0, 0.0), hi=(1.0, 1.0), queries=None, precision="f64", nthreads=0,
-                  want_mhat=False):
+                  want_mhat=False, abf_form="chain"):
     """Weights for every stencil entry (Eqs. disc_form, lsys, w_abf).
 
     ``C`` is ``[n_ops, p]`` (or ``[n_ops, 44]``) in D ordering, physical units.
@@ -163,7 +167,7 @@ def build_weights(xy, h, periodic, row_ptr, col, C, k=None, order=None, rbf="wen
     mh = np.zeros((nq, PMAX, PMAX)) if want_mhat else None
     rc = lib.orc_build_weights(_ptr(xy), _ptr(h), int(periodic), _ptr(np.asarray(lo, np.float64)),
                                _ptr(np.asarray(hi, np.float64)), _ptr(q), nq, _ptr(rp), _ptr(cl),
-                               _ptr(od), int(k or 0), RBF[rbf], n_ops, _ptr(Cp), _ptr(w), _ptr(st),
+                               _ptr(od), int(k or 0), RBF[rbf] | ABF_FORM[abf_form], n_ops, _ptr(Cp), _ptr(w), _ptr(st),
                                _ptr(pr), _ptr(mh), int(nthreads))
     assert rc == 0
     out = {"w": w[:nnz], "status": st, "piv_ratio": pr}
@@ -223,7 +227,7 @@ def monomials(x, y, k, precision="f64"):
     return out
 
 
-def abfs(rbf, x, y, k, precision="f64"):
+def abfs(rbf, x, y, k, precision="f64", abf_form="chain"):
     out = np.zeros(p_of_k(k))
-    _lib(precision).orc_abfs(RBF[rbf], float(x), float(y), int(k), _ptr(out))
+    _lib(precision).orc_abfs(RBF[rbf] | ABF_FORM[abf_form], float(x), float(y), int(k), _ptr(out))
     return out

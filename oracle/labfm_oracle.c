@@ -284,15 +284,20 @@ void orc_monomials(double x, double y, int k, double *X)
  * ABFs W = D(W0(|r|)) at (x, y) with h = 1 (Sec. 2.2, Appendix A).
  * Elements 1..9 (|alpha| <= 3): the chain rule for W0(r(x, y)) with all of
  * W0', W0'', W0'''; elements >= 10 (|alpha| >= 4): W0'(r) d^alpha r only.
+ * With ORC_ABF_DW0_ONLY set in rbf_form, the W0'' and W0''' terms are dropped
+ * for the elements 1..9 as well, so that every element is W0'(r) d^alpha r.
  * ------------------------------------------------------------------------- */
-static void abfs_r(int rbf, real x, real y, int k, real *W)
+#define ORC_ABF_DW0_ONLY 0x100
+static void abfs_r(int rbf_form, real x, real y, int k, real *W)
 {
     int p = orc_p_of_k(k);
+    int rbf = rbf_form & 0xff;
     real dr[ORC_KMAX + 1][ORC_KMAX + 1];
     dr_table(x, y, k < 3 ? 3 : k, dr);
     real d[4];
     orc_rbf_derivs_r(rbf, dr[0][0], d);
     real f1 = d[1], f2 = d[2], f3 = d[3];
+    if (rbf_form & ORC_ABF_DW0_ONLY) f2 = f3 = 0;
     real rx = dr[1][0], ry = dr[0][1];
     real rxx = dr[2][0], rxy = dr[1][1], ryy = dr[0][2];
     for (int e = 0; e < p; e++) {

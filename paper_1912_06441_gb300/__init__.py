@@ -20,6 +20,7 @@ __all__ = ["Labfm", "LabfmError", "load_library", "RBF", "PREC", "DTYPE", "NODE"
 
 RBF = {"wendland_c2": 0, "quadratic": 1, "cone": 2, "wendland_c6": 3, "gaussian": 4}
 PREC = {"fp64": 0, "mixed": 1}
+ABF_FORM = {"chain": 0, "dw0": 0x100}  # LABFM_ABF_DW0_ONLY: every ABF element is dW0/dr d^alpha|r|
 
 
 def precision_code(precision: str, refine: int | None = None) -> int:
@@ -198,8 +199,11 @@ class Labfm:
 
     def build_weights(self, C, order=None, uniform_order: int = 4, rbf: str = "wendland_c2",
                       precision: str = "fp64", weight_dtype: str = "f64", node_status=None,
-                      refine: int | None = None) -> int:
+                      refine: int | None = None, abf_form: str = "chain") -> int:
         """Weights w_ji^d for the target vectors C (rows, D ordering, Sec. 2); returns #flagged nodes.
+
+        ``abf_form`` "chain" keeps the full chain rule in the ABF elements 1-9 (Appendix A as
+        printed), "dw0" truncates every element to dW0/dr d^alpha|r| (LABFM_ABF_DW0_ONLY).
 
         Raises LabfmError(LABFM_ERR_SINGULAR) only if ``node_status`` is None and a node was
         flagged; with a node_status tensor the flags are returned there and the count here."""
@@ -215,7 +219,7 @@ class Labfm:
         ps = None if node_status is None else self._dev(node_status, torch.int32, "node_status", self.n)
         self._sync_stream()
         nbad = ct.c_int64()
-        st = self.lib.labfm_build_weights(self._ctx, po, int(uniform_order), RBF[rbf], n_ops,
+        st = self.lib.labfm_build_weights(self._ctx, po, int(uniform_order), RBF[rbf] | ABF_FORM[abf_form], n_ops,
                                           Cp.ctypes.data_as(ct.c_void_p), precision_code(precision, refine),
                                           DTYPE[weight_dtype], ps,
                                           ct.byref(nbad))

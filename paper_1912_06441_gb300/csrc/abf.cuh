@@ -81,12 +81,14 @@ constexpr RPolyTable make_rpoly_table()
     return T;
 }
 
-// d^m W0/dq^m, m = 1..3, at q in [0, 2) for the kernels of labfm.h.
-__device__ __forceinline__ void rbf_derivs(int rbf, double q, double &d1, double &d2, double &d3)
+// d^m W0/dq^m, m = 1..3, at q in [0, 2) for the kernels of labfm.h.  rbf_form is a
+// LABFM_RBF_* value, optionally with LABFM_ABF_DW0_ONLY: then d2 = d3 = 0, which reduces the
+// chain rule of the elements 1..9 to dW0/dq d^alpha|r| (the form of the elements >= 10).
+__device__ __forceinline__ void rbf_derivs(int rbf_form, double q, double &d1, double &d2, double &d3)
 {
     const double PI = 3.141592653589793238462643383279502884;
     double t = 1.0 - 0.5 * q;
-    switch (rbf) {
+    switch (rbf_form & LABFM_RBF_MASK) {
     case LABFM_RBF_WENDLAND_C2: {  // W = c t^4 (1 + 2q)
         const double c = 7.0 / (4.0 * PI);
         d1 = -5.0 * c * q * t * t * t;
@@ -130,6 +132,7 @@ __device__ __forceinline__ void rbf_derivs(int rbf, double q, double &d1, double
         break;
     }
     }
+    if (rbf_form & LABFM_ABF_DW0_ONLY) d2 = d3 = 0.0;
 }
 
 namespace {

@@ -251,7 +251,6 @@ labfm_status labfm_build_neighbours(labfm_ctx *ctx, int64_t n, const double *xy,
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, LABFM_ERR_CUDA, "cudaSetDevice failed");
     ctx->have_weights = false;
     ctx->wcomb_valid = false;
-    ctx->graph.release();
     return run_neighbours(ctx, n, xy, h, periodic ? 1 : 0, box_lo, box_hi, nnz_out);
 }
 
@@ -276,7 +275,11 @@ labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int unifor
     if (ctx->n == 0) return fail(ctx, LABFM_ERR_STATE, "labfm_build_neighbours must come first");
     if (!order && (uniform_order < 1 || uniform_order > LABFM_MAX_ORDER))
         return fail(ctx, LABFM_ERR_ARG, "uniform_order must be in 1..8");
-    if (rbf < LABFM_RBF_WENDLAND_C2 || rbf > LABFM_RBF_GAUSSIAN) return fail(ctx, LABFM_ERR_ARG, "unknown rbf");
+    {
+        int base = rbf & LABFM_RBF_MASK, form = rbf & ~LABFM_RBF_MASK;
+        if (base < LABFM_RBF_WENDLAND_C2 || base > LABFM_RBF_GAUSSIAN || (form & ~LABFM_ABF_DW0_ONLY))
+            return fail(ctx, LABFM_ERR_ARG, "unknown rbf");
+    }
     if (n_ops < 1 || n_ops > LABFM_MAX_OPS) return fail(ctx, LABFM_ERR_ARG, "n_ops must be in 1..8");
     if (!C) return fail(ctx, LABFM_ERR_ARG, "C is null");
     for (int t = 0; t < n_ops * LABFM_PMAX; t++)
@@ -290,7 +293,6 @@ labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int unifor
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, LABFM_ERR_CUDA, "cudaSetDevice failed");
     ctx->have_weights = false;
     ctx->wcomb_valid = false;
-    ctx->graph.release();
     labfm_status st =
         run_build(ctx, order, uniform_order, rbf, n_ops, C, precision, weight_dtype, node_status, n_bad_out);
     if (st == LABFM_OK || st == LABFM_ERR_SINGULAR) {

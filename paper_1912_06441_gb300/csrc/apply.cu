@@ -7,6 +7,10 @@
 // every weight and index load of a warp is a contiguous, fully used segment; UNR entries per
 // lane are in flight before the first use.  The partial sums of a group are combined with
 // butterfly shuffles.
+//
+// (G, UNR) is chosen per context by a small autotuner: the first apply (or RK4 run) for a
+// given operator count, data types and problem class times every shape once on the real
+// stencils and keeps the fastest.
 #include <cmath>
 #include <type_traits>
 
@@ -16,10 +20,6 @@ namespace labfm {
 namespace {
 
 constexpr int APPLY_THREADS = 256;
-constexpr int UNR = 4;
-
-template <class T> struct Acc { using type = double; };
-template <> struct Acc<float> { using type = float; };
 
 // Weights of entry e (NOPS of them) into wv[], converted to the accumulation type.
 template <int NOPS, class WT, class AT>
@@ -42,15 +42,18 @@ __device__ __forceinline__ void load_w(const WT *__restrict__ w, int64_t e, AT *
     }
 }
 
+template <class FT, class WT>
+using acc_t = typename std::conditional<std::is_same<FT, float>::value && std::is_same<WT, float>::value, float,
+                                        double>::type;
+
 // out[sel(d)][i] = sum_j (f_j - f_i) w_ji^d for the operators in mask.
-template <int NOPS, class FT, class WT>
+template <int NOPS, class FT, class WT, int UNR>
 __global__ void __launch_bounds__(APPLY_THREADS) k_apply(int64_t n, const int64_t *__restrict__ row_ptr,
                                                          const int32_t *__restrict__ col, const WT *__restrict__ w,
                                                          const FT *__restrict__ f, FT *__restrict__ out, uint32_t mask,
                                                          int G)
 {
-    using AT = typename std::conditional<std::is_same<FT, float>::value && std::is_same<WT, float>::value, float,
-                                         double>::type;
+    using AT = acc_t<FT, WT>;
     const int lane = threadIdx.x & (G - 1);
     const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) / G;
     const bool live = i < n;
@@ -102,45 +105,10 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_apply(int64_t n, const int64_
     }
 }
 
-int lanes_for(int64_t n, int64_t nnz)
-{
-    double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-    int G = 4;
-    while (G < 32 && G * UNR < avg) G *= 2;
-    return G;
-}
-
-template <int NOPS, class FT, class WT>
-cudaError_t launch_apply_t(labfm_ctx *ctx, uint32_t mask, const void *f, void *out)
-{
-    int G = lanes_for(ctx->n, ctx->nnz);
-    if (G < NOPS) G = NOPS < 8 ? (NOPS <= 4 ? 4 : 8) : 8;  // lane d writes operator d
-    int64_t threads = ctx->n * G;
-    unsigned blocks = (unsigned)((threads + APPLY_THREADS - 1) / APPLY_THREADS);
-    k_apply<NOPS, FT, WT><<<blocks, APPLY_THREADS, 0, ctx->stream>>>(
-        ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(), (const WT *)ctx->w.ptr, (const FT *)f, (FT *)out,
-        mask, G);
-    return cudaGetLastError();
-}
-
-template <int NOPS>
-cudaError_t launch_apply_n(labfm_ctx *ctx, uint32_t mask, const void *f, int fdt, void *out)
-{
-    if (ctx->wdtype == LABFM_F64)
-        return fdt == LABFM_F64 ? launch_apply_t<NOPS, double, double>(ctx, mask, f, out)
-                                : launch_apply_t<NOPS, float, double>(ctx, mask, f, out);
-    return fdt == LABFM_F64 ? launch_apply_t<NOPS, double, float>(ctx, mask, f, out)
-                            : launch_apply_t<NOPS, float, float>(ctx, mask, f, out);
-}
-
-// ---------------------------------------------------------------------------------------------
-// RK4
-// ---------------------------------------------------------------------------------------------
-
 // wc[e] = sum_d beta_d w[e][d] (in double, stored in WT)
 template <class WT>
-__global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, WT *__restrict__ wc, double b0, double b1, double b2, double b3, double b4, double b5,
-                          double b6, double b7)
+__global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, WT *__restrict__ wc, double b0, double b1,
+                          double b2, double b3, double b4, double b5, double b6, double b7)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
@@ -155,7 +123,7 @@ __global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, WT *
 //   stage 1: acc += dt/3 F,     nxt = u + dt/2 F
 //   stage 2: acc += dt/3 F,     nxt = u + dt F
 //   stage 3: u = acc + dt/6 F
-template <class FT, class WT>
+template <class FT, class WT, int UNR>
 __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const int64_t *__restrict__ row_ptr,
                                                              const int32_t *__restrict__ col, const WT *__restrict__ wc,
                                                              const FT *__restrict__ src, FT *__restrict__ u,
@@ -163,8 +131,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const in
                                                              const uint8_t *__restrict__ frozen, int stage, double dt,
                                                              int G)
 {
-    using AT = typename std::conditional<std::is_same<FT, float>::value && std::is_same<WT, float>::value, float,
-                                         double>::type;
+    using AT = acc_t<FT, WT>;
     const int lane = threadIdx.x & (G - 1);
     const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) / G;
     const bool live = i < n;
@@ -218,23 +185,165 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const in
     }
 }
 
-template <class FT, class WT>
-cudaError_t enqueue_steps(labfm_ctx *ctx, void *u, double dt, int64_t nsteps, const uint8_t *frozen, cudaStream_t s)
+// ---------------------------------------------------------------------------------------------
+// Launch shapes and the autotuner
+// ---------------------------------------------------------------------------------------------
+struct Shape {
+    int G, UNR;
+};
+
+// default shape: enough lanes that UNR entries per lane cover an average stencil
+Shape default_shape(const labfm_ctx *ctx, int min_g)
 {
-    int G = lanes_for(ctx->n, ctx->nnz);
-    int64_t threads = ctx->n * G;
-    unsigned blocks = (unsigned)((threads + APPLY_THREADS - 1) / APPLY_THREADS);
-    FT *uu = (FT *)u, *acc = ctx->rk_acc.as<FT>(), *sa = ctx->rk_stage_a.as<FT>(), *sb = ctx->rk_stage_b.as<FT>();
+    double avg = ctx->n > 0 ? (double)ctx->nnz / (double)ctx->n : 0.0;
+    int G = 4;
+    while (G < 32 && G * 4 < avg) G *= 2;
+    if (G < min_g) G = min_g;
+    return Shape{G, 4};
+}
+
+unsigned blocks_for(int64_t n, int G) { return (unsigned)((n * G + APPLY_THREADS - 1) / APPLY_THREADS); }
+
+template <int NOPS, class FT, class WT>
+cudaError_t launch_apply_shape(labfm_ctx *ctx, Shape sh, uint32_t mask, const void *f, void *out, cudaStream_t s)
+{
+    const unsigned blocks = blocks_for(ctx->n, sh.G);
+    auto args = [&](auto kern) {
+        kern<<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(),
+                                              (const WT *)ctx->w.ptr, (const FT *)f, (FT *)out, mask, sh.G);
+    };
+    switch (sh.UNR) {
+    case 2: args(k_apply<NOPS, FT, WT, 2>); break;
+    case 8: args(k_apply<NOPS, FT, WT, 8>); break;
+    default: args(k_apply<NOPS, FT, WT, 4>); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class FT, class WT>
+cudaError_t launch_stage_shape(labfm_ctx *ctx, Shape sh, const FT *src, FT *u, FT *acc, FT *nxt, const uint8_t *frozen,
+                               int stage, double dt, cudaStream_t s)
+{
+    const unsigned blocks = blocks_for(ctx->n, sh.G);
     const WT *wc = (const WT *)ctx->wcomb.ptr;
-    const int64_t *rp = ctx->row_ptr.as<int64_t>();
-    const int32_t *cl = ctx->col.as<int32_t>();
+    auto args = [&](auto kern) {
+        kern<<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(), wc, src, u,
+                                              acc, nxt, frozen, stage, dt, sh.G);
+    };
+    switch (sh.UNR) {
+    case 2: args(k_rk4_stage<FT, WT, 2>); break;
+    case 8: args(k_rk4_stage<FT, WT, 8>); break;
+    default: args(k_rk4_stage<FT, WT, 4>); break;
+    }
+    return cudaGetLastError();
+}
+
+// Time every shape with `run` (which enqueues one launch on ctx->stream) and keep the fastest.
+template <class RunFn>
+cudaError_t autotune(labfm_ctx *ctx, uint64_t key, int min_g, RunFn run, Shape &best)
+{
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        best = Shape{(int)(it->second >> 8), (int)(it->second & 0xff)};
+        return cudaSuccess;
+    }
+    best = default_shape(ctx, min_g);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(ctx->stream, &cap);
+    if (ce != cudaSuccess) return ce;
+    if (cap != cudaStreamCaptureStatusNone) return cudaSuccess;  // caller is recording a graph: no timing
+    if (ctx->n < 4096) {  // too small to time meaningfully
+        ctx->tuned[key] = ((uint32_t)best.G << 8) | (uint32_t)best.UNR;
+        return cudaSuccess;
+    }
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    float best_ms = 1e30f;
+    const int gs[4] = {4, 8, 16, 32}, us[3] = {2, 4, 8};
+    for (int gi = 0; gi < 4 && e == cudaSuccess; gi++) {
+        for (int ui = 0; ui < 3 && e == cudaSuccess; ui++) {
+            Shape sh{gs[gi], us[ui]};
+            if (sh.G < min_g) continue;
+            e = run(sh);  // warm-up
+            if (e != cudaSuccess) break;
+            cudaEventRecord(e0, ctx->stream);
+            e = run(sh);
+            cudaEventRecord(e1, ctx->stream);
+            if (e != cudaSuccess) break;
+            e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best = sh;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) ctx->tuned[key] = ((uint32_t)best.G << 8) | (uint32_t)best.UNR;
+    return e;
+}
+
+// Shapes are tuned per kind of launch, data types and problem class: floor(log2 n) and the mean
+// stencil size rounded to an integer, so that rebuilding stencils of the same kind (a moving node
+// set, a bench repetition) reuses the choice instead of timing again.
+uint64_t tune_key(const labfm_ctx *ctx, int kind, int nops, int fdt, int wdt)
+{
+    uint64_t lg = 0;
+    while (lg < 62 && ((int64_t)1 << (lg + 1)) <= ctx->n) lg++;
+    uint64_t deg = ctx->n > 0 ? (uint64_t)((double)ctx->nnz / (double)ctx->n + 0.5) : 0;
+    if (deg > 0xffff) deg = 0xffff;
+    return (deg << 40) | (lg << 32) | ((uint64_t)kind << 24) | ((uint64_t)nops << 16) | ((uint64_t)fdt << 8) |
+           (uint64_t)wdt;
+}
+
+template <int NOPS, class FT, class WT>
+cudaError_t launch_apply_t(labfm_ctx *ctx, uint32_t mask, const void *f, int fdt, void *out)
+{
+    const int min_g = NOPS <= 4 ? 4 : 8;  // lane d writes operator d
+    Shape sh;
+    cudaError_t e = autotune(
+        ctx, tune_key(ctx, 1, NOPS, fdt, ctx->wdtype), min_g,
+        [&](Shape s) { return launch_apply_shape<NOPS, FT, WT>(ctx, s, mask, f, out, ctx->stream); }, sh);
+    if (e != cudaSuccess) return e;
+    return launch_apply_shape<NOPS, FT, WT>(ctx, sh, mask, f, out, ctx->stream);
+}
+
+template <int NOPS>
+cudaError_t launch_apply_n(labfm_ctx *ctx, uint32_t mask, const void *f, int fdt, void *out)
+{
+    if (ctx->wdtype == LABFM_F64)
+        return fdt == LABFM_F64 ? launch_apply_t<NOPS, double, double>(ctx, mask, f, fdt, out)
+                                : launch_apply_t<NOPS, float, double>(ctx, mask, f, fdt, out);
+    return fdt == LABFM_F64 ? launch_apply_t<NOPS, double, float>(ctx, mask, f, fdt, out)
+                            : launch_apply_t<NOPS, float, float>(ctx, mask, f, fdt, out);
+}
+
+template <class FT, class WT>
+cudaError_t enqueue_steps(labfm_ctx *ctx, void *u, int fdt, double dt, int64_t nsteps, const uint8_t *frozen,
+                          cudaStream_t s)
+{
+    FT *uu = (FT *)u, *acc = ctx->rk_acc.as<FT>(), *sa = ctx->rk_stage_a.as<FT>(), *sb = ctx->rk_stage_b.as<FT>();
+    // tune on stage 0, which reads u and writes only the work buffers
+    Shape sh;
+    cudaError_t e = autotune(
+        ctx, tune_key(ctx, 2, 1, fdt, ctx->wdtype), 1,
+        [&](Shape sp) { return launch_stage_shape<FT, WT>(ctx, sp, uu, uu, acc, sa, frozen, 0, dt, ctx->stream); },
+        sh);
+    if (e != cudaSuccess) return e;
     for (int64_t st = 0; st < nsteps; st++) {
-        k_rk4_stage<FT, WT><<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, rp, cl, wc, uu, uu, acc, sa, frozen, 0, dt, G);
-        k_rk4_stage<FT, WT><<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, rp, cl, wc, sa, uu, acc, sb, frozen, 1, dt, G);
-        k_rk4_stage<FT, WT><<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, rp, cl, wc, sb, uu, acc, sa, frozen, 2, dt, G);
-        k_rk4_stage<FT, WT><<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, rp, cl, wc, sa, uu, acc, nullptr, frozen, 3, dt, G);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if ((e = launch_stage_shape<FT, WT>(ctx, sh, uu, uu, acc, sa, frozen, 0, dt, s)) != cudaSuccess) return e;
+        if ((e = launch_stage_shape<FT, WT>(ctx, sh, sa, uu, acc, sb, frozen, 1, dt, s)) != cudaSuccess) return e;
+        if ((e = launch_stage_shape<FT, WT>(ctx, sh, sb, uu, acc, sa, frozen, 2, dt, s)) != cudaSuccess) return e;
+        if ((e = launch_stage_shape<FT, WT>(ctx, sh, sa, uu, acc, (FT *)nullptr, frozen, 3, dt, s)) != cudaSuccess)
+            return e;
     }
     return cudaSuccess;
 }
@@ -243,10 +352,10 @@ cudaError_t enqueue_steps_dt(labfm_ctx *ctx, int fdt, void *u, double dt, int64_
                              cudaStream_t s)
 {
     if (ctx->wdtype == LABFM_F64)
-        return fdt == LABFM_F64 ? enqueue_steps<double, double>(ctx, u, dt, nsteps, frozen, s)
-                                : enqueue_steps<float, double>(ctx, u, dt, nsteps, frozen, s);
-    return fdt == LABFM_F64 ? enqueue_steps<double, float>(ctx, u, dt, nsteps, frozen, s)
-                            : enqueue_steps<float, float>(ctx, u, dt, nsteps, frozen, s);
+        return fdt == LABFM_F64 ? enqueue_steps<double, double>(ctx, u, fdt, dt, nsteps, frozen, s)
+                                : enqueue_steps<float, double>(ctx, u, fdt, dt, nsteps, frozen, s);
+    return fdt == LABFM_F64 ? enqueue_steps<double, float>(ctx, u, fdt, dt, nsteps, frozen, s)
+                            : enqueue_steps<float, float>(ctx, u, fdt, dt, nsteps, frozen, s);
 }
 
 }  // namespace
@@ -276,9 +385,7 @@ labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int fdt, doub
     bool same_beta = ctx->wcomb_valid;
     for (int d = 0; d < ctx->n_ops && same_beta; d++) same_beta = (ctx->beta_cached[d] == beta[d]);
     if (!same_beta) {
-        void *old = ctx->wcomb.ptr;
         LABFM_CUDA_TRY(ctx, ctx->wcomb.reserve(wsz * (nnz > 0 ? nnz : 1)));
-        if (old != ctx->wcomb.ptr) ctx->graph.release();
         double b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int d = 0; d < ctx->n_ops; d++) b[d] = beta[d];
         unsigned blocks = (unsigned)((nnz + 255) / 256);
@@ -296,19 +403,30 @@ labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int fdt, doub
         for (int d = 0; d < ctx->n_ops; d++) ctx->beta_cached[d] = beta[d];
         ctx->wcomb_valid = true;
     }
-    void *old_a = ctx->rk_acc.ptr, *old_b = ctx->rk_stage_a.ptr, *old_c = ctx->rk_stage_b.ptr;
     LABFM_CUDA_TRY(ctx, ctx->rk_acc.reserve(fsz * n));
     LABFM_CUDA_TRY(ctx, ctx->rk_stage_a.reserve(fsz * n));
     LABFM_CUDA_TRY(ctx, ctx->rk_stage_b.reserve(fsz * n));
-    if (old_a != ctx->rk_acc.ptr || old_b != ctx->rk_stage_a.ptr || old_c != ctx->rk_stage_b.ptr) ctx->graph.release();
 
     StepGraph &g = ctx->graph;
-    if (!(g.exec && g.u == u && g.frozen == frozen && g.dtype == fdt && g.dt == dt && g.nsteps == nsteps)) {
+    const bool same = g.exec && g.u == u && g.frozen == frozen && g.dtype == fdt && g.dt == dt &&
+                      g.nsteps == nsteps && g.n == n && g.nnz == nnz && g.wdtype == ctx->wdtype &&
+                      g.row_ptr == ctx->row_ptr.ptr && g.col == ctx->col.ptr && g.wc == ctx->wcomb.ptr &&
+                      g.acc == ctx->rk_acc.ptr && g.sa == ctx->rk_stage_a.ptr && g.sb == ctx->rk_stage_b.ptr;
+    if (!same) {
         g.release();
         if (!ctx->capture_stream) {
             LABFM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
         }
+        // the capture stream must see the combined weights (enqueued on the context stream)
+        LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         cudaGraph_t graph = nullptr;
+        // shapes are tuned (on the context stream) before the capture begins
+        {
+            cudaError_t te = enqueue_steps_dt(ctx, fdt, u, dt, 0, frozen, s);
+            if (te != cudaSuccess) return cuda_fail(ctx, te, "RK4 stage tuning");
+            // the capture stream must not start before the tuning launches end
+            LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        }
         LABFM_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = enqueue_steps_dt(ctx, fdt, u, dt, nsteps, frozen, ctx->capture_stream);
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &graph);
@@ -328,6 +446,15 @@ labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int fdt, doub
         g.dtype = fdt;
         g.dt = dt;
         g.nsteps = nsteps;
+        g.n = n;
+        g.nnz = nnz;
+        g.wdtype = ctx->wdtype;
+        g.row_ptr = ctx->row_ptr.ptr;
+        g.col = ctx->col.ptr;
+        g.wc = ctx->wcomb.ptr;
+        g.acc = ctx->rk_acc.ptr;
+        g.sa = ctx->rk_stage_a.ptr;
+        g.sb = ctx->rk_stage_b.ptr;
     }
     LABFM_CUDA_TRY(ctx, cudaGraphLaunch(g.exec, s));
     return LABFM_OK;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 
 #include "labfm.h"
 
@@ -25,7 +26,8 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(ptr); }
 };
 
-// Cached CUDA graph of an RK4 run.
+// Cached CUDA graph of an RK4 run, with everything its launches were recorded with: it is
+// replayed only while all of these are unchanged.
 struct StepGraph {
     cudaGraphExec_t exec = nullptr;
     const void *u = nullptr;
@@ -33,6 +35,9 @@ struct StepGraph {
     int dtype = -1;
     double dt = 0;
     int64_t nsteps = 0;
+    int64_t n = -1, nnz = -1;
+    int wdtype = -1;
+    const void *row_ptr = nullptr, *col = nullptr, *wc = nullptr, *acc = nullptr, *sa = nullptr, *sb = nullptr;
     void release();
 };
 
@@ -71,6 +76,10 @@ struct labfm_ctx {
     bool wcomb_valid = false;
     labfm::StepGraph graph;
     cudaStream_t capture_stream = nullptr;  // private stream used only to record the RK4 graph
+
+    // launch shapes chosen by the apply / RK4 autotuner:
+    // key (kind, n_ops, dtypes, size class of n, mean stencil size) -> (G << 8) | UNR
+    std::unordered_map<uint64_t, uint32_t> tuned;
 
     // pinned host word for status read-back
     void *host_small = nullptr;

@@ -24,7 +24,8 @@ def c_matrix(k, ops):
     return np.stack([S.op_c_vector(o, k) for o in ops])
 
 
-def gpu_run(ns, k, ops, rbf="wendland_c2", weight_dtype="f64", order=None, precision="fp64", refine=None):
+def gpu_run(ns, k, ops, rbf="wendland_c2", weight_dtype="f64", order=None, precision="fp64", refine=None,
+            abf_form="chain"):
     import torch
 
     from paper_1912_06441_gb300 import Labfm
@@ -37,7 +38,7 @@ def gpu_run(ns, k, ops, rbf="wendland_c2", weight_dtype="f64", order=None, preci
     status = torch.full((ns.n,), -1, dtype=torch.int32, device=dev)
     od = None if order is None else torch.from_numpy(np.ascontiguousarray(order, dtype=np.int8)).to(dev)
     nbad = L.build_weights(c_matrix(k, ops), order=od, uniform_order=k, rbf=rbf, weight_dtype=weight_dtype,
-                           node_status=status, precision=precision, refine=refine)
+                           node_status=status, precision=precision, refine=refine, abf_form=abf_form)
     rp, col = L.get_neighbours()
     w = L.get_weights()
     torch.cuda.synchronize()
@@ -65,9 +66,9 @@ def node_rel_err(a, b, rp):
     return out
 
 
-def oracle_refs(ns, k, ops, q, rp_q, col_q, rbf="wendland_c2", order=None):
+def oracle_refs(ns, k, ops, q, rp_q, col_q, rbf="wendland_c2", order=None, abf_form="chain"):
     C = c_matrix(k, ops)
-    kw = dict(queries=q, rbf=rbf, lo=ns.lo, hi=ns.hi)
+    kw = dict(queries=q, rbf=rbf, lo=ns.lo, hi=ns.hi, abf_form=abf_form)
     if order is None:
         kw["k"] = k
     else:

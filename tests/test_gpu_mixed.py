@@ -32,6 +32,19 @@ def test_mixed_weights_parity_by_order(k):
     G.assert_weights_parity(w[idx], r64, rld, rp_q, label=f"mixed k={k}")
 
 
+@pytest.mark.parametrize("k,hs,rbf", [(4, 2.0, "quadratic"), (8, 2.2, "quadratic")])
+def test_mixed_weights_parity_dw0_form(k, hs, rbf):
+    """The dW0/dr-only ABF form (LABFM_ABF_DW0_ONLY) through the mixed-precision build."""
+    ns = S.jittered_lattice(36, hs, k, seed=50 + k, jitter=0.2)
+    ops = G.OPS[k]
+    _, rp, col, w, status, _ = G.gpu_run(ns, k, ops, rbf=rbf, precision="mixed", abf_form="dw0")
+    q = np.arange(2, ns.n, 3)
+    rp_q, col_q, idx = G.rows_of(rp, col, q)
+    r64, rld = G.oracle_refs(ns, k, ops, q, rp_q, col_q, rbf=rbf, abf_form="dw0")
+    assert np.array_equal(status[q], r64["status"])
+    G.assert_weights_parity(w[idx], r64, rld, rp_q, label=f"mixed dw0 k={k}")
+
+
 def test_mixed_refinement_reaches_the_fp64_floor():
     """At k = 8 the double-float solution alone is far from FP64 (condition numbers ~1e12);
     each refinement step on the reproduction residual brings it down to the FP64 floor."""

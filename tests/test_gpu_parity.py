@@ -119,6 +119,25 @@ def test_weights_parity_multi_chunk_stencils(k, hs):
     G.assert_weights_parity(w[idx], r64, rld, rp_q, label=f"chunked k={k}")
 
 
+@pytest.mark.parametrize("k,hs,rbf", [(2, 1.6, "quadratic"), (4, 2.0, "cone"), (6, 2.0, "wendland_c6"),
+                                      (8, 2.2, "quadratic"), (8, 2.8, "wendland_c2")])
+def test_weights_parity_dw0_form(k, hs, rbf):
+    """LABFM_ABF_DW0_ONLY: every ABF element dW0/dr d^alpha|r| (the form the stability results of
+    Sec. 3.3 belong to), FP64 build against the oracle's dw0 form."""
+    ns = S.jittered_lattice(36, hs, k, seed=40 + k, jitter=0.2)
+    ops = G.OPS[k]
+    _, rp, col, w, status, _ = G.gpu_run(ns, k, ops, rbf=rbf, abf_form="dw0")
+    q = np.arange(1, ns.n, 3)
+    rp_q, col_q, idx = G.rows_of(rp, col, q)
+    r64, rld = G.oracle_refs(ns, k, ops, q, rp_q, col_q, rbf=rbf, abf_form="dw0")
+    assert np.array_equal(status[q], r64["status"])
+    G.assert_weights_parity(w[idx], r64, rld, rp_q, label=f"dw0 k={k} {rbf}")
+    # the two forms differ (elements 3-9 change) unless the kernel's d2W0/dq2 vanishes identically
+    if rbf != "cone":
+        _, _, _, w_chain, _, _ = G.gpu_run(ns, k, ops, rbf=rbf)
+        assert np.abs(w_chain - w).max() > 1e-6 * np.abs(w).max()
+
+
 def test_weights_variable_order_and_walls():
     """Per-node order 2..8 on a non-periodic set with varying spacing (one-sided stencils at walls)."""
     ns = S.variable_wall_nodes(40, seed=4)
@@ -249,6 +268,37 @@ def test_rk4_parity(dtype):
     assert np.array_equal(got[::7], u0[::7].astype(np.float32 if dtype == "f32" else np.float64).astype(np.float64))
 
 
+def test_rk4_parity_order8_hyperviscosity():
+    """The time-stepping operator at order 8: advection + diffusion + the -alpha nabla^8
+    hyperviscosity of Sec. 3.3 (alpha = 1e-3 h^8), quadratic ABFs in the dw0 form on +-0.2 dr
+    noise, where every eigenvalue has a non-positive real part; 30 steps against the oracle."""
+    import torch
+
+    k = 8
+    ns = S.jittered_lattice(40, 2.2, k, seed=72, jitter=0.2)
+    ops = ("dx", "dy", "lap", "lap4")
+    L, rp, col, w, status, _ = G.gpu_run(ns, k, ops, rbf="quadratic", abf_form="dw0")
+    assert (status == 0).all()
+    h = ns.h[0]
+    beta = np.array([-1.0, -0.5, 1e-3, -1e-3 * h ** 8])
+    # RK4 step inside its stability region: dt = 2 / rho, rho = spectral radius of the operator
+    A = np.zeros((ns.n, ns.n))
+    node = np.repeat(np.arange(ns.n), np.diff(rp))
+    np.add.at(A, (node, col), w @ beta)
+    np.add.at(A, (node, node), -(w @ beta))
+    lam = np.linalg.eigvals(A)
+    assert lam.real.max() < 1e-9 * np.abs(lam).max()  # no growing mode
+    dt = 2.0 / np.abs(lam).max()
+    u0 = S.sincos_field().value(ns.xy)
+    dev = torch.device("cuda", 0)
+    u = torch.from_numpy(u0).to(dev)
+    L.step(beta, u, dt, 30)
+    got = u.cpu().numpy()
+    ref = oracle.rk4(rp, col, w, beta, u0, dt, 30)
+    assert np.isfinite(ref).all() and np.abs(ref).max() < 1.01
+    assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+
+
 # ---------------------------------------------------------------------------------- errors
 
 
@@ -279,3 +329,16 @@ def test_argument_and_state_errors():
     with pytest.raises(LabfmError) as e:
         L.build_weights(G.c_matrix(2, ("dx",)), order=order)
     assert e.value.status == 1
+    # rbf values outside LABFM_RBF_* | LABFM_ABF_DW0_ONLY are rejected on the host
+    import ctypes as ct
+
+    C = np.zeros((1, 44))
+    C[0, 0] = 1.0
+    nbad = ct.c_int64()
+    for bad_rbf in (5, 0x200, 0x101 | 0x400, -1):
+        st = L.lib.labfm_build_weights(L._ctx, None, 2, bad_rbf, 1, C.ctypes.data_as(ct.c_void_p), 0, 0, None,
+                                       ct.byref(nbad))
+        assert st == 1, bad_rbf
+    st = L.lib.labfm_build_weights(L._ctx, None, 2, 0x101, 1, C.ctypes.data_as(ct.c_void_p), 0, 0, None,
+                                   ct.byref(nbad))
+    assert st in (0, 5)

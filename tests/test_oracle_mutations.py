@@ -24,6 +24,8 @@ MUTATIONS = {
     "truncation rule ignored (W'' kept at order 4)": ("        } else if (n == 3) {",
                                                       "        } else if (n == 4) { v += f2 * rx * rx * rx * rx;\n        } else if (n == 3) {"),
     "stencil radius h instead of 2h": ("double R = 2.0 * h[i];", "double R = h[i];"),
+    "dw0 form keeps the d2W0/dr2 terms": ("if (rbf_form & ORC_ABF_DW0_ONLY) f2 = f3 = 0;",
+                                          "if (rbf_form & ORC_ABF_DW0_ONLY) f3 = 0;"),
 }
 
 PINS = [
@@ -38,6 +40,8 @@ PINS = [
     lambda: P.test_polynomial_reproduction(6, 2.0, "wendland_c2", 1e-9),
     P.test_rk4_linear_system_is_taylor_polynomial,
     P.test_abfs_truncated_high_orders_vs_sympy,
+    lambda: P.test_abfs_dw0_form_is_the_printed_dW0_bracket("quadratic"),
+    lambda: P.test_laplacian_noise_limits_dw0_form(4, 2.0, 1.0),
 ]
 
 

@@ -506,3 +506,95 @@ def test_rk4_linear_system_is_taylor_polynomial():
     Zf[fz.astype(bool)] = 0.0
     Pf = np.eye(n) + Zf + Zf @ Zf / 2 + Zf @ Zf @ Zf / 6 + Zf @ Zf @ Zf @ Zf / 24
     np.testing.assert_allclose(got2, np.linalg.matrix_power(Pf, 3) @ u0, rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------------------ ABF forms, stability
+
+
+@pytest.mark.parametrize("rbf", ["cone", "wendland_c2", "quadratic", "gaussian", "wendland_c6"])
+def test_abfs_dw0_form_is_the_printed_dW0_bracket(rbf):
+    """abf_form "dw0" (every element truncated to dW0/dr d^alpha|r|): elements 1-14 equal dW0/dr
+    times the printed dW0/dr bracket of Sec. 2.2 / Appendix A, for every kernel."""
+    rows = [r for r in _printed_abfs() if r[1] == "d1"]
+    assert sorted(e for e, _, _ in rows) == list(range(1, 15))
+    for x, y in [(0.3, 0.5), (-1.1, 0.4), (0.9, -1.2), (-0.2, -0.35)]:
+        r = math.hypot(x, y)
+        d1 = oracle.rbf_derivs(rbf, r)[1]
+        ref = np.zeros(14)
+        for e, _, expr in rows:
+            ref[e - 1] = d1 * eval(expr, {"__builtins__": {}}, {"x": x, "y": y, "r": r})
+        got = oracle.abfs(rbf, x, y, 4, abf_form="dw0")
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+        # elements >= 10 are the same in both forms
+        np.testing.assert_array_equal(oracle.abfs(rbf, x, y, 8, abf_form="dw0")[9:],
+                                      oracle.abfs(rbf, x, y, 8)[9:])
+
+
+def _global_matrix(n, rp, col, w):
+    """A with (A f)_i = sum_j (f_j - f_i) w_ji (the global derivative matrix of Sec. 3.3)."""
+    A = np.zeros((n, n))
+    node = np.repeat(np.arange(n), np.diff(rp))
+    np.add.at(A, (node, col), w)
+    np.add.at(A, (node, node), -w)
+    return A
+
+
+def _spectrum(k, hdr, rbf, form, jitter, op, seed=5, n_side=21):
+    ns = S.jittered_lattice(n_side, hdr, k, jitter=jitter, seed=seed)
+    rp, col = oracle.neighbours(ns.xy, ns.h, True)
+    w = oracle.build_weights(ns.xy, ns.h, True, rp, col, S.op_c_vector(op, k)[None, :], k=k, rbf=rbf,
+                             abf_form=form)["w"][:, 0]
+    return np.linalg.eigvals(_global_matrix(ns.n, rp, col, w)), ns.h[0]
+
+
+def _noise_limits():
+    out = []
+    with open(os.path.join(GOLD, "paper_numbers.txt")) as fh:
+        for line in fh:
+            if line.startswith("noise_limit_quadratic"):
+                _, k, hdr, lim = line.split()
+                out.append((int(k), float(hdr), float(lim)))
+    return out
+
+
+@pytest.mark.parametrize("k,hdr,limit", _noise_limits())
+def test_laplacian_noise_limits_dw0_form(k, hdr, limit):
+    """Sec. 3.3, Table of noise limits: with the quadratic ABFs the Laplacian has no growing mode
+    for noise below the printed limit.  Checked at half the limit (at most 0.5 dr of displacement;
+    each coordinate uniform in +-eps/sqrt(2), so no node moves further than eps) on two node sets:
+    the largest real part of the spectrum stays at rounding level."""
+    eps = min(0.5, limit / 2)
+    for seed in (5, 6):
+        lam, h = _spectrum(k, hdr, "quadratic", "dw0", eps / math.sqrt(2), "lap", seed=seed)
+        assert lam.real.max() * h * h < 1e-10, (seed, lam.real.max() * h * h)
+        assert lam.real.min() * h * h < -1.0  # the operator does damp
+
+
+def test_chain_form_breaks_the_noise_limits():
+    """The same points with the chain-rule terms kept in elements 1-9 (Appendix A as printed)
+    have modes that grow at rates far above rounding level: the stability results of Sec. 3.3
+    are those of the dW0/dr-only form.  (Records why both forms exist.)"""
+    for k, hdr, limit in _noise_limits():
+        eps = min(0.5, limit / 2)
+        lam, h = _spectrum(k, hdr, "quadratic", "chain", eps / math.sqrt(2), "lap")
+        assert lam.real.max() * h * h > 0.1, (k, hdr)
+
+
+def test_convective_spectrum_on_a_regular_lattice():
+    """Sec. 3.3 (eigenvalues of the convective operator, regular lattice, h/dr = 2): the
+    real parts are at rounding level for the quadratic and Wendland ABFs, larger by orders of
+    magnitude (yet small) for the Gaussian, and substantial for the cone, whose dW0/dr does not
+    vanish at q = 2.  At h/dr = 2 lattice neighbours sit on the support edge, so only kernels
+    whose ABFs vanish there give a skew-symmetric operator."""
+    def ratio(rbf, k, form="dw0"):
+        lam, _ = _spectrum(k, 2.0, rbf, form, 0.0, "dx")
+        return np.abs(lam.real).max() / np.abs(lam).max()
+    for k in (2, 4, 6):
+        assert ratio("quadratic", k) < 1e-13
+        assert ratio("wendland_c2", k) < 1e-13
+        assert ratio("wendland_c6", k) < 1e-13
+        assert ratio("gaussian", k) < 1e-6
+        assert ratio("cone", k) > 1e-2
+    assert ratio("gaussian", 6) > 1e3 * ratio("quadratic", 6)
+    # the chain-rule form with the quadratic kernel does not have this property (d2W0/dq2 != 0 at q = 2)
+    assert ratio("quadratic", 4, form="chain") > 0.1
