@@ -184,8 +184,12 @@ labfm_status labfm_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int fi
  * Explicit time stepping with the classical four-stage Runge-Kutta scheme (Sec. 4.1) of
  *   du/dt = F(u),  F(u)_i = sum_d beta_d L_i^d(u)
  * for nsteps steps of size dt.  The operators are combined once into one weight per
- * stencil entry, w_ji = sum_d beta_d w_ji^d (L^d is linear in w), cached while beta
- * and the weights are unchanged.  Nodes with frozen[i] != 0 keep their value
+ * stencil entry, w_ji = sum_d beta_d w_ji^d (L^d is linear in w, summed in double), cached
+ * while beta, the weights and the field type are unchanged.  It is kept in the weight type,
+ * except for FP64 weights with FP32 fields: then it is kept as a double-float pair (two
+ * floats, ~48 bits) and the stencil sums run in double-float arithmetic on the FP32 pipes.
+ * The per-node stage update is in double (in float when weights and field are FP32).
+ * Nodes with frozen[i] != 0 keep their value
  * (Dirichlet nodes, Sec. 4.1).  The nsteps x 4 stage launches are recorded once into a
  * CUDA graph and replayed; it is recorded again when an argument other than beta, the
  * stencil count or size, the weight type or a context buffer changes.  The stage's launch

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "df64.cuh"
 #include "labfm_internal.cuh"
 
 namespace labfm {
@@ -105,17 +106,35 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_apply(int64_t n, const int64_
     }
 }
 
-// wc[e] = sum_d beta_d w[e][d] (in double, stored in WT)
+// Storage of the combined RK4 weight wc_ji = sum_d beta_d w_ji^d (a context-owned buffer):
+//   CW_F64  double           FP64 weights, FP64 fields: accumulated in double
+//   CW_F32  float            FP32 weights: accumulated in the field type
+//   CW_DF   float2 (hi, lo)  FP64 weights, FP32 fields: the double rounded to a double-float
+//                            pair once, here, so that the stage accumulates on the FP32 pipes
+//                            (about 48 bits, far below the FP32 field rounding) instead of
+//                            converting and multiplying in FP64 for every stencil entry
+enum { CW_F64 = 0, CW_F32 = 1, CW_DF = 2 };
+
+int cw_format(int fdt, int wdt) { return wdt == LABFM_F32 ? CW_F32 : (fdt == LABFM_F32 ? CW_DF : CW_F64); }
+size_t cw_bytes(int fmt) { return fmt == CW_F32 ? 4 : 8; }
+
 template <class WT>
-__global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, WT *__restrict__ wc, double b0, double b1,
-                          double b2, double b3, double b4, double b5, double b6, double b7)
+__global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, void *__restrict__ wc, int fmt, double b0,
+                          double b1, double b2, double b3, double b4, double b5, double b6, double b7)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
     const double b[8] = {b0, b1, b2, b3, b4, b5, b6, b7};
     double s = 0.0;
     for (int d = 0; d < n_ops; d++) s = fma(b[d], (double)w[e * n_ops + d], s);
-    wc[e] = (WT)s;
+    if (fmt == CW_F64) {
+        ((double *)wc)[e] = s;
+    } else if (fmt == CW_F32) {
+        ((float *)wc)[e] = (float)s;
+    } else {
+        df v = df_from_double(s);
+        ((float2 *)wc)[e] = make_float2(v.hi, v.lo);
+    }
 }
 
 // One RK4 stage.  F_i = sum_j (src_j - src_i) wc_ji (0 on frozen nodes), then
@@ -123,45 +142,68 @@ __global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, WT *
 //   stage 1: acc += dt/3 F,     nxt = u + dt/2 F
 //   stage 2: acc += dt/3 F,     nxt = u + dt F
 //   stage 3: u = acc + dt/6 F
-template <class FT, class WT, int UNR>
+// The per-node update runs in double (float for FP32 weights and fields).
+template <class FT, int CW, int UNR>
 __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const int64_t *__restrict__ row_ptr,
-                                                             const int32_t *__restrict__ col, const WT *__restrict__ wc,
+                                                             const int32_t *__restrict__ col,
+                                                             const void *__restrict__ wc_raw,
                                                              const FT *__restrict__ src, FT *__restrict__ u,
                                                              FT *__restrict__ acc_buf, FT *__restrict__ nxt,
                                                              const uint8_t *__restrict__ frozen, int stage, double dt,
                                                              int G)
 {
-    using AT = acc_t<FT, WT>;
+    // AT: type of the per-node update; the stencil sum runs in AT, or in double-float for CW_DF
+    using AT = typename std::conditional<std::is_same<FT, float>::value && CW == CW_F32, float, double>::type;
+    using WT = typename std::conditional<CW == CW_F64, double, typename std::conditional<CW == CW_F32, float,
+                                                                                         float2>::type>::type;
+    const WT *__restrict__ wc = (const WT *)wc_raw;
     const int lane = threadIdx.x & (G - 1);
     const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) / G;
     const bool live = i < n;
     int64_t rs = 0, re = 0;
-    AT si = 0;
+    FT si = 0;
     if (live) {
         rs = row_ptr[i];
         re = row_ptr[i + 1];
-        si = (AT)src[i];
+        si = src[i];
     }
     AT acc = 0;
+    df accd{0.0f, 0.0f};
     for (int64_t base = rs; base < re; base += (int64_t)G * UNR) {
         int cj[UNR];
-        AT wv[UNR];
+        WT wv[UNR];
 #pragma unroll
         for (int q = 0; q < UNR; q++) {
             int64_t e = base + (int64_t)q * G + lane;
             if (e < re) {
                 cj[q] = __ldcs(col + e);
-                wv[q] = (AT)__ldcs(wc + e);
+                wv[q] = __ldcs(wc + e);
             } else {
                 cj[q] = -1;
-                wv[q] = 0;
             }
         }
 #pragma unroll
-        for (int q = 0; q < UNR; q++)
-            if (cj[q] >= 0) acc = fma((AT)src[cj[q]] - si, wv[q], acc);
+        for (int q = 0; q < UNR; q++) {
+            if (cj[q] >= 0) {
+                if constexpr (CW == CW_DF) {
+                    float dh, dl;  // src_j - src_i exactly, as a double-float
+                    two_sum((float)src[cj[q]], -(float)si, dh, dl);
+                    accd = df_fma(df{dh, dl}, df{wv[q].x, wv[q].y}, accd);
+                } else {
+                    acc = fma((AT)src[cj[q]] - (AT)si, (AT)wv[q], acc);
+                }
+            }
+        }
     }
-    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if constexpr (CW == CW_DF) {
+        for (int o = G >> 1; o > 0; o >>= 1) {
+            df other{__shfl_xor_sync(0xffffffffu, accd.hi, o), __shfl_xor_sync(0xffffffffu, accd.lo, o)};
+            accd = df_add(accd, other);
+        }
+        acc = df_to_double(accd);
+    } else {
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    }
     if (!live || lane != 0) return;
     AT F = (frozen && frozen[i]) ? (AT)0 : acc;
     AT h = (AT)dt;
@@ -220,20 +262,20 @@ cudaError_t launch_apply_shape(labfm_ctx *ctx, Shape sh, uint32_t mask, const vo
     return cudaGetLastError();
 }
 
-template <class FT, class WT>
+template <class FT, int CW>
 cudaError_t launch_stage_shape(labfm_ctx *ctx, Shape sh, const FT *src, FT *u, FT *acc, FT *nxt, const uint8_t *frozen,
                                int stage, double dt, cudaStream_t s)
 {
     const unsigned blocks = blocks_for(ctx->n, sh.G);
-    const WT *wc = (const WT *)ctx->wcomb.ptr;
+    const void *wc = ctx->wcomb.ptr;
     auto args = [&](auto kern) {
         kern<<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(), wc, src, u,
                                               acc, nxt, frozen, stage, dt, sh.G);
     };
     switch (sh.UNR) {
-    case 2: args(k_rk4_stage<FT, WT, 2>); break;
-    case 8: args(k_rk4_stage<FT, WT, 8>); break;
-    default: args(k_rk4_stage<FT, WT, 4>); break;
+    case 2: args(k_rk4_stage<FT, CW, 2>); break;
+    case 8: args(k_rk4_stage<FT, CW, 8>); break;
+    default: args(k_rk4_stage<FT, CW, 4>); break;
     }
     return cudaGetLastError();
 }
@@ -326,7 +368,7 @@ cudaError_t launch_apply_n(labfm_ctx *ctx, uint32_t mask, const void *f, int fdt
                             : launch_apply_t<NOPS, float, float>(ctx, mask, f, fdt, out);
 }
 
-template <class FT, class WT>
+template <class FT, int CW>
 cudaError_t enqueue_steps(labfm_ctx *ctx, void *u, int fdt, double dt, int64_t nsteps, const uint8_t *frozen,
                           cudaStream_t s)
 {
@@ -335,14 +377,14 @@ cudaError_t enqueue_steps(labfm_ctx *ctx, void *u, int fdt, double dt, int64_t n
     Shape sh;
     cudaError_t e = autotune(
         ctx, tune_key(ctx, 2, 1, fdt, ctx->wdtype), 1,
-        [&](Shape sp) { return launch_stage_shape<FT, WT>(ctx, sp, uu, uu, acc, sa, frozen, 0, dt, ctx->stream); },
+        [&](Shape sp) { return launch_stage_shape<FT, CW>(ctx, sp, uu, uu, acc, sa, frozen, 0, dt, ctx->stream); },
         sh);
     if (e != cudaSuccess) return e;
     for (int64_t st = 0; st < nsteps; st++) {
-        if ((e = launch_stage_shape<FT, WT>(ctx, sh, uu, uu, acc, sa, frozen, 0, dt, s)) != cudaSuccess) return e;
-        if ((e = launch_stage_shape<FT, WT>(ctx, sh, sa, uu, acc, sb, frozen, 1, dt, s)) != cudaSuccess) return e;
-        if ((e = launch_stage_shape<FT, WT>(ctx, sh, sb, uu, acc, sa, frozen, 2, dt, s)) != cudaSuccess) return e;
-        if ((e = launch_stage_shape<FT, WT>(ctx, sh, sa, uu, acc, (FT *)nullptr, frozen, 3, dt, s)) != cudaSuccess)
+        if ((e = launch_stage_shape<FT, CW>(ctx, sh, uu, uu, acc, sa, frozen, 0, dt, s)) != cudaSuccess) return e;
+        if ((e = launch_stage_shape<FT, CW>(ctx, sh, sa, uu, acc, sb, frozen, 1, dt, s)) != cudaSuccess) return e;
+        if ((e = launch_stage_shape<FT, CW>(ctx, sh, sb, uu, acc, sa, frozen, 2, dt, s)) != cudaSuccess) return e;
+        if ((e = launch_stage_shape<FT, CW>(ctx, sh, sa, uu, acc, (FT *)nullptr, frozen, 3, dt, s)) != cudaSuccess)
             return e;
     }
     return cudaSuccess;
@@ -351,11 +393,13 @@ cudaError_t enqueue_steps(labfm_ctx *ctx, void *u, int fdt, double dt, int64_t n
 cudaError_t enqueue_steps_dt(labfm_ctx *ctx, int fdt, void *u, double dt, int64_t nsteps, const uint8_t *frozen,
                              cudaStream_t s)
 {
-    if (ctx->wdtype == LABFM_F64)
-        return fdt == LABFM_F64 ? enqueue_steps<double, double>(ctx, u, fdt, dt, nsteps, frozen, s)
-                                : enqueue_steps<float, double>(ctx, u, fdt, dt, nsteps, frozen, s);
-    return fdt == LABFM_F64 ? enqueue_steps<double, float>(ctx, u, fdt, dt, nsteps, frozen, s)
-                            : enqueue_steps<float, float>(ctx, u, fdt, dt, nsteps, frozen, s);
+    switch (cw_format(fdt, ctx->wdtype)) {
+    case CW_F64: return enqueue_steps<double, CW_F64>(ctx, u, fdt, dt, nsteps, frozen, s);
+    case CW_DF: return enqueue_steps<float, CW_DF>(ctx, u, fdt, dt, nsteps, frozen, s);
+    default:
+        return fdt == LABFM_F64 ? enqueue_steps<double, CW_F32>(ctx, u, fdt, dt, nsteps, frozen, s)
+                                : enqueue_steps<float, CW_F32>(ctx, u, fdt, dt, nsteps, frozen, s);
+    }
 }
 
 }  // namespace
@@ -379,29 +423,28 @@ labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int fdt, doub
 {
     cudaStream_t s = ctx->stream;
     const int64_t n = ctx->n, nnz = ctx->nnz;
-    size_t wsz = ctx->wdtype == LABFM_F64 ? 8 : 4;
     size_t fsz = fdt == LABFM_F64 ? 8 : 4;
-    // combined weight, cached while beta and the weights are unchanged
-    bool same_beta = ctx->wcomb_valid;
+    const int fmt = cw_format(fdt, ctx->wdtype);
+    // combined weight, cached while beta, the weights and the storage format are unchanged
+    bool same_beta = ctx->wcomb_valid && ctx->wcomb_dtype == fmt;
     for (int d = 0; d < ctx->n_ops && same_beta; d++) same_beta = (ctx->beta_cached[d] == beta[d]);
     if (!same_beta) {
-        LABFM_CUDA_TRY(ctx, ctx->wcomb.reserve(wsz * (nnz > 0 ? nnz : 1)));
+        LABFM_CUDA_TRY(ctx, ctx->wcomb.reserve(cw_bytes(fmt) * (nnz > 0 ? nnz : 1)));
         double b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int d = 0; d < ctx->n_ops; d++) b[d] = beta[d];
         unsigned blocks = (unsigned)((nnz + 255) / 256);
         if (nnz > 0) {
             if (ctx->wdtype == LABFM_F64)
-                k_combine<double><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<double>(),
-                                                         ctx->wcomb.as<double>(), b[0], b[1], b[2], b[3], b[4], b[5],
-                                                         b[6], b[7]);
+                k_combine<double><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<double>(), ctx->wcomb.ptr, fmt,
+                                                         b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7]);
             else
-                k_combine<float><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<float>(),
-                                                        ctx->wcomb.as<float>(), b[0], b[1], b[2], b[3], b[4], b[5],
-                                                        b[6], b[7]);
+                k_combine<float><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<float>(), ctx->wcomb.ptr, fmt,
+                                                        b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7]);
             LABFM_CUDA_TRY(ctx, cudaGetLastError());
         }
         for (int d = 0; d < ctx->n_ops; d++) ctx->beta_cached[d] = beta[d];
         ctx->wcomb_valid = true;
+        ctx->wcomb_dtype = fmt;
     }
     LABFM_CUDA_TRY(ctx, ctx->rk_acc.reserve(fsz * n));
     LABFM_CUDA_TRY(ctx, ctx->rk_stage_a.reserve(fsz * n));
