@@ -559,6 +559,50 @@ def run_labfm(args, rank, world, local_rank):
     L.close()
 
 
+PROFILE_CASES = ("apply_f32_512", "apply_f64_512", "stage_df_1024", "stage_f32_1024", "build_fp64_256",
+                 "build_mixed_256")
+
+
+def profile_case(name):
+    """A small, untimed run of one kernel family, for profiler captures (ncu -k ... python bench.py
+    --profile NAME): the workloads above at sizes that hold a few GB at most."""
+    import torch
+
+    import paper_1912_06441_gb300 as P
+
+    dev = torch.device("cuda", 0)
+    L = P.Labfm(0)
+    if name.startswith("apply") or name.startswith("build"):
+        n_side = 512 if name.startswith("apply") else 256
+        ns = S.jittered_lattice(n_side, HS, K, jitter=JITTER, seed=2)
+        C = np.stack([S.op_c_vector(o, K) for o in OPS])
+        L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), True)
+        wdt = "f32" if name == "apply_f32_512" else "f64"
+        prec = "mixed" if name == "build_mixed_256" else "fp64"
+        for _ in range(1 if name.startswith("apply") else 3):
+            L.build_weights(C, uniform_order=K, precision=prec, weight_dtype=wdt)
+        if name.startswith("apply"):
+            f = torch.from_numpy(field_for_profile(ns)).to(dev, torch.float32 if wdt == "f32" else torch.float64)
+            for _ in range(30):
+                L.apply(f)
+    else:
+        ns = S.jittered_lattice(1024, HS, K, jitter=RK4_JITTER, seed=5)
+        C = np.stack([S.op_c_vector(o, K) for o in OPS])
+        L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), True)
+        L.build_weights(C, uniform_order=K, rbf=RK4_RBF, abf_form=RK4_ABF,
+                        weight_dtype="f64" if name == "stage_df_1024" else "f32")
+        h = ns.h[0]
+        u = torch.from_numpy(S.sincos_field().value(ns.xy).astype(np.float32)).to(dev)
+        for _ in range(3):
+            L.step([-C_ADV[0], -C_ADV[1], NU, -HV * h ** 8], u, 1e-4, 2)
+    torch.cuda.synchronize()
+    L.close()
+
+
+def field_for_profile(ns):
+    return S.fourier_field(n_modes=16, kmax=32, seed=3).value(ns.xy)
+
+
 def main():
     global N_SIDE, SKIP_LARGE
     ap = argparse.ArgumentParser()
@@ -573,7 +617,12 @@ def main():
                     help="leave out the 2048^2 RK4 and 1000^2 wall workloads (profiler captures)")
     ap.add_argument("--n-side", type=int, default=512,
                     help="lattice side (default 512; smaller sizes are for profiler captures only)")
+    ap.add_argument("--profile", choices=PROFILE_CASES, default=None,
+                    help="run one small untimed case of a kernel family for a profiler capture, then exit")
     args = ap.parse_args()
+    if args.profile:
+        profile_case(args.profile)
+        return
     N_SIDE = args.n_side
     SKIP_LARGE = args.skip_large or args.n_side != 512
     rank = int(os.environ.get("RANK", 0))

@@ -52,11 +52,12 @@ template <int NOPS, class FT, class WT, int UNR>
 __global__ void __launch_bounds__(APPLY_THREADS) k_apply(int64_t n, const int64_t *__restrict__ row_ptr,
                                                          const int32_t *__restrict__ col, const WT *__restrict__ w,
                                                          const FT *__restrict__ f, FT *__restrict__ out, uint32_t mask,
-                                                         int G)
+                                                         int lg_g)
 {
     using AT = acc_t<FT, WT>;
+    const int G = 1 << lg_g;  // lanes per node, a power of two
     const int lane = threadIdx.x & (G - 1);
-    const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) / G;
+    const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) >> lg_g;
     const bool live = i < n;
     int64_t rs = 0, re = 0;
     AT fi = 0;
@@ -142,23 +143,24 @@ __global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, void
 //   stage 1: acc += dt/3 F,     nxt = u + dt/2 F
 //   stage 2: acc += dt/3 F,     nxt = u + dt F
 //   stage 3: u = acc + dt/6 F
-// The per-node update runs in double (float for FP32 weights and fields).
+// The per-node update runs in the field type.
 template <class FT, int CW, int UNR>
 __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const int64_t *__restrict__ row_ptr,
                                                              const int32_t *__restrict__ col,
                                                              const void *__restrict__ wc_raw,
                                                              const FT *__restrict__ src, FT *__restrict__ u,
                                                              FT *__restrict__ acc_buf, FT *__restrict__ nxt,
-                                                             const uint8_t *__restrict__ frozen, int stage, double dt,
-                                                             int G)
+                                                             const uint8_t *__restrict__ frozen, int stage, FT dt,
+                                                             int lg_g)
 {
-    // AT: type of the per-node update; the stencil sum runs in AT, or in double-float for CW_DF
-    using AT = typename std::conditional<std::is_same<FT, float>::value && CW == CW_F32, float, double>::type;
+    // AT: type of the stencil sum (double-float for CW_DF); the per-node update runs in FT
+    using AT = typename std::conditional<std::is_same<FT, float>::value && CW != CW_F64, float, double>::type;
     using WT = typename std::conditional<CW == CW_F64, double, typename std::conditional<CW == CW_F32, float,
                                                                                          float2>::type>::type;
     const WT *__restrict__ wc = (const WT *)wc_raw;
+    const int G = 1 << lg_g;  // lanes per node, a power of two
     const int lane = threadIdx.x & (G - 1);
-    const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) / G;
+    const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) >> lg_g;
     const bool live = i < n;
     int64_t rs = 0, re = 0;
     FT si = 0;
@@ -200,29 +202,28 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const in
             df other{__shfl_xor_sync(0xffffffffu, accd.hi, o), __shfl_xor_sync(0xffffffffu, accd.lo, o)};
             accd = df_add(accd, other);
         }
-        acc = df_to_double(accd);
+        acc = accd.hi + accd.lo;  // CW_DF comes with FP32 fields
     } else {
         for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     }
     if (!live || lane != 0) return;
-    AT F = (frozen && frozen[i]) ? (AT)0 : acc;
-    AT h = (AT)dt;
-    AT ui = (AT)u[i];
+    const FT F = (frozen && frozen[i]) ? (FT)0 : (FT)acc;
+    const FT ui = u[i];
     switch (stage) {
     case 0:
-        acc_buf[i] = (FT)(ui + h * (AT)(1.0 / 6.0) * F);
-        nxt[i] = (FT)(ui + h * (AT)0.5 * F);
+        acc_buf[i] = ui + dt * (FT)(1.0 / 6.0) * F;
+        nxt[i] = ui + dt * (FT)0.5 * F;
         break;
     case 1:
-        acc_buf[i] = (FT)((AT)acc_buf[i] + h * (AT)(1.0 / 3.0) * F);
-        nxt[i] = (FT)(ui + h * (AT)0.5 * F);
+        acc_buf[i] = acc_buf[i] + dt * (FT)(1.0 / 3.0) * F;
+        nxt[i] = ui + dt * (FT)0.5 * F;
         break;
     case 2:
-        acc_buf[i] = (FT)((AT)acc_buf[i] + h * (AT)(1.0 / 3.0) * F);
-        nxt[i] = (FT)(ui + h * F);
+        acc_buf[i] = acc_buf[i] + dt * (FT)(1.0 / 3.0) * F;
+        nxt[i] = ui + dt * F;
         break;
     default:
-        u[i] = (FT)((AT)acc_buf[i] + h * (AT)(1.0 / 6.0) * F);
+        u[i] = acc_buf[i] + dt * (FT)(1.0 / 6.0) * F;
         break;
     }
 }
@@ -245,6 +246,12 @@ Shape default_shape(const labfm_ctx *ctx, int min_g)
 }
 
 unsigned blocks_for(int64_t n, int G) { return (unsigned)((n * G + APPLY_THREADS - 1) / APPLY_THREADS); }
+int log2_of(int G)
+{
+    int l = 0;
+    while ((1 << l) < G) l++;
+    return l;
+}
 
 template <int NOPS, class FT, class WT>
 cudaError_t launch_apply_shape(labfm_ctx *ctx, Shape sh, uint32_t mask, const void *f, void *out, cudaStream_t s)
@@ -252,7 +259,7 @@ cudaError_t launch_apply_shape(labfm_ctx *ctx, Shape sh, uint32_t mask, const vo
     const unsigned blocks = blocks_for(ctx->n, sh.G);
     auto args = [&](auto kern) {
         kern<<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(),
-                                              (const WT *)ctx->w.ptr, (const FT *)f, (FT *)out, mask, sh.G);
+                                              (const WT *)ctx->w.ptr, (const FT *)f, (FT *)out, mask, log2_of(sh.G));
     };
     switch (sh.UNR) {
     case 2: args(k_apply<NOPS, FT, WT, 2>); break;
@@ -270,7 +277,7 @@ cudaError_t launch_stage_shape(labfm_ctx *ctx, Shape sh, const FT *src, FT *u, F
     const void *wc = ctx->wcomb.ptr;
     auto args = [&](auto kern) {
         kern<<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(), wc, src, u,
-                                              acc, nxt, frozen, stage, dt, sh.G);
+                                              acc, nxt, frozen, stage, (FT)dt, log2_of(sh.G));
     };
     switch (sh.UNR) {
     case 2: args(k_rk4_stage<FT, CW, 2>); break;
