@@ -232,7 +232,7 @@ def deriv_errors(d, ref):
     e = np.abs(d - ref) / sc
     return {"l2": (np.linalg.norm(d - ref, axis=1) / np.linalg.norm(ref, axis=1)).tolist(),
             "median": np.median(e, axis=1).tolist(), "p99": np.percentile(e, 99, axis=1).tolist(),
-            "max": e.max(axis=1).tolist()}
+            "max": e.max(axis=1).tolist(), "frac_nodes_le_1e-8": (e <= 1e-8).mean(axis=1).tolist()}
 
 
 def mixed_vs_fp64(torch, P, dev, local_rank, nsx, k, ops, field):
@@ -277,15 +277,23 @@ def extra_measurements(torch, P, dev, local_rank, ns, field, hbm):
     f32 = torch.from_numpy(field.value(ns.xy).astype(np.float32)).to(dev)
     o32 = torch.empty((len(OPS), n), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    ts = []
-    for _ in range(5):
-        flush.zero_()
-        ts.append(_time(torch, lambda: L32.apply(f32, out=o32), reps=1))
-    ms = float(np.median(ts))
+    L32.apply(f32, out=o32)  # tunes the launch shape
+    flush.zero_()
+    # 20 back-to-back launches: the 325 MB the kernel streams exceed the 129 MB L2, so each
+    # launch reads its weights from HBM; the average leaves out the host launch latency
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        L32.apply(f32, out=o32)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
     by = apply_bytes(n, L32.nnz, len(OPS), wbytes=4, fbytes=4)
     out["apply_f32"] = {"kernel": "k_apply<4,float,float>", "ms": ms, "achieved_gbs": by / (ms * 1e-3) / 1e9,
                         "frac_of_hbm": by / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": by,
-                        "derivatives_per_s": len(OPS) * n / (ms * 1e-3)}
+                        "derivatives_per_s": len(OPS) * n / (ms * 1e-3),
+                        "timing": f"mean of {reps} back-to-back launches (inputs larger than L2)"}
     L32.close()
     if not SKIP_LARGE:
         out["rk4_2048"] = rk4_large(torch, P, dev, local_rank)
@@ -361,6 +369,23 @@ def rk4_large(torch, P, dev, local_rank, n_side=2048, nsteps=1000):
         exact = np.exp(-8 * np.pi ** 2 * NU * T) * np.sin(2 * np.pi * (x - C_ADV[0] * T)) * \
             np.cos(2 * np.pi * (y - C_ADV[1] * T))
         got = u.cpu().numpy().astype(np.float64)
+        if wdt == "f32":
+            # the FP32 apply of all four operators on this 4.2M-node set (1.3 GB per launch)
+            f = torch.from_numpy(u0.astype(np.float32)).to(dev)
+            o = torch.empty((len(OPS), n), dtype=torch.float32, device=dev)
+            L.apply(f, out=o)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(10):
+                L.apply(f, out=o)
+            a1.record()
+            a1.synchronize()
+            ams = a0.elapsed_time(a1) / 10
+            aby = apply_bytes(n, L.nnz, len(OPS), wbytes=4, fbytes=4)
+            res["apply_f32"] = {"ms": ams, "achieved_gbs": aby / (ams * 1e-3) / 1e9,
+                                "frac_of_hbm": aby / (ams * 1e-3) / 1e9 / hbm_peak()[0],
+                                "derivatives_per_s": len(OPS) * n / (ams * 1e-3)}
+            del f, o
         wb = 8 if wdt == "f64" else 4
         stage_bytes = L.nnz * (4 + wb) + n * (8 + 4 + 4 * 3)  # col + combined weight; row_ptr, u, src, acc, next
         sub = (np.arange(n) // n_side % 8 == 0) & (np.arange(n) % n_side % 8 == 0)  # the 256^2 subsample
