@@ -245,14 +245,16 @@ def mixed_vs_fp64(torch, P, dev, local_rank, nsx, k, ops, field):
     f = torch.from_numpy(field.value(nsx.xy)).to(dev)
     res = {}
     ders = {}
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "mixed_tc"):
         L.build_weights(C, uniform_order=k, precision=prec)
         ms = _time(torch, lambda: L.build_weights(C, uniform_order=k, precision=prec))
         ders[prec] = L.apply(f).cpu().numpy()
         res[prec] = {"ms": ms, "mnodes_per_s": n / (ms * 1e-3) / 1e6}
     res["speedup_mixed_over_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+    res["speedup_mixed_tc_over_fp64"] = res["fp64"]["ms"] / res["mixed_tc"]["ms"]
     res["ops"] = list(ops)
     res["deriv_err_mixed_vs_fp64"] = deriv_errors(ders["mixed"], ders["fp64"])
+    res["deriv_err_mixed_tc_vs_fp64"] = deriv_errors(ders["mixed_tc"], ders["fp64"])
     res["nref"] = 1
     L.close()
     return res
@@ -416,7 +418,7 @@ def walls_variable_order(torch, P, dev, local_rank, n_side=1000):
     status = torch.zeros(n, dtype=torch.int32, device=dev)
     res = {"nodes": n, "nnz": int(L.nnz), "order_counts": {int(k): int(v) for k, v in
                                                            zip(*np.unique(ns.order, return_counts=True))}}
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "mixed_tc"):
         L.build_weights(C, order=order, precision=prec, node_status=status)
         ms = _time(torch, lambda: L.build_weights(C, order=order, precision=prec, node_status=status), reps=2)
         st = status.cpu().numpy()
@@ -585,7 +587,7 @@ def run_labfm(args, rank, world, local_rank):
 
 
 PROFILE_CASES = ("apply_f32_512", "apply_f64_512", "stage_df_1024", "stage_f32_1024", "build_fp64_256",
-                 "build_mixed_256")
+                 "build_mixed_256", "build_mixed_tc_256")
 
 
 def profile_case(name):
@@ -603,7 +605,7 @@ def profile_case(name):
         C = np.stack([S.op_c_vector(o, K) for o in OPS])
         L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), True)
         wdt = "f32" if name == "apply_f32_512" else "f64"
-        prec = "mixed" if name == "build_mixed_256" else "fp64"
+        prec = {"build_mixed_256": "mixed", "build_mixed_tc_256": "mixed_tc"}.get(name, "fp64")
         for _ in range(1 if name.startswith("apply") else 3):
             L.build_weights(C, uniform_order=K, precision=prec, weight_dtype=wdt)
         if name.startswith("apply"):

@@ -74,10 +74,17 @@ enum {
      * (pairs of FP32, ~48 bits, on the FP32 pipes); then iterative refinement on the
      * polynomial-reproduction residual C - sum_j X_j w_j computed in double (the moment
      * conditions of Sec. 2.1).  Default: 1 refinement step. */
-    LABFM_PREC_MIXED = 1
+    LABFM_PREC_MIXED = 1,
+    /* As LABFM_PREC_MIXED, with M formed on the tensor cores: X and W are scaled per row (a power
+     * of two per chunk of <= 64 neighbours) and cut into seven 8-bit BF16 slices; the slice
+     * products of each level a + b = 2..8 are summed exactly in FP32 (tcgen05.mma, accumulators
+     * in tensor memory) and combined in double-float. */
+    LABFM_PREC_MIXED_TC = 2
 };
 /* LABFM_PREC_MIXED with exactly n refinement steps, n = 0..4 */
 #define LABFM_PREC_MIXED_REFINE(n) (LABFM_PREC_MIXED | (((n) + 1) << 8))
+/* LABFM_PREC_MIXED_TC with exactly n refinement steps, n = 0..4 */
+#define LABFM_PREC_MIXED_TC_REFINE(n) (LABFM_PREC_MIXED_TC | (((n) + 1) << 8))
 
 /* Storage type of weights and fields. */
 enum { LABFM_F64 = 0, LABFM_F32 = 1 };
@@ -155,7 +162,8 @@ labfm_status labfm_get_neighbours(labfm_ctx *ctx, const int64_t **row_ptr, const
  *   n_bad_out    host, receives the number of flagged nodes (may be NULL)
  * Flagged nodes get zero weights.  Returns LABFM_ERR_SINGULAR if any node was
  * flagged (the weights of all other nodes are valid), LABFM_ERR_STATE if no
- * stencils were built.
+ * stencils were built, LABFM_ERR_TIMEOUT if a bounded wait for the tensor cores
+ * (LABFM_PREC_MIXED_TC) gave up (the weights are then undefined).
  */
 labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf,
                                  int n_ops, const double *C, int precision, int weight_dtype,

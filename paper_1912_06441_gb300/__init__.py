@@ -19,16 +19,16 @@ from .build import LIB as _LIB_PATH, build_library
 __all__ = ["Labfm", "LabfmError", "load_library", "RBF", "PREC", "DTYPE", "NODE", "C_FUNCTIONS"]
 
 RBF = {"wendland_c2": 0, "quadratic": 1, "cone": 2, "wendland_c6": 3, "gaussian": 4}
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "mixed_tc": 2}
 ABF_FORM = {"chain": 0, "dw0": 0x100}  # LABFM_ABF_DW0_ONLY: every ABF element is dW0/dr d^alpha|r|
 
 
 def precision_code(precision: str, refine: int | None = None) -> int:
-    """C ABI precision value: LABFM_PREC_FP64, LABFM_PREC_MIXED or LABFM_PREC_MIXED_REFINE(refine)."""
+    """C ABI precision value: LABFM_PREC_FP64, LABFM_PREC_MIXED[_TC] or LABFM_PREC_MIXED[_TC]_REFINE(refine)."""
     code = PREC[precision]
     if refine is not None:
-        if precision != "mixed" or not 0 <= refine <= 4:
-            raise ValueError("refine applies to precision='mixed', 0..4 steps")
+        if precision not in ("mixed", "mixed_tc") or not 0 <= refine <= 4:
+            raise ValueError("refine applies to precision='mixed' or 'mixed_tc', 0..4 steps")
         code |= (refine + 1) << 8
     return code
 DTYPE = {"f64": 0, "f32": 1}

@@ -286,7 +286,9 @@ labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int unifor
         if (!std::isfinite(C[t])) return fail(ctx, LABFM_ERR_ARG, "C has a non-finite entry");
     {
         int base = precision & 0xff, forced = (precision >> 8) & 0xf, rest = precision >> 12;
-        bool ok = rest == 0 && (base == LABFM_PREC_FP64 ? forced == 0 : (base == LABFM_PREC_MIXED && forced <= 5));
+        bool ok = rest == 0 && (base == LABFM_PREC_FP64
+                                    ? forced == 0
+                                    : ((base == LABFM_PREC_MIXED || base == LABFM_PREC_MIXED_TC) && forced <= 5));
         if (!ok) return fail(ctx, LABFM_ERR_ARG, "unknown precision");
     }
     if (weight_dtype != LABFM_F64 && weight_dtype != LABFM_F32) return fail(ctx, LABFM_ERR_ARG, "bad weight_dtype");

@@ -355,7 +355,8 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
 {
     cudaStream_t s = ctx->stream;
     const int64_t n = ctx->n;
-    const bool mixed = (precision & 0xff) == LABFM_PREC_MIXED;
+    const int base_prec = precision & 0xff;
+    const bool mixed = base_prec == LABFM_PREC_MIXED || base_prec == LABFM_PREC_MIXED_TC;
     size_t wbytes = (size_t)ctx->nnz * n_ops * (weight_dtype == LABFM_F64 ? 8 : 4);
     LABFM_CUDA_TRY(ctx, ctx->w.reserve(wbytes > 0 ? wbytes : 8));
     if (mixed) LABFM_CUDA_TRY(ctx, ctx->wtilde.reserve((size_t)ctx->nnz * n_ops * 8 + 8));
@@ -401,6 +402,8 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         m.node_status = node_status;
         m.n_bad = dmisc;
         m.num_sms = ctx->num_sms;
+        m.tc = base_prec == LABFM_PREC_MIXED_TC;
+        m.tc_timeout = dmisc + 30;
         for (int t = 0; t < n_ops * PMAX; t++) m.C[t] = Cin[t];
         for (int d = 0; d < n_ops; d++) {
             int l = 0;
@@ -457,8 +460,9 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
             LABFM_CUDA_TRY(ctx, launch(k, list + base[k], (int64_t)cnt[k]));
         }
     }
-    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, 32 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hs[30]) return fail(ctx, LABFM_ERR_TIMEOUT, "a tensor-core completion wait gave up");
     int64_t nbad = (int64_t)hs[0];
     if (n_bad_out) *n_bad_out = nbad;
     if (nbad) return fail(ctx, LABFM_ERR_SINGULAR, std::to_string(nbad) + " node(s) flagged");

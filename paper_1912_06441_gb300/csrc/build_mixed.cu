@@ -16,6 +16,8 @@
 // transform as the FP64 build (exact in exact arithmetic).
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "abf.cuh"
 #include "df64.cuh"
 
@@ -86,6 +88,7 @@ struct MixedArgs {
     df *Mg;             // [n_list][P][P] scratch: M, then M^-1
     int *flag;          // [n_list] scratch: per-node failure bits
     Rec *recs;          // [nnz] per-entry preamble (k_mixed_records)
+    unsigned long long *tc_timeout;  // tensor-core assembly: waits that gave up
     int32_t *node_status;
     unsigned long long *n_bad;
     int lmax[MAX_OPS];
@@ -357,6 +360,328 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_assemble(MixedArgs A)
         __syncthreads();
         if (tid == 0) A.flag[li] = s_bad;
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// A': M on the tensor cores (tcgen05), exact in BF16 slices.
+//
+// Every X_alpha(j) and W_beta(j) of a chunk of <= 64 neighbours is scaled by a power of two
+// common to its row over the chunk, 2^-e, e = the exponent of the row's largest magnitude, and
+// cut into NSL = 7 BF16 slices of 8 bits:
+//     v 2^-e = sum_{s=1..7} c_s 2^-8s,   c_1 in [-256, 256], c_s in [-128, 128] (s > 1),
+// integers, so exact in BF16 (8 significant bits), with |remainder| <= 2^-57 (relative to the
+// row's largest value; a value far below it keeps fewer bits, hence seven slices rather than
+// six: order-8 rows span up to ~2^20 across a stencil).  For each level t = a + b (2..8) the
+// products of slices a of X and b of W over the chunk are summed on the tensor cores into one
+// FP32 accumulator per level:
+//     D_t[alpha][beta] = sum_{a + b = t} sum_j cX_a[alpha](j) cW_b[beta](j),
+// every partial sum an integer of magnitude <= 64 (2 * 256 * 128 + 5 * 128 * 128) < 2^24, so
+// the FP32 accumulation is exact.  Then M[alpha][beta] = 2^(eX + eW) sum_t D_t 2^-8t in
+// double-float (levels >= 9 lie below 2^-56 of the leading one and are not formed).
+//
+// Operands sit in shared memory in the K-major core-matrix layout without swizzle (8 rows x 16
+// bytes per core matrix; K-adjacent core matrices 128 B apart, 8-row groups 1 KB apart for a
+// 64-deep chunk).  A = X slice (rows alpha, M = 128: rows >= p are don't-care), B = W slice
+// (rows beta, N = p rounded up to 16), K = neighbours.  Accumulators D_t live in tensor memory
+// (lane = alpha, column = (t - t0) N + beta); the CTA holds 256 columns, two CTAs per SM.
+// ------------------------------------------------------------------------------------------
+constexpr int TC_THREADS = 256;
+constexpr int NSL = 7;          // slices per operand
+constexpr int TC_KC = 64;       // neighbours per chunk (the K of one pass)
+constexpr int TC_ROWB = TC_KC / 8 * 128;  // bytes per 8-row group of an operand slice
+constexpr int TC_TMEM_COLS = 256;
+
+template <int K> struct TcCfg {
+    static constexpr int P = p_of_k(K);
+    static constexpr int PN = (P + 15) / 16 * 16;        // N of one level (columns)
+    static constexpr int RA = (P + 7) / 8 * 8;           // rows stored per X slice
+    static constexpr int SA = RA / 8 * TC_ROWB;          // bytes per X slice
+    static constexpr int SB = PN / 8 * TC_ROWB;          // bytes per W slice
+    static constexpr int A_BYTES = (NSL - 1) * SA + 16 * TC_ROWB;  // the last slice's 128-row window
+    static constexpr int B_BYTES = NSL * SB;
+    // levels per tensor-memory round: the columns fit the allocation, and the exact int64
+    // combination of a round's levels (each < 2^24, 8 bits apart) stays below 2^63
+    static constexpr int LPR = TC_TMEM_COLS / PN < 5 ? TC_TMEM_COLS / PN : 5;
+    static constexpr int LDS = P;                        // row stride (df) of the staging arrays
+    static constexpr size_t smem = (size_t)A_BYTES + B_BYTES + 8 * (size_t)P * P + 16;
+    static_assert((size_t)TC_KC * LDS * 8 <= (size_t)A_BYTES && (size_t)TC_KC * LDS * 8 <= (size_t)B_BYTES,
+                  "staging fits the operand regions");
+    static_assert(P <= 64, "rows alpha in the first two lane quadrants");
+};
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, no swizzle, LBO = 128 B (K direction), SBO = 1 KB
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(TC_ROWB >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t tc_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, int accumulate)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                 "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 20); it++) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity));
+        if (done) return true;
+    }
+    return false;
+}
+
+// 2^e as a float for |e| <= 126 (clamped: values beyond lie outside the double-float range)
+__device__ __forceinline__ float tc_pow2(int e)
+{
+    e = max(-126, min(127, e));
+    return __int_as_float((e + 127) << 23);
+}
+
+// exponent e with |v| < 2^e for every v of magnitude <= m (m = max |hi| of a row), 0 for m = 0
+__device__ __forceinline__ int tc_row_exp(float m) { return m > 0.0f ? ilogbf(m) + 1 : 0; }
+
+// byte offset of element (row r, k) in a K-major core-matrix slice
+__device__ __forceinline__ int tc_off(int r, int k) { return (r >> 3) * TC_ROWB + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+template <int K>
+__global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A)
+{
+    using C = TcCfg<K>;
+    constexpr int P = C::P, PN = C::PN, LDS = C::LDS;
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    unsigned char *sA = smem_tc;                      // X slices (and the X staging)
+    unsigned char *sB = smem_tc + C::A_BYTES;         // W slices (and the W staging)
+    df *sM = reinterpret_cast<df *>(sB + C::B_BYTES);  // M of the node, accumulated over chunks
+    df *Xst = reinterpret_cast<df *>(sA);
+    df *Wst = reinterpret_cast<df *>(sB);
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ uint32_t s_max[2 * P];  // per-row max |hi| of X (0..P-1) and W (P..2P-1) over the chunk
+    __shared__ int s_e[2 * P];          // the rows' scaling exponents
+    __shared__ int s_bad, s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&s_mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(&s_tmem)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+    const uint32_t mbar = tc_smem_u32(&s_mbar);
+    uint32_t phase = 0;
+
+    // epilogue role: warps 0, 1, 4, 5 read lane quadrants 0 and 1 (alpha = lane + 32 q);
+    // warps w and w + 4 take the two halves of the beta columns
+    const int q = warp & 3, half = warp >> 2;
+    const int alpha = 32 * q + lane;
+    const bool epi = q < 2;
+
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
+        const int64_t i = node_of(A, li);
+        const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
+        const int ni = (int)(re - rs);
+        if (ni < P) {
+            mark_undersampled(A, li, i, rs, ni);
+            continue;
+        }
+        if (tid == 0) s_bad = 0;
+        for (int j0 = 0; j0 < ni; j0 += TC_KC) {
+            const int nj = min(TC_KC, ni - j0);
+            const int ksteps = (nj + 15) / 16;
+            // 1. X and W of the chunk in double-float (PARTS threads per neighbour)
+            if (tid < 2 * P) s_max[tid] = 0u;
+            for (int t = tid; t < TC_KC * PARTS; t += TC_THREADS) {
+                const int part = t / TC_KC, jj = t - part * TC_KC;
+                if (jj < nj)
+                    eval_xw_part<K>(A.recs[rs + j0 + jj].v, part, Xst + jj * LDS, Wst + jj * LDS);
+            }
+            __syncthreads();
+            // 2. octets (row r of one operand, 8 consecutive neighbours) to registers, and the
+            //    row maxima of |hi| (as ordered bit patterns: non-negative floats compare as integers)
+            constexpr int NOCT = 2 * P * (TC_KC / 8);
+            constexpr int PER = (NOCT + TC_THREADS - 1) / TC_THREADS;
+            df val[PER][8];
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                const int o = tid + u * TC_THREADS;
+                const int opnd = o / (P * (TC_KC / 8)), rem = o - opnd * (P * (TC_KC / 8));
+                const int r = rem % P, oct = rem / P;
+                uint32_t m = 0u;
+#pragma unroll
+                for (int c = 0; c < 8; c++) {
+                    const int jj = 8 * oct + c;
+                    val[u][c] = (o < NOCT && jj < nj) ? (opnd == 0 ? Xst : Wst)[jj * LDS + r] : df{0.0f, 0.0f};
+                    m = max(m, __float_as_uint(fabsf(val[u][c].hi)));  // NaN and inf sort above finite
+                }
+                if (o < NOCT && m) atomicMax(&s_max[opnd * P + r], m);
+            }
+            __syncthreads();
+            // 3. slices -> BF16 operands, one 16-byte core-matrix row (8 neighbours) per store;
+            //    K positions nj .. 16 ksteps - 1 are zero
+            if (tid < 2 * P) {
+                const uint32_t mb = s_max[tid];
+                s_e[tid] = tc_row_exp(mb >= 0x7f800000u ? 0.0f : __uint_as_float(mb));
+            }
+#pragma unroll
+            for (int u = 0; u < PER; u++) {
+                const int o = tid + u * TC_THREADS;
+                const int opnd = o / (P * (TC_KC / 8)), rem = o - opnd * (P * (TC_KC / 8));
+                const int r = rem % P, oct = rem / P;
+                if (o >= NOCT || 8 * oct >= 16 * ksteps) continue;
+                const uint32_t mb = s_max[opnd * P + r];
+                if (mb >= 0x7f800000u) s_bad = 4;  // a neighbour on top of node i: singular ABFs
+                const float sc = tc_pow2(-tc_row_exp(mb >= 0x7f800000u ? 0.0f : __uint_as_float(mb)));
+                float rh[8], rl[8];
+#pragma unroll
+                for (int c = 0; c < 8; c++) {
+                    rh[c] = val[u][c].hi * sc;
+                    rl[c] = val[u][c].lo * sc;
+                }
+                unsigned char *base = (opnd == 0 ? sA : sB) + tc_off(r, 8 * oct);
+                const int sstride = opnd == 0 ? C::SA : C::SB;
+#pragma unroll
+                for (int sl = 1; sl <= NSL; sl++) {
+                    const float up = tc_pow2(8 * sl), dn = tc_pow2(-8 * sl);
+                    uint32_t packed[4];
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2) {
+                        const float c0 = rintf(rh[c] * up), c1 = rintf(rh[c + 1] * up);  // integers, |c| <= 256
+                        two_sum(__fsub_rn(rh[c], c0 * dn), rl[c], rh[c], rl[c]);          // exact remainders
+                        two_sum(__fsub_rn(rh[c + 1], c1 * dn), rl[c + 1], rh[c + 1], rl[c + 1]);
+                        __nv_bfloat162 pr = __floats2bfloat162_rn(c0, c1);
+                        packed[c / 2] = *reinterpret_cast<uint32_t *>(&pr);
+                    }
+                    *reinterpret_cast<uint4 *>(base + (sl - 1) * sstride) =
+                        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            // 4. per round of levels: issue, wait, read out
+            for (int t0 = 2; t0 <= NSL + 1 && !s_abort; t0 += C::LPR) {
+                const int t1 = min(NSL + 1, t0 + C::LPR - 1);
+                asm volatile("tcgen05.fence::after_thread_sync;");  // the last read-out is complete
+                if (tid == 0) {
+                    uint64_t ad[NSL], bd[NSL];
+                    const uint32_t a0 = tc_smem_u32(sA), b0 = tc_smem_u32(sB);
+#pragma unroll
+                    for (int sl = 0; sl < NSL; sl++) {
+                        ad[sl] = tc_desc(a0 + sl * C::SA);
+                        bd[sl] = tc_desc(b0 + sl * C::SB);
+                    }
+                    // one MMA per (X slice a, K step): B = the W slices b_lo .. b_hi that pair with a
+                    // inside the round (adjacent rows), D shifted so that column block b lands in
+                    // level a + b's accumulator.  a = 1 covers every level of the round, so its
+                    // first K step initialises all of them.
+                    for (int a = 1; a <= NSL && a < t1; a++) {
+                        const int b_lo = max(1, t0 - a), b_hi = min(NSL, t1 - a);
+                        if (b_lo > b_hi) continue;
+                        const uint32_t idesc = tc_idesc((b_hi - b_lo + 1) * PN);
+                        const uint32_t dcol = (uint32_t)((a + b_lo - t0) * PN);
+                        for (int ks = 0; ks < ksteps; ks++)  // +256 B per K step = +16 in the address field
+                            tc_mma(tmem + dcol, ad[a - 1] + (uint64_t)(16 * ks), bd[b_lo - 1] + (uint64_t)(16 * ks),
+                                   idesc, (a == 1 && ks == 0) ? 0 : 1);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        mbar));
+                }
+                const bool ok = tc_wait(mbar, phase);
+                phase ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (!ok) {
+                    if (tid == 0) {
+                        s_abort = 1;
+                        atomicAdd(A.tc_timeout, 1ull);
+                    }
+                } else if (epi) {
+                    // thread (alpha, half): M[alpha][beta] for its half of the beta columns,
+                    // accumulated over the rounds and chunks in shared memory.  The levels of a
+                    // round are exact integers < 2^24: S = sum_t D_t 2^(8 (t1 - t)) is exact in
+                    // int64 (< 2^57), and M += 2^(eX + eW - 8 t1) S.
+                    const bool own = alpha < P;
+                    constexpr int HB = PN / 2;  // columns per half
+                    df *Mrow = sM + (own ? alpha : 0) * P;
+                    const int ex = s_e[own ? alpha : 0] - 8 * t1;
+                    for (int g = 0; g < HB; g += 8) {
+                        // all levels of this round for 8 columns: issue the loads, then one wait
+                        uint32_t v[C::LPR][8];
+#pragma unroll
+                        for (int l = 0; l < C::LPR; l++) {
+                            if (t0 + l <= t1) {
+                                asm volatile(
+                                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                    : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
+                                      "=r"(v[l][5]), "=r"(v[l][6]), "=r"(v[l][7])
+                                    : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(l * PN + half * HB + g)));
+                            }
+                        }
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (own) {
+#pragma unroll
+                            for (int c = 0; c < 8; c++) {
+                                const int beta = half * HB + g + c;
+                                if (beta >= P) continue;
+                                long long S = 0;
+#pragma unroll
+                                for (int l = 0; l < C::LPR; l++)
+                                    if (t0 + l <= t1) S = S * 256 + (long long)__float2int_rn(__uint_as_float(v[l][c]));
+                                // S = H 2^32 + L1 2^16 + L0, |H| < 2^25, L1, L0 < 2^16: three exact floats
+                                const int H = (int)(S >> 32);
+                                const uint32_t L = (uint32_t)S;
+                                float sh, sl;
+                                two_sum((float)H * 4294967296.0f, (float)(L >> 16) * 65536.0f, sh, sl);
+                                sl = __fadd_rn(sl, (float)(L & 0xffffu));
+                                fast_two_sum(sh, sl, sh, sl);
+                                const float sc = tc_pow2(ex + s_e[P + beta]);
+                                const df add = df{sh * sc, sl * sc};
+                                Mrow[beta] = (j0 == 0 && t0 == 2) ? add : df_add(Mrow[beta], add);
+                            }
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();
+            }
+            if (s_abort) break;
+        }
+        if (s_abort) break;
+        // M of the node -> global
+        df *Mg = A.Mg + li * (int64_t)P * P;
+        bool finite = true;
+        for (int u = tid; u < P * P; u += TC_THREADS) {
+            const df v = sM[u];
+            finite &= df_isfinite(v);
+            Mg[u] = v;
+        }
+        if (!finite) s_bad = 4;
+        __syncthreads();
+        if (tid == 0) A.flag[li] = s_bad;
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -645,13 +970,14 @@ __global__ void __launch_bounds__(MIX_THREADS, 2) k_mixed_weights(MixedArgs A)
 
 template <class KernelT>
 cudaError_t launch_persistent(KernelT kern, const MixedArgs &a, int threads, size_t smem, int64_t units, int num_sms,
-                              cudaStream_t s)
+                              cudaStream_t s, int max_per_sm = 1 << 30)
 {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
+    if (per_sm > max_per_sm) per_sm = max_per_sm;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = std::min<int64_t>(units, (int64_t)num_sms * per_sm);
     if (grid < 1) return cudaSuccess;
@@ -660,7 +986,7 @@ cudaError_t launch_persistent(KernelT kern, const MixedArgs &a, int threads, siz
 }
 
 template <int K>
-cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, cudaStream_t s)
+cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, bool tc, cudaStream_t s)
 {
     using C = MCfg<K>;
     {
@@ -669,7 +995,23 @@ cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, cudaStream_t s)
         cudaError_t e0 = cudaGetLastError();
         if (e0 != cudaSuccess) return e0;
     }
-    cudaError_t e = launch_persistent(k_mixed_assemble<K>, a, MIX_THREADS, C::smemA, a.n_list, num_sms, s);
+    cudaError_t e;
+    if (tc) {
+        // two CTAs per SM, each holding TC_TMEM_COLS of the 512 tensor-memory columns for its
+        // whole run: the shared-memory request (>= 80 KB) keeps a third CTA off the SM
+        const size_t smem = std::max<size_t>(TcCfg<K>::smem, 80 * 1024);
+        e = cudaFuncSetAttribute(k_mixed_assemble_tc<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_mixed_assemble_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        // two CTAs per SM by construction (<= 113 KB of shared memory and 32 K registers each)
+        const int64_t grid = std::min<int64_t>(a.n_list, 2 * (int64_t)num_sms);
+        if (grid > 0) k_mixed_assemble_tc<K><<<(unsigned)grid, TC_THREADS, smem, s>>>(a);
+        e = cudaGetLastError();
+    } else {
+        e = launch_persistent(k_mixed_assemble<K>, a, MIX_THREADS, C::smemA, a.n_list, num_sms, s);
+    }
     if (e != cudaSuccess) return e;
     e = launch_persistent(k_mixed_invert<K>, a, INV_THREADS, 0, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
@@ -707,6 +1049,7 @@ cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
     a.node_status = p.node_status;
     a.n_bad = p.n_bad;
     a.recs = reinterpret_cast<Rec *>(p.recs);
+    a.tc_timeout = p.tc_timeout;
     for (int d = 0; d < MAX_OPS; d++) a.lmax[d] = p.lmax[d];
     for (int t = 0; t < MAX_OPS * PMAX; t++) a.C[t] = p.C[t];
     const int pk = p_of_k(k);
@@ -720,14 +1063,14 @@ cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
         a.flag = reinterpret_cast<int *>(reinterpret_cast<char *>(p.scratch) + sizeof(df) * (size_t)pk * pk * batch);
         cudaError_t e;
         switch (k) {
-        case 1: e = launch_mixed_k<1>(a, p.num_sms, s); break;
-        case 2: e = launch_mixed_k<2>(a, p.num_sms, s); break;
-        case 3: e = launch_mixed_k<3>(a, p.num_sms, s); break;
-        case 4: e = launch_mixed_k<4>(a, p.num_sms, s); break;
-        case 5: e = launch_mixed_k<5>(a, p.num_sms, s); break;
-        case 6: e = launch_mixed_k<6>(a, p.num_sms, s); break;
-        case 7: e = launch_mixed_k<7>(a, p.num_sms, s); break;
-        default: e = launch_mixed_k<8>(a, p.num_sms, s); break;
+        case 1: e = launch_mixed_k<1>(a, p.num_sms, p.tc != 0, s); break;
+        case 2: e = launch_mixed_k<2>(a, p.num_sms, p.tc != 0, s); break;
+        case 3: e = launch_mixed_k<3>(a, p.num_sms, p.tc != 0, s); break;
+        case 4: e = launch_mixed_k<4>(a, p.num_sms, p.tc != 0, s); break;
+        case 5: e = launch_mixed_k<5>(a, p.num_sms, p.tc != 0, s); break;
+        case 6: e = launch_mixed_k<6>(a, p.num_sms, p.tc != 0, s); break;
+        case 7: e = launch_mixed_k<7>(a, p.num_sms, p.tc != 0, s); break;
+        default: e = launch_mixed_k<8>(a, p.num_sms, p.tc != 0, s); break;
         }
         if (e != cudaSuccess) return e;
     }

@@ -119,6 +119,8 @@ struct MixedArgsPublic {
     int64_t batch_nodes;  // nodes per batch; `scratch` holds batch_nodes * mixed_scratch_bytes_per_node(k)
     void *scratch;
     void *recs;  // [nnz] per-entry records, mixed_record_bytes() each
+    int tc;      // 1: moment matrices on the tensor cores (exact BF16 slices), 0: double-float
+    unsigned long long *tc_timeout;  // device counter of tensor-core waits that gave up
 };
 cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s);
 size_t mixed_scratch_bytes_per_node(int k);

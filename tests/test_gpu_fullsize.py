@@ -60,7 +60,7 @@ def _check_apply_all_nodes(L, rp, col, w, f):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_tc"])
 def test_lattice512_order8(precision):
     k, ops = 8, ("dx", "dy", "lap", "lap4")
     ns = S.jittered_lattice(512, 2.2, k, jitter=0.3, seed=2)
@@ -97,7 +97,7 @@ def test_lattice512_order6_and_fp32_apply():
     assert np.all(np.abs(f32 - full) <= 64 * 2.0 ** -24 * bound + 2.0 ** -24 * np.abs(full))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_tc"])
 def test_walls_1m_variable_order(precision):
     ns = S.variable_wall_nodes(1000, seed=4)
     ops = ("dx", "dy", "lap")

@@ -1,0 +1,128 @@
+"""Parity of the mixed-precision build with M formed on the tensor cores (LABFM_PREC_MIXED_TC:
+exact BF16 slice products per level, tcgen05.mma with accumulators in tensor memory) with the
+oracle, under the same floor-aware tolerance as the FP64 build."""
+import numpy as np
+import pytest
+
+import labfm_synth as S
+import oracle
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+PREC = "mixed_tc"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1912_06441_gb300 as P
+
+    P.load_library()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_tc_weights_parity_by_order(k):
+    ns = S.jittered_lattice(37, G.HS[k], k, seed=10 + k)
+    ops = G.OPS[k]
+    _, rp, col, w, status, _ = G.gpu_run(ns, k, ops, precision=PREC)
+    q = np.arange(0, ns.n, 3)
+    rp_q, col_q, idx = G.rows_of(rp, col, q)
+    r64, rld = G.oracle_refs(ns, k, ops, q, rp_q, col_q)
+    assert np.array_equal(status[q], r64["status"])
+    G.assert_weights_parity(w[idx], r64, rld, rp_q, label=f"mixed_tc k={k}")
+
+
+def test_tc_refinement_reaches_the_fp64_floor():
+    """Without refinement the solution carries the ~48-bit error of M and of the double-float
+    solve amplified by cond(M) ~ 1e12; one step on the FP64 residual brings it to the floor."""
+    k = 8
+    ns = S.jittered_lattice(32, G.HS[k], k, seed=18)
+    ops = G.OPS[k]
+    q = np.arange(0, ns.n, 3)
+    med = []
+    for nref in (0, 1, 2):
+        _, rp, col, w, status, _ = G.gpu_run(ns, k, ops, precision=PREC, refine=nref)
+        rp_q, col_q, idx = G.rows_of(rp, col, q)
+        if nref == 0:
+            r64, rld = G.oracle_refs(ns, k, ops, q, rp_q, col_q)
+            ok = (r64["status"] == 0) & (rld["status"] == 0)
+            floor = np.median(G.node_rel_err(r64["w"], rld["w"], rp_q)[ok])
+        med.append(np.median(G.node_rel_err(w[idx], rld["w"], rp_q)[ok]))
+    assert med[1] < med[0] and med[2] <= med[1] * 1.5, med
+    assert med[2] <= max(G.TOL_FLOOR_MEDIAN, G.FLOOR_FACTOR * floor), (med, floor)
+
+
+def test_tc_variable_order_and_walls():
+    ns = S.variable_wall_nodes(40, seed=4)
+    ops = ("dx", "dy", "lap")
+    _, rp, col, w, status, _ = G.gpu_run(ns, 8, ops, order=ns.order, precision=PREC)
+    q = np.arange(0, ns.n, 3)
+    rp_q, col_q, idx = G.rows_of(rp, col, q)
+    r64, rld = G.oracle_refs(ns, 8, ops, q, rp_q, col_q, order=ns.order)
+    assert np.array_equal(status[q], r64["status"])
+    G.assert_weights_parity(w[idx], r64, rld, rp_q, label="mixed_tc variable order")
+
+
+@pytest.mark.parametrize("k,hs", [(4, 3.0), (8, 2.7)])
+def test_tc_multi_chunk_stencils(k, hs):
+    """More than 64 neighbours: several K chunks, each with its own row scaling, summed in
+    double-float."""
+    ns = S.jittered_lattice(40, hs, k, seed=31)
+    ops = G.OPS[k]
+    _, rp, col, w, status, _ = G.gpu_run(ns, k, ops, precision=PREC)
+    assert np.diff(rp).min() > 64
+    q = np.arange(0, ns.n, 5)
+    rp_q, col_q, idx = G.rows_of(rp, col, q)
+    r64, rld = G.oracle_refs(ns, k, ops, q, rp_q, col_q)
+    G.assert_weights_parity(w[idx], r64, rld, rp_q, label=f"mixed_tc chunked k={k}")
+
+
+def test_tc_dw0_form():
+    k = 8
+    ns = S.jittered_lattice(36, 2.2, k, seed=58, jitter=0.2)
+    ops = G.OPS[k]
+    _, rp, col, w, status, _ = G.gpu_run(ns, k, ops, rbf="quadratic", precision=PREC, abf_form="dw0")
+    q = np.arange(2, ns.n, 3)
+    rp_q, col_q, idx = G.rows_of(rp, col, q)
+    r64, rld = G.oracle_refs(ns, k, ops, q, rp_q, col_q, rbf="quadratic", abf_form="dw0")
+    assert np.array_equal(status[q], r64["status"])
+    G.assert_weights_parity(w[idx], r64, rld, rp_q, label="mixed_tc dw0")
+
+
+def test_tc_status_codes_match_oracle():
+    xs = np.linspace(0.3, 0.7, 21)
+    line = np.stack([xs, np.full_like(xs, 0.5)], 1)
+    sparse = np.array([[0.1, 0.1], [0.12, 0.1], [0.1, 0.13]])
+    dup = np.array([[0.8, 0.8], [0.8, 0.8]])
+    rng = S.uniform01(77, 40).reshape(20, 2) * 0.08 + 0.76
+    xy = np.concatenate([line, sparse, dup, rng])
+    h = np.full(len(xy), 0.06)
+    ns = S.NodeSet(xy=xy, h=h, s=h, order=np.full(len(xy), 2, np.int8), periodic=False, lo=(0.0, 0.0),
+                   hi=(1.0, 1.0))
+    ops = ("dx", "dy", "lap")
+    _, rp, col, w, status, nbad = G.gpu_run(ns, 2, ops, precision=PREC)
+    r64 = oracle.build_weights(ns.xy, ns.h, False, rp, col, G.c_matrix(2, ops), k=2, queries=np.arange(ns.n))
+    assert np.array_equal(status, r64["status"])
+    for t in np.nonzero(status)[0]:
+        assert np.all(w[rp[t]:rp[t + 1]] == 0)
+
+
+def test_tc_matches_double_float_assembly():
+    """The two mixed builds differ only in how M is formed (both ~48 bits); after refinement
+    their derivatives agree with the FP64 build's to 1e-8 (order 6)."""
+    import torch
+
+    k = 6
+    ns = S.jittered_lattice(64, G.HS[k], k, seed=2)
+    ops = G.OPS[k]
+    f = S.fourier_field(16, 8, seed=3).value(ns.xy)
+    dev = torch.device("cuda", 0)
+    outs = []
+    for prec in ("fp64", "mixed", PREC):
+        L, rp, col, w, status, _ = G.gpu_run(ns, k, ops, precision=prec)
+        outs.append(L.apply(torch.from_numpy(f).to(dev)).cpu().numpy())
+    for o in outs[1:]:
+        err = np.linalg.norm(o - outs[0], axis=1) / np.linalg.norm(outs[0], axis=1)
+        assert np.all(err < 1e-8), err
