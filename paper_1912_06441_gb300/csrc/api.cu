@@ -219,7 +219,7 @@ void labfm_destroy(labfm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->node_xy, &ctx->node_h, &ctx->row_ptr, &ctx->col, &ctx->cell_of, &ctx->cell_count, &ctx->cell_start,
                       &ctx->cell_nodes, &ctx->counts, &ctx->scan_tmp, &ctx->misc, &ctx->w,
-                      &ctx->status_tmp, &ctx->wtilde, &ctx->mscratch, &ctx->mrecs, &ctx->wcomb, &ctx->rk_acc,
+                      &ctx->status_tmp, &ctx->wtilde, &ctx->mscratch, &ctx->mrecs, &ctx->mwstore, &ctx->wcomb, &ctx->rk_acc,
                       &ctx->rk_stage_a, &ctx->rk_stage_b};
     for (DevBuf *b : bufs) b->release();
     ctx->graph.release();

@@ -429,6 +429,14 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         e = ctx->mrecs.reserve(mixed_record_bytes() * (size_t)ctx->nnz + 256);
         if (e != cudaSuccess) return e;
         m.recs = ctx->mrecs.ptr;
+        // W of every entry, kept from the assembly for the weights kernel (8 bytes per element);
+        // above 24 GB the weights kernel evaluates W again instead
+        const size_t wbytes_k = (size_t)8 * p_of_k(k) * (size_t)ctx->nnz;
+        m.wstore = nullptr;
+        if (wbytes_k <= ((size_t)24 << 30) && ctx->mwstore.reserve(wbytes_k + 256) == cudaSuccess)
+            m.wstore = ctx->mwstore.ptr;
+        else
+            cudaGetLastError();  // a failed reservation only disables the store
         return launch_build_mixed(k, m, s);
     };
 

@@ -30,7 +30,9 @@ constexpr int NREC = 8;             // per-neighbour record: q, 1/q, u, v, W0', 
 
 template <int K> struct MCfg {
     static constexpr int P = p_of_k(K);
-    static constexpr int LDX = (P + 3) / 4 * 4;
+    // row stride (df) of the per-neighbour arrays: even (16-byte rows for the vector loads) and
+    // 2 mod 4, so that 8-byte accesses of consecutive neighbours conflict at most 2-way
+    static constexpr int LDX = ((P + 1) / 2 * 2) % 4 == 0 ? (P + 1) / 2 * 2 + 2 : (P + 1) / 2 * 2;
     static constexpr int NB = K >= 7 ? 72 : 64;
     static_assert(NB * PARTS <= MIX_THREADS, "one evaluation pass per chunk");
     static constexpr int TM = 2, TN = 4;
@@ -88,6 +90,8 @@ struct MixedArgs {
     df *Mg;             // [n_list][P][P] scratch: M, then M^-1
     int *flag;          // [n_list] scratch: per-node failure bits
     Rec *recs;          // [nnz] per-entry preamble (k_mixed_records)
+    df *wstore;         // [nnz][P] W of every entry in double-float, written by the assembly and
+                        // read by the weights kernel; null: the weights kernel evaluates W again
     unsigned long long *tc_timeout;  // tensor-core assembly: waits that gave up
     int32_t *node_status;
     unsigned long long *n_bad;
@@ -263,9 +267,18 @@ __device__ __forceinline__ void stage_chunk(const MixedArgs &A, int64_t rs, int 
             for (int e = P; e < LDX; e++) X[e] = 0.0;
         }
     }
-    for (int t = threadIdx.x; t < nj * PARTS; t += MIX_THREADS) {
-        const int part = t / nj, jj = t - part * nj;
-        eval_xw_part<K>(Nrec + jj * NREC, part, Xf ? Xf + jj * LDX : nullptr, Wf + jj * LDX);
+    if (A.wstore && !Xf) {
+        // W as the assembly stored it (coalesced: consecutive threads, consecutive elements)
+        const df *ws = A.wstore + (rs + j0) * (int64_t)P;
+        for (int t = threadIdx.x; t < nj * P; t += MIX_THREADS) {
+            const int jj = t / P, e = t - jj * P;
+            Wf[jj * LDX + e] = ws[t];
+        }
+    } else {
+        for (int t = threadIdx.x; t < nj * PARTS; t += MIX_THREADS) {
+            const int part = t / nj, jj = t - part * nj;
+            eval_xw_part<K>(Nrec + jj * NREC, part, Xf ? Xf + jj * LDX : nullptr, Wf + jj * LDX);
+        }
     }
     // the padding columns the tiles read
     for (int t = threadIdx.x; t < nj * (LDX - P); t += MIX_THREADS) {
@@ -318,6 +331,13 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_assemble(MixedArgs A)
         for (int j0 = 0; j0 < ni; j0 += NB) {
             const int nj = min(NB, ni - j0);
             stage_chunk<K>(A, rs, j0, nj, nullptr, Xf, Wf, Nrec);
+            if (A.wstore) {
+                df *ws = A.wstore + (rs + j0) * (int64_t)P;
+                for (int t = tid; t < nj * P; t += MIX_THREADS) {
+                    const int jj = t / P, e = t - jj * P;
+                    ws[t] = Wf[jj * LDX + e];
+                }
+            }
             if (tile_active) {
                 for (int j = 0; j < nj; j++) {
                     const df *X = Xf + j * LDX + rg * TM;
@@ -402,7 +422,9 @@ template <int K> struct TcCfg {
     // levels per tensor-memory round: the columns fit the allocation, and the exact int64
     // combination of a round's levels (each < 2^24, 8 bits apart) stays below 2^63
     static constexpr int LPR = TC_TMEM_COLS / PN < 5 ? TC_TMEM_COLS / PN : 5;
-    static constexpr int LDS = P;                        // row stride (df) of the staging arrays
+    // row stride (df) of the staging arrays: odd, so that the 8-byte accesses of consecutive
+    // neighbours (threads) fall on distinct bank pairs
+    static constexpr int LDS = P % 2 ? P : P + 1;
     static constexpr size_t smem = (size_t)A_BYTES + B_BYTES + 8 * (size_t)P * P + 16;
     static_assert((size_t)TC_KC * LDS * 8 <= (size_t)A_BYTES && (size_t)TC_KC * LDS * 8 <= (size_t)B_BYTES,
                   "staging fits the operand regions");
@@ -517,6 +539,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
                     eval_xw_part<K>(A.recs[rs + j0 + jj].v, part, Xst + jj * LDS, Wst + jj * LDS);
             }
             __syncthreads();
+            if (A.wstore) {  // W for the weights kernel (the staging is read-only until the next barrier)
+                df *ws = A.wstore + (rs + j0) * (int64_t)P;
+                for (int t = tid; t < nj * P; t += TC_THREADS) {
+                    const int jj = t / P, e = t - jj * P;
+                    ws[t] = Wst[jj * LDS + e];
+                }
+            }
             // 2. octets (row r of one operand, 8 consecutive neighbours) to registers, and the
             //    row maxima of |hi| (as ordered bit patterns: non-negative floats compare as integers)
             constexpr int NOCT = 2 * P * (TC_KC / 8);
@@ -1050,6 +1079,7 @@ cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
     a.n_bad = p.n_bad;
     a.recs = reinterpret_cast<Rec *>(p.recs);
     a.tc_timeout = p.tc_timeout;
+    a.wstore = reinterpret_cast<df *>(p.wstore);
     for (int d = 0; d < MAX_OPS; d++) a.lmax[d] = p.lmax[d];
     for (int t = 0; t < MAX_OPS * PMAX; t++) a.C[t] = p.C[t];
     const int pk = p_of_k(k);

@@ -68,6 +68,7 @@ struct labfm_ctx {
     labfm::DevBuf wtilde;  // scratch of the mixed-precision build: unscaled weights in double
     labfm::DevBuf mscratch;  // scratch of the mixed-precision build: per-node matrices of one batch
     labfm::DevBuf mrecs;     // scratch of the mixed-precision build: per-entry preamble records
+    labfm::DevBuf mwstore;   // scratch of the mixed-precision build: W of every entry (double-float)
 
     // RK4
     labfm::DevBuf wcomb, rk_acc, rk_stage_a, rk_stage_b;
@@ -121,6 +122,7 @@ struct MixedArgsPublic {
     void *recs;  // [nnz] per-entry records, mixed_record_bytes() each
     int tc;      // 1: moment matrices on the tensor cores (exact BF16 slices), 0: double-float
     unsigned long long *tc_timeout;  // device counter of tensor-core waits that gave up
+    void *wstore;  // [nnz][p(k)] double-float W kept between the assembly and the weights, or null
 };
 cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s);
 size_t mixed_scratch_bytes_per_node(int k);
