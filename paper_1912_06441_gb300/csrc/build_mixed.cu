@@ -139,6 +139,8 @@ __device__ __forceinline__ void eval_xw_part(const df *__restrict__ rec, int par
             qn = q;
         }
         if (!part_has_degree(part, n)) continue;
+        // d^alpha|r| = P_alpha(u, v) q^(1-n): with gn = W0'(q) / q^(n-1) the dW0/dr term is P gn
+        const df gn = df_mul(d1, iqn);
         df mono[K + 1];
 #pragma unroll
         for (int t = 0; t <= n; t++) mono[t] = df_mul(up[t], vp[n - t]);
@@ -154,14 +156,26 @@ __device__ __forceinline__ void eval_xw_part(const df *__restrict__ rec, int par
             const int b = n - a;
             const int e = p_of_k(n - 1) + b;
             if (Xf) Xf[e] = df_mul(df_mul(qn, mono[a]), c_dft.invfact2[a][b]);
-            df s = df{0.0f, 0.0f};
+            // P_alpha(u, v) = sum_t c_t u^t v^(n-t) with integer c_t (exact floats): each product
+            // c m is split exactly (TwoProduct), the high parts summed with TwoSum and the low
+            // parts and sum errors collected in one float, renormalised once at the end
+            float sh = 0.0f, sl = 0.0f;
 #pragma unroll
             for (int t = 0; t <= n; t++) {
                 const float c = c_dft.rpoly[e][t];
-                if (c != 0.0f) s = df_fma(df{c, 0.0f}, mono[t], s);
+                if (c != 0.0f) {
+                    const float ph = __fmul_rn(c, mono[t].hi);
+                    float pl = __fmaf_rn(c, mono[t].hi, -ph);
+                    pl = __fmaf_rn(c, mono[t].lo, pl);
+                    float s2, err;
+                    two_sum(sh, ph, s2, err);
+                    sh = s2;
+                    sl = __fadd_rn(sl, __fadd_rn(err, pl));
+                }
             }
-            const df dr = df_mul(s, iqn);
-            df wv = df_mul(d1, dr);
+            df s;
+            two_sum(sh, sl, s.hi, s.lo);  // |sl| may exceed |sh| when P_alpha nearly vanishes
+            df wv = df_mul(s, gn);
             // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
             if (n == 2) {
                 wv = df_fma(d2, a == 2 ? up[2] : (a == 1 ? df_mul(u, v) : vp[2]), wv);
