@@ -570,7 +570,13 @@ def run_labfm(args, rank, world, local_rank):
         "apply_roofline": {"bound": "hbm", "kernel": "k_apply<4,double,double>", "achieved": a_ach, "peak": hbm,
                            "unit": "GB/s", "frac": a_ach / hbm, "peak_source": hbm_src,
                            "algorithmic_bytes": abytes,
-                           "derivatives_per_s": len(OPS) * n / (apply_ms * 1e-3)},
+                           "derivatives_per_s": len(OPS) * n / (apply_ms * 1e-3),
+                           # on GB300 this FP64 kernel is bound by the FP64 pipe, not by HBM: one
+                           # subtraction and n_ops multiply-adds per stencil entry
+                           "fp64_pipe": {"achieved_tflops": nnz * (1 + 2 * len(OPS)) / (apply_ms * 1e-3) / 1e12,
+                                         "peak_tflops": fp64_peak,
+                                         "frac": nnz * (1 + 2 * len(OPS)) / (apply_ms * 1e-3) / 1e12 / fp64_peak},
+                           "f32_variant": "extra.apply_f32 (HBM-bound: k_apply<4,float,float>)"},
         "build_mnodes_per_s": n / (build_ms * 1e-3) / 1e6,
         "e2e": {"value": world * n / (e2e_ms * 1e-3) / 1e6, "unit": "Mnodes/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -108,20 +108,26 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_apply(int64_t n, const int64_
 }
 
 // Storage of the combined RK4 weight wc_ji = sum_d beta_d w_ji^d (a context-owned buffer):
-//   CW_F64  double           FP64 weights, FP64 fields: accumulated in double
-//   CW_F32  float            FP32 weights: accumulated in the field type
-//   CW_DF   float2 (hi, lo)  FP64 weights, FP32 fields: the double rounded to a double-float
-//                            pair once, here, so that the stage accumulates on the FP32 pipes
-//                            (about 48 bits, far below the FP32 field rounding) instead of
-//                            converting and multiplying in FP64 for every stencil entry
+//   CW_F64  double                    FP64 weights, FP64 fields: accumulated in double (the
+//                                     stencil indices are read from the CSR)
+//   CW_F32  int2 (j, w)               FP32 weights: each entry's stencil index and weight as one
+//                                     8-byte word, accumulated in the field type
+//   CW_DF   int2 (j, hi), float lo    FP64 weights, FP32 fields: the double rounded to a
+//                                     double-float pair once, here, so that the stage
+//                                     accumulates on the FP32 pipes (about 48 bits, far below the
+//                                     FP32 field rounding) instead of converting and multiplying
+//                                     in FP64 for every stencil entry; the low parts follow the
+//                                     nnz index/high-part words
+// Packing the index with the weight gives one wide load per entry for the same bytes.
 enum { CW_F64 = 0, CW_F32 = 1, CW_DF = 2 };
 
 int cw_format(int fdt, int wdt) { return wdt == LABFM_F32 ? CW_F32 : (fdt == LABFM_F32 ? CW_DF : CW_F64); }
-size_t cw_bytes(int fmt) { return fmt == CW_F32 ? 4 : 8; }
+size_t cw_bytes(int fmt) { return fmt == CW_DF ? 12 : 8; }
 
 template <class WT>
-__global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, void *__restrict__ wc, int fmt, double b0,
-                          double b1, double b2, double b3, double b4, double b5, double b6, double b7)
+__global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, const int32_t *__restrict__ col,
+                          void *__restrict__ wc, int fmt, double b0, double b1, double b2, double b3, double b4,
+                          double b5, double b6, double b7)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
@@ -131,10 +137,11 @@ __global__ void k_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, void
     if (fmt == CW_F64) {
         ((double *)wc)[e] = s;
     } else if (fmt == CW_F32) {
-        ((float *)wc)[e] = (float)s;
+        ((int2 *)wc)[e] = make_int2(col[e], __float_as_int((float)s));
     } else {
         df v = df_from_double(s);
-        ((float2 *)wc)[e] = make_float2(v.hi, v.lo);
+        ((int2 *)wc)[e] = make_int2(col[e], __float_as_int(v.hi));
+        ((float *)((int2 *)wc + nnz))[e] = v.lo;
     }
 }
 
@@ -148,6 +155,7 @@ template <class FT, int CW, int UNR>
 __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const int64_t *__restrict__ row_ptr,
                                                              const int32_t *__restrict__ col,
                                                              const void *__restrict__ wc_raw,
+                                                             const float *__restrict__ wc_lo,
                                                              const FT *__restrict__ src, FT *__restrict__ u,
                                                              FT *__restrict__ acc_buf, FT *__restrict__ nxt,
                                                              const uint8_t *__restrict__ frozen, int stage, FT dt,
@@ -155,9 +163,9 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const in
 {
     // AT: type of the stencil sum (double-float for CW_DF); the per-node update runs in FT
     using AT = typename std::conditional<std::is_same<FT, float>::value && CW != CW_F64, float, double>::type;
-    using WT = typename std::conditional<CW == CW_F64, double, typename std::conditional<CW == CW_F32, float,
-                                                                                         float2>::type>::type;
-    const WT *__restrict__ wc = (const WT *)wc_raw;
+    using WT = typename std::conditional<CW == CW_F64, double, float2>::type;  // (weight, low part)
+    const double *__restrict__ wcd = (const double *)wc_raw;
+    const int2 *__restrict__ wcp = (const int2 *)wc_raw;
     const int G = 1 << lg_g;  // lanes per node, a power of two
     const int lane = threadIdx.x & (G - 1);
     const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) >> lg_g;
@@ -178,8 +186,14 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const in
         for (int q = 0; q < UNR; q++) {
             int64_t e = base + (int64_t)q * G + lane;
             if (e < re) {
-                cj[q] = __ldcs(col + e);
-                wv[q] = __ldcs(wc + e);
+                if constexpr (CW == CW_F64) {
+                    cj[q] = __ldcs(col + e);
+                    wv[q] = __ldcs(wcd + e);
+                } else {
+                    const int2 pr = __ldcs(wcp + e);  // stencil index and (high part of the) weight
+                    cj[q] = pr.x;
+                    wv[q] = make_float2(__int_as_float(pr.y), CW == CW_DF ? __ldcs(wc_lo + e) : 0.0f);
+                }
             } else {
                 cj[q] = -1;
             }
@@ -191,6 +205,8 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const in
                     float dh, dl;  // src_j - src_i exactly, as a double-float
                     two_sum((float)src[cj[q]], -(float)si, dh, dl);
                     accd = df_fma(df{dh, dl}, df{wv[q].x, wv[q].y}, accd);
+                } else if constexpr (CW == CW_F32) {
+                    acc = fma((AT)src[cj[q]] - (AT)si, (AT)wv[q].x, acc);
                 } else {
                     acc = fma((AT)src[cj[q]] - (AT)si, (AT)wv[q], acc);
                 }
@@ -275,9 +291,10 @@ cudaError_t launch_stage_shape(labfm_ctx *ctx, Shape sh, const FT *src, FT *u, F
 {
     const unsigned blocks = blocks_for(ctx->n, sh.G);
     const void *wc = ctx->wcomb.ptr;
+    const float *wc_lo = CW == CW_DF ? reinterpret_cast<const float *>(ctx->wcomb.as<int2>() + ctx->nnz) : nullptr;
     auto args = [&](auto kern) {
-        kern<<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(), wc, src, u,
-                                              acc, nxt, frozen, stage, (FT)dt, log2_of(sh.G));
+        kern<<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(), wc, wc_lo,
+                                              src, u, acc, nxt, frozen, stage, (FT)dt, log2_of(sh.G));
     };
     switch (sh.UNR) {
     case 2: args(k_rk4_stage<FT, CW, 2>); break;
@@ -442,10 +459,12 @@ labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int fdt, doub
         unsigned blocks = (unsigned)((nnz + 255) / 256);
         if (nnz > 0) {
             if (ctx->wdtype == LABFM_F64)
-                k_combine<double><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<double>(), ctx->wcomb.ptr, fmt,
+                k_combine<double><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<double>(), ctx->col.as<int32_t>(),
+                                                         ctx->wcomb.ptr, fmt,
                                                          b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7]);
             else
-                k_combine<float><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<float>(), ctx->wcomb.ptr, fmt,
+                k_combine<float><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<float>(), ctx->col.as<int32_t>(),
+                                                        ctx->wcomb.ptr, fmt,
                                                         b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7]);
             LABFM_CUDA_TRY(ctx, cudaGetLastError());
         }
