@@ -428,6 +428,20 @@ def walls_variable_order(torch, P, dev, local_rank, n_side=1000):
     return res
 
 
+def max_over_ranks(torch, x, world, device):
+    """The largest of every rank's x (the slowest replica sets a multi-GPU step time)."""
+    if world <= 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_throughput(world, nodes_per_rank, ms_per_step):
+    """Whole-job Mnodes/s of `world` replicas, each building nodes_per_rank nodes per step."""
+    return world * nodes_per_rank / (ms_per_step * 1e-3) / 1e6
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -513,12 +527,9 @@ def run_labfm(args, rank, world, local_rank):
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
     phase = np.array([[evs[s][t].elapsed_time(evs[s][t + 1]) for t in range(4)] for s in range(args.steps)])
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(torch, total_ms, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * n / (ms_per_step * 1e-3) / 1e6
+    value = replicas_throughput(world, n, ms_per_step)
 
     # e2e through the public API from pinned host buffers: H2D of xy, h, f; D2H of the
     # derivatives and the stepped field, every step
@@ -537,7 +548,7 @@ def run_labfm(args, rank, world, local_rank):
         u_h.copy_(u, non_blocking=True)
     e1.record()
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_ms = max_over_ranks(torch, e0.elapsed_time(e1) / e2e_steps, world, dev)
     h2d = xy_h.numel() * 8 + h_h.numel() * 8 + f_h.numel() * 8
     d2h = out_h.numel() * 8 + u_h.numel() * 8
 
@@ -578,7 +589,7 @@ def run_labfm(args, rank, world, local_rank):
                                          "frac": nnz * (1 + 2 * len(OPS)) / (apply_ms * 1e-3) / 1e12 / fp64_peak},
                            "f32_variant": "extra.apply_f32 (HBM-bound: k_apply<4,float,float>)"},
         "build_mnodes_per_s": n / (build_ms * 1e-3) / 1e6,
-        "e2e": {"value": world * n / (e2e_ms * 1e-3) / 1e6, "unit": "Mnodes/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": replicas_throughput(world, n, e2e_ms), "unit": "Mnodes/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         # per step: stencil search, one build launch (uniform order), one apply, and the RK4
         # step (operator combination + 4 stage kernels)
