@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import shutil
 import subprocess
@@ -30,7 +31,8 @@ import labfm_synth as S  # noqa: E402
 
 METRIC = "order-8 weight build Mnodes/s; apply GB/s vs HBM; mixed vs FP64 at ≤1e-8 err"
 N_SIDE, HS, K, JITTER = 512, 2.2, 8, 0.3
-SKIP_LARGE = False  # --skip-large: leave out the 4.2M-node RK4 and 1M-node wall workloads
+SKIP_LARGE = False  # --skip-large: leave out the heat-equation run (350 k graph-replayed steps), the
+                    # 4.2M-node RK4 and the 1M-node wall workloads
 OPS = ("dx", "dy", "lap", "lap4")
 def workload_name():
     return (f"2D periodic jittered lattice {N_SIDE}x{N_SIDE} (+-{JITTER}s), h={HS}s, Wendland C2, order {K} "
@@ -298,9 +300,60 @@ def extra_measurements(torch, P, dev, local_rank, ns, field, hbm):
                         "timing": f"mean of {reps} back-to-back launches (inputs larger than L2)"}
     L32.close()
     if not SKIP_LARGE:
+        out["heat_dirichlet_k4"] = heat_dirichlet(torch, P, dev, local_rank)
         out["rk4_2048"] = rk4_large(torch, P, dev, local_rank)
         out["walls_1m_variable_order"] = walls_variable_order(torch, P, dev, local_rank)
     return out
+
+
+def heat_dirichlet(torch, P, dev, local_rank, k=4, h_over_H=0.0125, chunk=5000):
+    """The heat equation with Dirichlet walls of Sec. 4.1 at the finest resolution of its table:
+    161 x 161 nodes (h/dr = 2, interior noise eps/dr = 0.5, wall nodes and the two rows inside
+    them on the lattice), quadratic ABFs in the dW0/dr form, order 4, u(x, 0) = sin(pi x) and 0
+    on the other walls (frozen), RK4 from zero interior values to t* = 8 pi^2 t = 100 in graph
+    replays of `chunk` steps; error of the steady state against the exact one."""
+    ns = S.dirichlet_square(int(round(2.0 / h_over_H)) + 1, 2.0, k, 0.5, seed=100 + k)
+    L = P.Labfm(local_rank)
+    L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), False)
+    st = torch.zeros(ns.n, dtype=torch.int32, device=dev)
+    nbad = L.build_weights(np.stack([S.op_c_vector("lap", k)]), uniform_order=k, rbf="quadratic",
+                           abf_form="dw0", node_status=st)
+    # spectral radius of the Laplacian on the internal rows (power iteration, walls held at 0)
+    keep = torch.from_numpy(~ns.wall).to(dev, torch.float64)
+    v = torch.randn(ns.n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    rho = 0.0
+    for _ in range(100):
+        v = v * keep
+        v = L.apply(v / v.norm())[0] * keep
+        rho = float(v.norm())
+    dt = min(0.05 * ns.h[0] ** 2, 0.8 * 2.785 / rho)  # Sec. 4.1's 0.05 h^2, within the RK4 region
+    nsteps = int(math.ceil(100.0 / (8.0 * math.pi ** 2) / dt))
+    nchunks = (nsteps + chunk - 1) // chunk
+    field = S.HeatSteadyField()
+    ub = field.boundary(ns.xy, ns.wall)
+    u = torch.from_numpy(ub).to(dev)
+    fz = torch.from_numpy(ns.wall.astype(np.uint8)).to(dev)
+    L.step([1.0], u, dt, chunk, frozen=fz)  # records the graph (tunes the stage shape first)
+    u.copy_(torch.from_numpy(ub).to(dev))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(nchunks):
+        L.step([1.0], u, dt, chunk, frozen=fz)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    got = u.cpu().numpy()
+    ex = field.value(ns.xy)
+    steps = nchunks * chunk
+    res = {"nodes": ns.n, "nnz": int(L.nnz), "order": k, "h_over_H": h_over_H, "flagged_nodes": int(nbad),
+           "spectral_radius_h2": rho * ns.h[0] ** 2, "dt_over_h2": dt / ns.h[0] ** 2, "steps": steps,
+           "t_star": 8.0 * math.pi ** 2 * dt * steps, "ms": ms, "steps_per_s": steps / (ms * 1e-3),
+           "us_per_step": ms * 1e3 / steps,
+           "l2_err_vs_exact_steady": float(np.linalg.norm(got - ex) / np.linalg.norm(ex)),
+           "paper_l2_err": 2.9e-10, "walls_unchanged": bool(np.array_equal(got[ns.wall], ub[ns.wall]))}
+    L.close()
+    return res
 
 
 RK4_JITTER = 0.1       # noise of the time-stepping node set: every order-8 stencil well conditioned
@@ -658,7 +711,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-large", action="store_true",
-                    help="leave out the 2048^2 RK4 and 1000^2 wall workloads (profiler captures)")
+                    help="leave out the heat-equation, 2048^2 RK4 and 1000^2 wall workloads (profiler captures)")
     ap.add_argument("--n-side", type=int, default=512,
                     help="lattice side (default 512; smaller sizes are for profiler captures only)")
     ap.add_argument("--profile", choices=PROFILE_CASES, default=None,

@@ -26,6 +26,8 @@ __all__ = [
     "NodeSet",
     "jittered_lattice",
     "variable_wall_nodes",
+    "dirichlet_square",
+    "HeatSteadyField",
     "FourierField",
     "fourier_field",
     "sincos_field",
@@ -170,6 +172,33 @@ def variable_wall_nodes(n_side: int, seed: int = 4, jitter: float = 0.3,
                    wall=(on_x_wall | on_y_wall))
 
 
+def dirichlet_square(n_side: int, h_over_s: float = 2.0, k: int = 4, eps: float = 0.5,
+                     seed: int = 1, wall_band: int = 2) -> NodeSet:
+    """Non-periodic unit square for the heat equation with Dirichlet walls (Sec. 4.1).
+
+    Lattice spacing s = 1/(n_side - 1) with nodes on the walls, (i s, j s) for i, j = 0 ..
+    n_side - 1.  Nodes on a wall (``wall`` mask: their values are prescribed) and the nodes
+    within ``wall_band`` lattice rows of a wall stay on the lattice; every other node is
+    displaced by independent U(-eps s/sqrt(2), +eps s/sqrt(2)) offsets in x and y, so that
+    no node moves further than eps s (eps is the maximum perturbation distance of Sec. 3.1
+    over the node spacing).  h = h_over_s * s everywhere.
+    """
+    m = n_side
+    s = 1.0 / (m - 1)
+    ii, jj = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+    i, j = ii.ravel(), jj.ravel()
+    n = m * m
+    d = np.minimum.reduce([i, m - 1 - i, j, m - 1 - j])  # lattice rows to the nearest wall
+    u = uniform01(seed, 2 * n)
+    a = np.where(d > wall_band, eps * s / math.sqrt(2.0), 0.0)
+    x = i * s + (2.0 * u[0::2] - 1.0) * a
+    y = j * s + (2.0 * u[1::2] - 1.0) * a
+    xy = np.ascontiguousarray(np.stack([x, y], axis=1))
+    return NodeSet(xy=xy, h=np.full(n, h_over_s * s), s=np.full(n, s),
+                   order=np.full(n, k, dtype=np.int8), periodic=False,
+                   lo=(0.0, 0.0), hi=(1.0, 1.0), wall=(d == 0))
+
+
 # ----------------------------------------------------------------------------------
 # Index conventions of the monomial vector X and derivative vector D (Sec. 2):
 # total degree n = 1, 2, ...; within a degree the power of x runs from n down to 0.
@@ -300,6 +329,30 @@ def fourier_field(n_modes: int = 16, kmax: int = 32, seed: int = 3) -> FourierFi
     amp = normal01(seed + 1, n_modes)
     phase = 2 * np.pi * uniform01(seed + 2, n_modes)
     return FourierField(kx=kx, ky=ky, amp=amp, phase=phase)
+
+
+class HeatSteadyField(_Field):
+    """Steady state of the heat equation on the unit square with u(x, 0) = sin(pi x) and
+    u = 0 on the other walls (Sec. 4.1): u = sinh(pi (1 - y)) sin(pi x) / sinh(pi), a
+    harmonic function (its Laplacian vanishes)."""
+
+    def value(self, xy):
+        return np.sinh(np.pi * (1.0 - xy[:, 1])) * np.sin(np.pi * xy[:, 0]) / np.sinh(np.pi)
+
+    def boundary(self, xy, wall):
+        """The prescribed wall values: sin(pi x) on y = 0, zero elsewhere (and off the walls)."""
+        return np.where(wall & (xy[:, 1] == 0.0), np.sin(np.pi * xy[:, 0]), 0.0)
+
+    def deriv(self, name, xy):
+        pi = np.pi
+        x, y = xy[:, 0], xy[:, 1]
+        if name == "dx":
+            return pi * np.sinh(pi * (1.0 - y)) * np.cos(pi * x) / np.sinh(pi)
+        if name == "dy":
+            return -pi * np.cosh(pi * (1.0 - y)) * np.sin(pi * x) / np.sinh(pi)
+        if name.startswith("lap"):
+            return np.zeros(xy.shape[0])
+        raise ValueError(name)
 
 
 class P6Field(_Field):

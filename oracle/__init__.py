@@ -208,6 +208,33 @@ def rk4(row_ptr, col, w, beta, u0, dt, nsteps, frozen=None, precision="f64", nth
     return u
 
 
+def operator_matrix(row_ptr, col, w, beta):
+    """The sparse matrix A with (A u)_i = sum_d beta_d sum_j (u_j - u_i) w_ji^d (Eq. general_do):
+    off-diagonal entries sum_d beta_d w_ji^d, diagonal minus their row sum (scipy CSR)."""
+    import scipy.sparse as sp
+
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    n = rp.shape[0] - 1
+    wb = np.asarray(w, dtype=np.float64) @ np.asarray(beta, dtype=np.float64)
+    node = np.repeat(np.arange(n), np.diff(rp))
+    A = sp.csr_matrix((wb, (node, np.asarray(col, dtype=np.int64))), shape=(n, n))
+    return (A - sp.diags(np.bincount(node, weights=wb, minlength=n))).tocsr()
+
+
+def steady_state(row_ptr, col, w, beta, u_fixed, frozen):
+    """Steady state of du/dt = sum_d beta_d L^d(u) with the frozen (Dirichlet) nodes held at
+    ``u_fixed`` (Sec. 4.1: boundary values prescribed, the equation solved at the internal
+    nodes only): the internal values solve A_II u_I = -A_IB u_B, by a sparse direct solve."""
+    import scipy.sparse.linalg as spl
+
+    A = operator_matrix(row_ptr, col, w, beta)
+    fz = np.asarray(frozen).astype(bool)
+    I, B = np.nonzero(~fz)[0], np.nonzero(fz)[0]
+    u = np.array(u_fixed, dtype=np.float64, copy=True)
+    u[I] = spl.spsolve(A[I][:, I].tocsc(), -(A[I][:, B] @ u[B]))
+    return u
+
+
 def rbf_derivs(rbf, q, precision="f64"):
     d = np.zeros(4)
     _lib(precision).orc_rbf_derivs(RBF[rbf], float(q), _ptr(d))

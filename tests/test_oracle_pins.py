@@ -598,3 +598,73 @@ def test_convective_spectrum_on_a_regular_lattice():
     assert ratio("gaussian", 6) > 1e3 * ratio("quadratic", 6)
     # the chain-rule form with the quadratic kernel does not have this property (d2W0/dq2 != 0 at q = 2)
     assert ratio("quadratic", 4, form="chain") > 0.1
+
+
+# ------------------------------------------------------------- heat equation (Sec. 4.1)
+
+
+def _heat_table():
+    rows = {}
+    with open(os.path.join(GOLD, "paper_numbers.txt")) as fh:
+        for line in fh:
+            if line.startswith("heat_steady_l2"):
+                _, k, hH, err, rate = line.split()
+                rows.setdefault(int(k), []).append((float(hH), float(err), None if rate == "-" else float(rate)))
+    return rows
+
+
+def heat_steady_errors(k, levels, seed):
+    """Oracle steady states of the Dirichlet heat problem of Sec. 4.1 (quadratic ABFs in the
+    dW0/dr form, h/dr = 2, interior noise eps/dr = 0.5) at the given h/H, as relative L2 errors
+    against sinh(pi (1 - y)) sin(pi x) / sinh(pi) over all nodes."""
+    field = S.HeatSteadyField()
+    errs = []
+    for hH in levels:
+        ns = S.dirichlet_square(int(round(2.0 / hH)) + 1, 2.0, k, 0.5, seed=seed)
+        rp, col = oracle.neighbours(ns.xy, ns.h, False)
+        r = oracle.build_weights(ns.xy, ns.h, False, rp, col, S.op_c_vector("lap", k)[None, :], k=k,
+                                 rbf="quadratic", abf_form="dw0")
+        assert (r["status"] == 0).all()
+        u = oracle.steady_state(rp, col, r["w"], [1.0], field.boundary(ns.xy, ns.wall), ns.wall)
+        ex = field.value(ns.xy)
+        errs.append(np.linalg.norm(u - ex) / np.linalg.norm(ex))
+    return np.array(errs)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_heat_steady_state_table(k):
+    """Sec. 4.1, Table of steady-state errors (inhomogeneous Dirichlet walls): the oracle's
+    errors at h/H = 0.2 ... 0.025 fall at the printed rates (k = 2, 4: each rate within 0.7 of
+    the printed one; k = 3, whose printed rates drift from 3.1 to 2.1: each within [2, 3.6])
+    and lie within a factor 5 of the printed errors (the node sets are random draws of the same
+    distribution, not the paper's; over six draws the rates stay within 0.56 of the printed ones
+    and the errors are 1.1-3.8 times the printed ones)."""
+    rows = _heat_table()[k][:4]
+    levels = [r[0] for r in rows]
+    errs = heat_steady_errors(k, levels, seed=100 + k)
+    rates = np.log2(errs[:-1] / errs[1:])
+    printed = np.array([r[2] for r in rows[1:]])
+    if k == 3:
+        assert np.all((rates >= 2.0) & (rates <= 3.6)), rates
+    else:
+        assert np.all(np.abs(rates - printed) <= 0.7), (rates, printed)
+    ratio = errs / np.array([r[1] for r in rows])
+    assert np.all((ratio > 0.2) & (ratio < 5.0)), ratio
+
+
+def test_heat_frozen_rk4_reaches_the_steady_state():
+    """RK4 with the wall nodes frozen at their prescribed values (Sec. 4.1), run from zero
+    interior values to t* = 8 pi^2 t = 100, lands on the sparse direct solution of the same
+    semi-discrete steady problem: two independent routes to one answer."""
+    k = 4
+    ns = S.dirichlet_square(11, 2.0, k, 0.5, seed=104)
+    rp, col = oracle.neighbours(ns.xy, ns.h, False)
+    w = oracle.build_weights(ns.xy, ns.h, False, rp, col, S.op_c_vector("lap", k)[None, :], k=k,
+                             rbf="quadratic", abf_form="dw0")["w"]
+    ub = S.HeatSteadyField().boundary(ns.xy, ns.wall)
+    uss = oracle.steady_state(rp, col, w, [1.0], ub, ns.wall)
+    dt = 0.05 * ns.h[0] ** 2  # Sec. 4.1: 0.05 h^2 / kappa, kappa = 1
+    nsteps = int(math.ceil(100.0 / (8.0 * math.pi ** 2) / dt))
+    u = oracle.rk4(rp, col, w, np.array([1.0]), ub, dt, nsteps, frozen=ns.wall.astype(np.uint8))
+    assert np.array_equal(u[ns.wall], ub[ns.wall])
+    assert np.abs(u - uss).max() < 1e-9 * np.abs(uss).max()
