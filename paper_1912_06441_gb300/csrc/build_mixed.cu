@@ -5,7 +5,7 @@
 // through global scratch:
 //   A  k_mixed_assemble (CTA per node): X and W of every neighbour in double-float, then
 //      M = sum_j X_j (outer) W_j in double-float register tiles  -> M (global).
-//   B  k_mixed_invert (64 threads per node, a row per thread in shared memory): Gauss-Jordan
+//   B  k_mixed_invert (two threads per row, the matrix in shared memory): Gauss-Jordan
 //      inversion of M with partial pivoting (interchanges undone on the columns) -> M^-1.
 //   C  k_mixed_weights (CTA per node): Psi~ = M^-1 C~, w~ = W . Psi~, then `nref` refinement
 //      steps on the residual of the moment conditions of Sec. 2.1
@@ -728,46 +728,60 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
 }
 
 // ------------------------------------------------------------------------------------------
-// B: Gauss-Jordan inversion with partial pivoting; one CTA of 64 threads per node, thread t
-// updates row t of the working matrix in shared memory.  Per pivot column c:
-//   1. argmax of |M[r][c]| over r >= c (warp shuffles, then the two warps through shared memory);
-//   2. rows c and argmax are exchanged (threads over columns);
-//   3. every row r != c: f = M[r][c] / p, M[r][q] -= f M[c][q] (q != c), M[r][c] = -f;
-//      row c: M[c][q] /= p (q != c), M[c][c] = 1 / p.
-// The column loop is unrolled (compile-time offsets, so loads are issued ahead of the
-// dependent stores); the pivot loop is not, which keeps the code small.  The row interchanges
-// are undone on the columns when the result is written out.
+// B: Gauss-Jordan inversion with partial pivoting, in double-float; one CTA per node with two
+// threads per row of the working matrix in shared memory: thread t updates columns
+// [h HALF, (h + 1) HALF) of row t / 2 (h = t % 2), so that 2P lanes do work and each thread's
+// update is half a row (a thread per row would keep 20 of 64 lanes idle at p = 44 and double
+// the length of each update).  A zero column pads odd P to 2 HALF columns.  Per pivot column c:
+//   1. argmax of |M[r][c]| over r >= c (even lanes; warp shuffles, then the warps through
+//      shared memory; the lowest row wins a tie);
+//   2. rows c and argmax exchanged (threads over columns), the pivot row and the pivot column
+//      (after the exchange) published in shared memory;
+//   3. f = M[r][c] / p, M[r][q] -= f M[c][q] on the thread's half (q != c), M[r][c] = -f;
+//      row c: M[c][q] /= p, M[c][c] = 1 / p.
+// The row interchanges are undone on the columns when the result is written out.
 // ------------------------------------------------------------------------------------------
-constexpr int INV_THREADS = 64;
+template <int P> struct InvCfg {
+    static constexpr int HALF = (P + 1) / 2;
+    static constexpr int WC = 2 * HALF;                  // working columns (one zero pad for odd P)
+    static constexpr int LDM = WC + 1;                   // odd row stride in 8-byte words
+    static constexpr int NT = (2 * P + 31) / 32 * 32;    // threads: two per row, whole warps
+    static constexpr int NW = NT / 32;
+    static_assert(NT >= WC && NT >= 2 * P, "a thread per column and two per row");
+};
 
 template <int K>
-__global__ void __launch_bounds__(INV_THREADS) k_mixed_invert(MixedArgs A)
+__global__ void __launch_bounds__(InvCfg<p_of_k(K)>::NT) k_mixed_invert(MixedArgs A)
 {
     using C = MCfg<K>;
     constexpr int P = C::P;
-    constexpr int LDM = P + 1;  // row stride (df) of the working matrix
-    static_assert(P <= INV_THREADS, "one row per thread");
+    using I = InvCfg<P>;
+    constexpr int HALF = I::HALF, WC = I::WC, LDM = I::LDM, NT = I::NT, NW = I::NW;
     __shared__ df s_m[P * LDM];
-    __shared__ df s_prow[P];
-    __shared__ float s_best[2];
-    __shared__ int s_br[2];
+    __shared__ df s_prow[WC];
+    __shared__ df s_pcol[P];
+    __shared__ float s_best[NW];
+    __shared__ int s_br[NW];
     __shared__ int s_src[P];
     __shared__ signed char s_piv[P];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const bool own = t < P;
+    const int r = t >> 1, hf = t & 1, q0 = hf * HALF;
+    const bool own = r < P;
 
     for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
         if (A.flag[li] != 0) continue;  // uniform per CTA
         const df *Mg = A.Mg + li * (int64_t)P * P;
-        for (int u = t; u < P * P; u += INV_THREADS) {
-            const int r = u / P;
-            s_m[r * LDM + (u - r * P)] = Mg[u];
+        for (int u = t; u < P * P; u += NT) {
+            const int rr = u / P;
+            s_m[rr * LDM + (u - rr * P)] = Mg[u];
         }
+        if (WC > P)
+            for (int rr = t; rr < P; rr += NT) s_m[rr * LDM + P] = df{0.0f, 0.0f};
         __syncthreads();
         bool zero = false;
         for (int c = 0; c < P; c++) {
-            float best = (own && t >= c) ? fabsf(s_m[t * LDM + c].hi) : -1.0f;
-            int br = t;
+            float best = (own && hf == 0 && r >= c) ? fabsf(s_m[r * LDM + c].hi) : -1.0f;
+            int br = own ? r : P;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const float ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -782,40 +796,51 @@ __global__ void __launch_bounds__(INV_THREADS) k_mixed_invert(MixedArgs A)
                 s_br[warp] = br;
             }
             __syncthreads();
-            if (s_best[1] > s_best[0]) {
-                best = s_best[1];
-                br = s_br[1];
-            } else {
-                best = s_best[0];
-                br = s_br[0];
-            }
+            best = s_best[0];
+            br = s_br[0];
+#pragma unroll
+            for (int w = 1; w < NW; w++)
+                if (s_best[w] > best) {  // later warps hold higher rows: strict keeps the lowest
+                    best = s_best[w];
+                    br = s_br[w];
+                }
             if (!(best > 0.0f) || !isfinite(best)) {
                 zero = true;
                 break;
             }
+            // best > 0 comes from an even lane of a row r >= c, so c <= br < P
             if (t == 0) s_piv[c] = (signed char)br;
-            // exchange rows c and br, and publish the pivot row
-            if (t < P) {
+            if (t < WC) {  // column t: exchange rows c and br, publish the pivot row
                 const df a = s_m[c * LDM + t], b = s_m[br * LDM + t];
                 s_prow[t] = b;
                 if (br != c) {
                     s_m[c * LDM + t] = b;
                     s_m[br * LDM + t] = a;
                 }
+                // row t's entry of the pivot column after the exchange (rows c and br from the
+                // values this thread just read when t == c; other rows are not being written)
+                if (t == c) {
+                    s_pcol[c] = b;
+                    if (br != c) s_pcol[br] = a;
+                } else if (t < P && t != br) {
+                    s_pcol[t] = s_m[t * LDM + c];
+                }
             }
             __syncthreads();
             const df inv = df_recip(s_prow[c]);
             if (own) {
-                df *row = s_m + t * LDM;
-                if (t == c) {
+                df *row = s_m + r * LDM + q0;
+                const bool mine = c >= q0 && c < q0 + HALF;
+                if (r == c) {
 #pragma unroll
-                    for (int q = 0; q < P; q++) row[q] = df_mul(row[q], inv);
-                    row[c] = inv;
+                    for (int q = 0; q < HALF; q++) row[q] = df_mul(row[q], inv);
+                    if (mine) row[c - q0] = inv;
                 } else {
-                    const df f = df_mul(row[c], inv);
+                    const df f = df_mul(s_pcol[r], inv);
+                    const df *pr = s_prow + q0;
 #pragma unroll
-                    for (int q = 0; q < P; q++) row[q] = df_fms(f, s_prow[q], row[q]);
-                    row[c] = df_neg(f);
+                    for (int q = 0; q < HALF; q++) row[q] = df_fms(f, pr[q], row[q]);
+                    if (mine) row[c - q0] = df_neg(f);
                 }
             }
             __syncthreads();
@@ -837,9 +862,9 @@ __global__ void __launch_bounds__(INV_THREADS) k_mixed_invert(MixedArgs A)
         }
         __syncthreads();
         df *Mo = A.Mg + li * (int64_t)P * P;
-        for (int u = t; u < P * P; u += INV_THREADS) {
-            const int r = u / P, q = u - r * P;
-            Mo[u] = s_m[r * LDM + s_src[q]];
+        for (int u = t; u < P * P; u += NT) {
+            const int rr = u / P, q = u - rr * P;
+            Mo[u] = s_m[rr * LDM + s_src[q]];
         }
         __syncthreads();
     }
@@ -1056,7 +1081,7 @@ cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, bool tc, cudaStream_
         e = launch_persistent(k_mixed_assemble<K>, a, MIX_THREADS, C::smemA, a.n_list, num_sms, s);
     }
     if (e != cudaSuccess) return e;
-    e = launch_persistent(k_mixed_invert<K>, a, INV_THREADS, 0, a.n_list, num_sms, s);
+    e = launch_persistent(k_mixed_invert<K>, a, InvCfg<C::P>::NT, 0, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
     return launch_persistent(k_mixed_weights<K>, a, MIX_THREADS, C::smemC, a.n_list, num_sms, s);
 }
