@@ -104,20 +104,31 @@ __device__ __forceinline__ int64_t node_of(const MixedArgs &A, int64_t li)
     return A.list ? (int64_t)A.list[li] : A.list_base + li;
 }
 
-// Degrees handled by evaluation part `part` (each part carries a similar (n+1)^2 workload):
-// part 0: 8, 3, 1   part 1: 7, 4, 2   part 2: 6, 5
+// Degrees handled by evaluation part `part` of NP (each part carries a similar (n+1)^2 workload):
+// NP = 3: part 0: 8, 3, 1   part 1: 7, 4, 2   part 2: 6, 5
+// NP = 4: part 0: 8, 1      part 1: 7, 2      part 2: 6, 3      part 3: 5, 4
+template <int NP>
 __device__ __forceinline__ bool part_has_degree(int part, int n)
 {
+    static_assert(NP == 3 || NP == 4, "three or four parts");
+    if (NP == 3) {
+        switch (part) {
+        case 0: return n == 8 || n == 3 || n == 1;
+        case 1: return n == 7 || n == 4 || n == 2;
+        default: return n == 6 || n == 5;
+        }
+    }
     switch (part) {
-    case 0: return n == 8 || n == 3 || n == 1;
-    case 1: return n == 7 || n == 4 || n == 2;
-    default: return n == 6 || n == 5;
+    case 0: return n == 8 || n == 1;
+    case 1: return n == 7 || n == 2;
+    case 2: return n == 6 || n == 3;
+    default: return n == 5 || n == 4;
     }
 }
 
 // X (when Xf != null) and W in double-float for the degrees of `part` of one neighbour, from
 // its record (polar form q, (u, v) as in abf.cuh's eval_xw).
-template <int K>
+template <int K, int NP>
 __device__ __forceinline__ void eval_xw_part(const df *__restrict__ rec, int part, df *__restrict__ Xf,
                                              df *__restrict__ Wf)
 {
@@ -138,7 +149,7 @@ __device__ __forceinline__ void eval_xw_part(const df *__restrict__ rec, int par
         } else {
             qn = q;
         }
-        if (!part_has_degree(part, n)) continue;
+        if (!part_has_degree<NP>(part, n)) continue;
         // d^alpha|r| = P_alpha(u, v) q^(1-n): with gn = W0'(q) / q^(n-1) the dW0/dr term is P gn
         const df gn = df_mul(d1, iqn);
         df mono[K + 1];
@@ -291,7 +302,7 @@ __device__ __forceinline__ void stage_chunk(const MixedArgs &A, int64_t rs, int 
     } else {
         for (int t = threadIdx.x; t < nj * PARTS; t += MIX_THREADS) {
             const int part = t / nj, jj = t - part * nj;
-            eval_xw_part<K>(Nrec + jj * NREC, part, Xf ? Xf + jj * LDX : nullptr, Wf + jj * LDX);
+            eval_xw_part<K, PARTS>(Nrec + jj * NREC, part, Xf ? Xf + jj * LDX : nullptr, Wf + jj * LDX);
         }
     }
     // the padding columns the tiles read
@@ -422,6 +433,8 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_assemble(MixedArgs A)
 constexpr int TC_THREADS = 256;
 constexpr int NSL = 7;          // slices per operand
 constexpr int TC_KC = 64;       // neighbours per chunk (the K of one pass)
+constexpr int TC_PARTS = 4;     // threads per neighbour in the X/W evaluation: one pass of the CTA
+static_assert(TC_KC * TC_PARTS == TC_THREADS, "every thread evaluates one (neighbour, part)");
 constexpr int TC_ROWB = TC_KC / 8 * 128;  // bytes per 8-row group of an operand slice
 constexpr int TC_TMEM_COLS = 256;
 
@@ -439,7 +452,10 @@ template <int K> struct TcCfg {
     // row stride (df) of the staging arrays: odd, so that the 8-byte accesses of consecutive
     // neighbours (threads) fall on distinct bank pairs
     static constexpr int LDS = P % 2 ? P : P + 1;
-    static constexpr size_t smem = (size_t)A_BYTES + B_BYTES + 8 * (size_t)P * P + 16;
+    // row stride (df) of M in shared memory: odd, so that the epilogue's lanes (consecutive rows,
+    // one column) fall on distinct bank pairs
+    static constexpr int LDSM = P % 2 ? P : P + 1;
+    static constexpr size_t smem = (size_t)A_BYTES + B_BYTES + 8 * (size_t)P * LDSM + 16;
     static_assert((size_t)TC_KC * LDS * 8 <= (size_t)A_BYTES && (size_t)TC_KC * LDS * 8 <= (size_t)B_BYTES,
                   "staging fits the operand regions");
     static_assert(P <= 64, "rows alpha in the first two lane quadrants");
@@ -545,12 +561,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
         for (int j0 = 0; j0 < ni; j0 += TC_KC) {
             const int nj = min(TC_KC, ni - j0);
             const int ksteps = (nj + 15) / 16;
-            // 1. X and W of the chunk in double-float (PARTS threads per neighbour)
+            // 1. X and W of the chunk in double-float (TC_PARTS threads per neighbour)
             if (tid < 2 * P) s_max[tid] = 0u;
-            for (int t = tid; t < TC_KC * PARTS; t += TC_THREADS) {
+            for (int t = tid; t < TC_KC * TC_PARTS; t += TC_THREADS) {
                 const int part = t / TC_KC, jj = t - part * TC_KC;
                 if (jj < nj)
-                    eval_xw_part<K>(A.recs[rs + j0 + jj].v, part, Xst + jj * LDS, Wst + jj * LDS);
+                    eval_xw_part<K, TC_PARTS>(A.recs[rs + j0 + jj].v, part, Xst + jj * LDS, Wst + jj * LDS);
             }
             __syncthreads();
             if (A.wstore) {  // W for the weights kernel (the staging is read-only until the next barrier)
@@ -664,7 +680,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
                     // int64 (< 2^57), and M += 2^(eX + eW - 8 t1) S.
                     const bool own = alpha < P;
                     constexpr int HB = PN / 2;  // columns per half
-                    df *Mrow = sM + (own ? alpha : 0) * P;
+                    df *Mrow = sM + (own ? alpha : 0) * C::LDSM;
                     const int ex = s_e[own ? alpha : 0] - 8 * t1;
                     for (int g = 0; g < HB; g += 8) {
                         // all levels of this round for 8 columns: issue the loads, then one wait
@@ -713,7 +729,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
         df *Mg = A.Mg + li * (int64_t)P * P;
         bool finite = true;
         for (int u = tid; u < P * P; u += TC_THREADS) {
-            const df v = sM[u];
+            const int r = u / P;
+            const df v = sM[r * C::LDSM + (u - r * P)];
             finite &= df_isfinite(v);
             Mg[u] = v;
         }
@@ -729,25 +746,28 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
 
 // ------------------------------------------------------------------------------------------
 // B: Gauss-Jordan inversion with partial pivoting, in double-float; one CTA per node with two
-// threads per row of the working matrix in shared memory: thread t updates columns
-// [h HALF, (h + 1) HALF) of row t / 2 (h = t % 2), so that 2P lanes do work and each thread's
+// threads per row of the working matrix in shared memory: thread t updates the columns
+// q = h, h + 2, h + 4, ... of row t / 2 (h = t % 2), so that 2P lanes do work and each thread's
 // update is half a row (a thread per row would keep 20 of 64 lanes idle at p = 44 and double
-// the length of each update).  A zero column pads odd P to 2 HALF columns.  Per pivot column c:
+// the length of each update).  A zero column pads odd P to an even width WC.  The row stride is
+// twice an odd number of 8-byte words, so the 16 lanes of a half-warp (8 rows, both column
+// parities) touch 16 distinct bank pairs.  Per pivot column c:
 //   1. argmax of |M[r][c]| over r >= c (even lanes; warp shuffles, then the warps through
 //      shared memory; the lowest row wins a tie);
 //   2. rows c and argmax exchanged (threads over columns), the pivot row and the pivot column
 //      (after the exchange) published in shared memory;
-//   3. f = M[r][c] / p, M[r][q] -= f M[c][q] on the thread's half (q != c), M[r][c] = -f;
+//   3. f = M[r][c] / p, M[r][q] -= f M[c][q] on the thread's columns (q != c), M[r][c] = -f;
 //      row c: M[c][q] /= p, M[c][c] = 1 / p.
 // The row interchanges are undone on the columns when the result is written out.
 // ------------------------------------------------------------------------------------------
 template <int P> struct InvCfg {
-    static constexpr int HALF = (P + 1) / 2;
+    static constexpr int HALF = (P + 1) / 2;             // columns per thread
     static constexpr int WC = 2 * HALF;                  // working columns (one zero pad for odd P)
-    static constexpr int LDM = WC + 1;                   // odd row stride in 8-byte words
+    static constexpr int LDM = WC % 4 == 2 ? WC : WC + 2;  // row stride: 2 x odd, in 8-byte words
     static constexpr int NT = (2 * P + 31) / 32 * 32;    // threads: two per row, whole warps
     static constexpr int NW = NT / 32;
     static_assert(NT >= WC && NT >= 2 * P, "a thread per column and two per row");
+    static_assert(LDM % 4 == 2 && LDM >= WC, "row stride");
 };
 
 template <int K>
@@ -765,7 +785,7 @@ __global__ void __launch_bounds__(InvCfg<p_of_k(K)>::NT) k_mixed_invert(MixedArg
     __shared__ int s_src[P];
     __shared__ signed char s_piv[P];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int r = t >> 1, hf = t & 1, q0 = hf * HALF;
+    const int r = t >> 1, hf = t & 1;
     const bool own = r < P;
 
     for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
@@ -829,18 +849,18 @@ __global__ void __launch_bounds__(InvCfg<p_of_k(K)>::NT) k_mixed_invert(MixedArg
             __syncthreads();
             const df inv = df_recip(s_prow[c]);
             if (own) {
-                df *row = s_m + r * LDM + q0;
-                const bool mine = c >= q0 && c < q0 + HALF;
+                df *row = s_m + r * LDM + hf;  // this thread's columns: row[2 q]
+                const bool mine = (c & 1) == hf;
                 if (r == c) {
 #pragma unroll
-                    for (int q = 0; q < HALF; q++) row[q] = df_mul(row[q], inv);
-                    if (mine) row[c - q0] = inv;
+                    for (int q = 0; q < HALF; q++) row[2 * q] = df_mul(row[2 * q], inv);
+                    if (mine) row[c - hf] = inv;
                 } else {
                     const df f = df_mul(s_pcol[r], inv);
-                    const df *pr = s_prow + q0;
+                    const df *pr = s_prow + hf;
 #pragma unroll
-                    for (int q = 0; q < HALF; q++) row[q] = df_fms(f, pr[q], row[q]);
-                    if (mine) row[c - q0] = df_neg(f);
+                    for (int q = 0; q < HALF; q++) row[2 * q] = df_fms(f, pr[2 * q], row[2 * q]);
+                    if (mine) row[c - hf] = df_neg(f);
                 }
             }
             __syncthreads();

@@ -11,9 +11,13 @@
 
 namespace labfm {
 
-struct df {
+// 8-byte aligned, so that a value in shared or global memory moves as one 64-bit access (two
+// 32-bit accesses of a warp split across the banks conflict wherever rows are an even number
+// of words apart).  Every array of df starts on an 8-byte boundary.
+struct __align__(8) df {
     float hi, lo;
 };
+static_assert(sizeof(df) == 8 && alignof(df) == 8, "double-float layout");
 
 __device__ __forceinline__ df df_make(float h, float l) { return df{h, l}; }
 
