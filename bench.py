@@ -31,8 +31,8 @@ import labfm_synth as S  # noqa: E402
 
 METRIC = "order-8 weight build Mnodes/s; apply GB/s vs HBM; mixed vs FP64 at ≤1e-8 err"
 N_SIDE, HS, K, JITTER = 512, 2.2, 8, 0.3
-SKIP_LARGE = False  # --skip-large: leave out the heat-equation run (350 k graph-replayed steps), the
-                    # 4.2M-node RK4 and the 1M-node wall workloads
+SKIP_LARGE = False  # --skip-large: leave out the heat-equation and Burgers runs (graph-replayed
+                    # steps), the 4.2M-node RK4 and the 1M-node wall workloads
 OPS = ("dx", "dy", "lap", "lap4")
 def workload_name():
     return (f"2D periodic jittered lattice {N_SIDE}x{N_SIDE} (+-{JITTER}s), h={HS}s, Wendland C2, order {K} "
@@ -227,7 +227,7 @@ def _time(torch, fn, reps=3):
 
 def deriv_errors(d, ref):
     """Per operator: |d - ref| relative to max |ref| (median, 99th percentile, max over nodes)
-    and the normalised L2 norm of Sec. 3.1."""
+    and the normalised L2 norm of Sec. 4.1."""
     d = d.astype(np.float64)
     ref = ref.astype(np.float64)
     sc = np.abs(ref).max(axis=1, keepdims=True)
@@ -301,13 +301,14 @@ def extra_measurements(torch, P, dev, local_rank, ns, field, hbm):
     L32.close()
     if not SKIP_LARGE:
         out["heat_dirichlet_k4"] = heat_dirichlet(torch, P, dev, local_rank)
+        out["burgers_cole_k4"] = burgers_cole(torch, P, dev, local_rank)
         out["rk4_2048"] = rk4_large(torch, P, dev, local_rank)
         out["walls_1m_variable_order"] = walls_variable_order(torch, P, dev, local_rank)
     return out
 
 
 def heat_dirichlet(torch, P, dev, local_rank, k=4, h_over_H=0.0125, chunk=5000):
-    """The heat equation with Dirichlet walls of Sec. 4.1 at the finest resolution of its table:
+    """The heat equation with Dirichlet walls of Sec. 5.1 at the finest resolution of its table:
     161 x 161 nodes (h/dr = 2, interior noise eps/dr = 0.5, wall nodes and the two rows inside
     them on the lattice), quadratic ABFs in the dW0/dr form, order 4, u(x, 0) = sin(pi x) and 0
     on the other walls (frozen), RK4 from zero interior values to t* = 8 pi^2 t = 100 in graph
@@ -326,7 +327,7 @@ def heat_dirichlet(torch, P, dev, local_rank, k=4, h_over_H=0.0125, chunk=5000):
         v = v * keep
         v = L.apply(v / v.norm())[0] * keep
         rho = float(v.norm())
-    dt = min(0.05 * ns.h[0] ** 2, 0.8 * 2.785 / rho)  # Sec. 4.1's 0.05 h^2, within the RK4 region
+    dt = min(0.05 * ns.h[0] ** 2, 0.8 * 2.785 / rho)  # Sec. 5.1's 0.05 h^2, within the RK4 region
     nsteps = int(math.ceil(100.0 / (8.0 * math.pi ** 2) / dt))
     nchunks = (nsteps + chunk - 1) // chunk
     field = S.HeatSteadyField()
@@ -356,9 +357,46 @@ def heat_dirichlet(torch, P, dev, local_rank, k=4, h_over_H=0.0125, chunk=5000):
     return res
 
 
+def burgers_cole(torch, P, dev, local_rank, k=4, nside=161, Re=100.0, T=1.0, chunk=500):
+    """The periodic Burgers' problem of Sec. 5.3: u = sin(2 pi x), v = 0 on a 161 x 161 noisy
+    Cartesian set (h/dr = 2, eps/dr = 0.2), quadratic ABFs in the dW0/dr form, order 4,
+    Re = 100, RK4 to t = 1 with the time step of Eq. (tstep) in graph replays of `chunk` steps;
+    error against Cole's exact solution."""
+    ns = S.jittered_lattice(nside, 2.0, k, jitter=0.2 / math.sqrt(2), seed=7)
+    L = P.Labfm(local_rank)
+    L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), True)
+    nbad = L.build_weights(np.stack([S.op_c_vector(o, k) for o in ("dx", "dy", "lap")]), uniform_order=k,
+                           rbf="quadratic", abf_form="dw0", node_status=torch.zeros(ns.n, dtype=torch.int32, device=dev))
+    h = ns.h[0]
+    nsteps = int(math.ceil(T / min(0.2 * h, 0.05 * h * h * Re) / chunk)) * chunk
+    dt = T / nsteps
+    beta = [0.0, 0.0, 1.0 / Re]
+    u0 = torch.from_numpy(np.sin(2 * np.pi * ns.xy[:, 0])).to(dev)
+    u, v = u0.clone(), torch.zeros(ns.n, dtype=torch.float64, device=dev)
+    L.step_burgers(beta, u, v, dt, chunk)  # records the graph (tunes the stage shape first)
+    u.copy_(u0)
+    v.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(nsteps // chunk):
+        L.step_burgers(beta, u, v, dt, chunk)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    ex = S.ColeBurgersSolution(Re).u(ns.xy[:, 0], T)
+    got = u.cpu().numpy()
+    res = {"nodes": ns.n, "nnz": int(L.nnz), "order": k, "Re": Re, "T": T, "flagged_nodes": int(nbad),
+           "steps": nsteps, "dt": dt, "ms": ms, "steps_per_s": nsteps / (ms * 1e-3), "us_per_step": ms * 1e3 / nsteps,
+           "l2_err_vs_cole": float(np.linalg.norm(got - ex) / np.linalg.norm(ex)),
+           "max_abs_v": float(v.abs().max())}
+    L.close()
+    return res
+
+
 RK4_JITTER = 0.1       # noise of the time-stepping node set: every order-8 stencil well conditioned
-RK4_RBF = "quadratic"  # the kernel of the PDE tests of Sec. 4
-RK4_ABF = "dw0"        # dW0/dr-only ABFs: the form the stability results of Sec. 3.3 belong to
+RK4_RBF = "quadratic"  # the kernel of the PDE tests of Sec. 5
+RK4_ABF = "dw0"        # dW0/dr-only ABFs: the form the stability results of Sec. 4.2 belong to
 
 
 def spectral_radius(torch, L, beta, iters=80):
@@ -711,7 +749,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-large", action="store_true",
-                    help="leave out the heat-equation, 2048^2 RK4 and 1000^2 wall workloads (profiler captures)")
+                    help="leave out the heat-equation, Burgers, 2048^2 RK4 and 1000^2 wall workloads (profiler captures)")
     ap.add_argument("--n-side", type=int, default=512,
                     help="lattice side (default 512; smaller sizes are for profiler captures only)")
     ap.add_argument("--profile", choices=PROFILE_CASES, default=None,

@@ -46,11 +46,11 @@ typedef enum {
     LABFM_ERR_STATE = 7     /* call out of order (e.g. apply before build_weights) */
 } labfm_status;
 
-/* Fundamental RBFs W0(q), q = |r|/h, support [0, 2] (Sec. 2.2, Appendix A). */
+/* Fundamental RBFs W0(q), q = |r|/h, support [0, 2] (Sec. 3.2, Appendix A). */
 enum {
     LABFM_RBF_WENDLAND_C2 = 0, /* 7/(4 pi) (1 - q/2)^4 (1 + 2q) (standard Wendland C2, normalised as Appendix A asks) */
     LABFM_RBF_QUADRATIC = 1,   /* 3/(16 pi) (q - 2)^2, Appendix A.1 */
-    LABFM_RBF_CONE = 2,        /* 3/(4 pi) (1 - q/2), Sec. 2.2 */
+    LABFM_RBF_CONE = 2,        /* 3/(4 pi) (1 - q/2), Sec. 3.2 */
     LABFM_RBF_WENDLAND_C6 = 3, /* 78/(28 pi) (1 - q/2)^8 (4q^3 + 6.25q^2 + 4q + 1), Appendix A.2 */
     LABFM_RBF_GAUSSIAN = 4     /* 9/pi exp(-9 q^2), Appendix A.3 */
 };
@@ -62,7 +62,7 @@ enum {
  * dW0/dr d^alpha|r| (Appendix A, truncation rule).
  * LABFM_ABF_DW0_ONLY: every element is dW0/dr d^alpha|r|, i.e. the higher RBF derivatives are
  * dropped for the elements 1-9 too.  Appendix A's truncation sentence names only elements >= 10,
- * but the stability results of Sec. 3.3 (the Laplacian's noise limits, a purely imaginary
+ * but the stability results of Sec. 4.2 (the Laplacian's noise limits, a purely imaginary
  * convective spectrum on a regular lattice whenever dW0/dr vanishes at q = 2) are reproduced
  * by this form and not by the default one; explicit time stepping needs it. */
 #define LABFM_ABF_DW0_ONLY 0x100
@@ -73,7 +73,7 @@ enum {
     /* X and W in double; M, its partially pivoted LU, Psi and W . Psi in double-float
      * (pairs of FP32, ~48 bits, on the FP32 pipes); then iterative refinement on the
      * polynomial-reproduction residual C - sum_j X_j w_j computed in double (the moment
-     * conditions of Sec. 2.1).  Default: 1 refinement step. */
+     * conditions of Sec. 3.1).  Default: 1 refinement step. */
     LABFM_PREC_MIXED = 1,
     /* As LABFM_PREC_MIXED, with M formed on the tensor cores: X and W are scaled per row (a power
      * of two per chunk of <= 64 neighbours) and cut into seven 8-bit BF16 slices; the slice
@@ -100,7 +100,7 @@ enum {
 /* Limits of this build. */
 #define LABFM_MAX_ORDER 8 /* k <= 8, p <= 44 */
 #define LABFM_MAX_OPS 8   /* operators per build */
-#define LABFM_PMAX 44     /* p(8) = (8^2 + 3*8)/2, Sec. 2.1 */
+#define LABFM_PMAX 44     /* p(8) = (8^2 + 3*8)/2, Sec. 3.1 */
 
 /* Create a context on CUDA device `device` that enqueues work on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
@@ -142,9 +142,9 @@ labfm_status labfm_get_neighbours(labfm_ctx *ctx, const int64_t **row_ptr, const
                                   int64_t *n, int64_t *nnz);
 
 /*
- * Weights (Sec. 2.1-2.2): per node i, build M_i = sum_j X_ji (outer) W_ji
+ * Weights (Sec. 3.1-2.2): per node i, build M_i = sum_j X_ji (outer) W_ji
  * (Eq. disc_form) from the Taylor monomials X (Sec. 2) and the ABFs
- * W = D(W0)|r_ji (Sec. 2.2; elements >= 10 keep only the dW0/dr term, Appendix A),
+ * W = D(W0)|r_ji (Sec. 3.2; elements >= 10 keep only the dW0/dr term, Appendix A),
  * solve M_i Psi^d = C^d (Eq. lsys) by Gaussian elimination with partial pivoting,
  * and set w_ji^d = W_ji . Psi^d (Eq. w_abf).  Offsets are taken in units of h_i
  * and C^d is scaled by h_i^-|alpha| (an exact similarity transform of M_i).
@@ -189,7 +189,7 @@ labfm_status labfm_get_weights(labfm_ctx *ctx, const void **w, int *dtype, int *
 labfm_status labfm_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int field_dtype, void *out);
 
 /*
- * Explicit time stepping with the classical four-stage Runge-Kutta scheme (Sec. 4.1) of
+ * Explicit time stepping with the classical four-stage Runge-Kutta scheme (Sec. 5.1) of
  *   du/dt = F(u),  F(u)_i = sum_d beta_d L_i^d(u)
  * for nsteps steps of size dt.  The operators are combined once into one weight per
  * stencil entry, w_ji = sum_d beta_d w_ji^d (L^d is linear in w, summed in double), cached
@@ -198,7 +198,7 @@ labfm_status labfm_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int fi
  * floats, ~48 bits) and the stencil sums run in double-float arithmetic on the FP32 pipes.
  * The per-node stage update is in double (in float when weights and field are FP32).
  * Nodes with frozen[i] != 0 keep their value
- * (Dirichlet nodes, Sec. 4.1).  The nsteps x 4 stage launches are recorded once into a
+ * (Dirichlet nodes, Sec. 5.1).  The nsteps x 4 stage launches are recorded once into a
  * CUDA graph and replayed; it is recorded again when an argument other than beta, the
  * stencil count or size, the weight type or a context buffer changes.  The stage's launch
  * shape is tuned as for labfm_apply, on first-stage launches that read u and write only
@@ -210,6 +210,32 @@ labfm_status labfm_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int fi
  */
 labfm_status labfm_step(labfm_ctx *ctx, const double *beta, void *u, int field_dtype, double dt,
                         int64_t nsteps, const uint8_t *frozen);
+
+/*
+ * Explicit time stepping of the viscous Burgers' equation (Sec. 5.3, eq. burgers),
+ * du/dt + (u . grad) u = (1/Re) nabla^2 u for the velocity u = (u, v), with the classical
+ * four-stage Runge-Kutta scheme, in the form
+ *   du/dt = -(u_i L^0_i(u) + v_i L^1_i(u)) + sum_{d>=2} beta_d L^d_i(u)
+ *   dv/dt = -(u_i L^0_i(v) + v_i L^1_i(v)) + sum_{d>=2} beta_d L^d_i(v)
+ * where operators 0 and 1 of the built weights must be d/dx and d/dy (their targets C^d the
+ * unit vectors of the first two elements of D; LABFM_ERR_ARG otherwise) and the further
+ * operators carry the linear terms: beta_2 = 1/Re on nabla^2, and e.g. a hyperviscosity
+ * -alpha nabla^4 or alpha nabla^6 (Sec. 4.2) as another operator.  beta[0] and beta[1] are
+ * not read.  The advection coefficients are the stage's own field values, so d/dx and d/dy
+ * stay separate stencil sums; the linear operators are combined once into one weight per
+ * entry (summed in double, kept in the weight type, cached while beta[2..] and the weights are
+ * unchanged).  Sums run in double unless field and weights are both LABFM_F32.
+ * Nodes with frozen[i] != 0 keep their values of u and v.  The nsteps x 4 stage launches are
+ * recorded once into a CUDA graph and replayed, under the same rules as labfm_step; the
+ * stage's launch shape is tuned on first-stage launches that read u and v and write only
+ * context-owned buffers.
+ *   beta    host double[n_ops]
+ *   u, v    device [n] of field_dtype, distinct, updated in place
+ *   frozen  device uint8[n] or NULL
+ * Asynchronous.  LABFM_ERR_STATE before labfm_build_weights.
+ */
+labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int field_dtype,
+                                double dt, int64_t nsteps, const uint8_t *frozen);
 
 /*
  * Stencil search that allocates nothing.  (The paper has no counterpart: this is an interface

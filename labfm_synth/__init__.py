@@ -1,7 +1,7 @@
 """Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
 
 This module holds no arithmetic of the LABFM method itself.  It generates
-node sets (perturbed Cartesian lattices, Sec. 3.1 of King, Lind & Nasar,
+node sets (perturbed Cartesian lattices, Sec. 4.1 of King, Lind & Nasar,
 "High order difference schemes using the Local Anisotropic Basis Function
 Method"), test fields with their exact derivatives, and nothing else.  Both
 the oracle tests and the GPU tests draw from here so that the two sides see
@@ -28,6 +28,7 @@ __all__ = [
     "variable_wall_nodes",
     "dirichlet_square",
     "HeatSteadyField",
+    "ColeBurgersSolution",
     "FourierField",
     "fourier_field",
     "sincos_field",
@@ -96,7 +97,7 @@ def jittered_lattice(n_side: int, h_over_s: float, k: int, jitter: float = 0.3,
                      seed: int = 1, periodic: bool = True) -> NodeSet:
     """Cartesian lattice on the unit square, spacing s = 1/n_side, each node at
     ((i+1/2)s, (j+1/2)s) moved by independent U(-jitter*s, +jitter*s) offsets in x
-    and y (the "noisy Cartesian" distribution of Sec. 3.1, maximum perturbation
+    and y (the "noisy Cartesian" distribution of Sec. 4.1, maximum perturbation
     eps = jitter*s per coordinate).  Node index = j*n_side + i (row-major in y).
     Periodic sets are wrapped back into [0, 1).
     """
@@ -119,7 +120,7 @@ def jittered_lattice(n_side: int, h_over_s: float, k: int, jitter: float = 0.3,
                    lo=(0.0, 0.0), hi=(1.0, 1.0))
 
 
-# h/s per order for the variable-resolution set (each above the critical h/dr of Sec. 2.2).
+# h/s per order for the variable-resolution set (each above the critical h/dr of Sec. 3.2).
 H_OVER_S_BY_ORDER = {2: 1.0, 3: 1.1, 4: 1.4, 5: 1.6, 6: 1.8, 7: 2.0, 8: 2.2}
 
 
@@ -135,7 +136,7 @@ def variable_wall_nodes(n_side: int, seed: int = 4, jitter: float = 0.3,
     are jittered by +-jitter*s per coordinate, wall nodes only along their wall,
     corners are fixed.  Order k_i = min(8, 2 + floor(7 x_i)) rises left to right,
     capped at ``wall_order_cap`` within 2h of a wall (one-sided stencils keep
-    order up to 4 there, Sec. 3.1); h_i = (h/s)(k_i) * s_i, times
+    order up to 4 there, Sec. 4.1); h_i = (h/s)(k_i) * s_i, times
     ``wall_h_boost`` in that band (larger stencils at incomplete support).
     """
     m = n_side
@@ -174,13 +175,13 @@ def variable_wall_nodes(n_side: int, seed: int = 4, jitter: float = 0.3,
 
 def dirichlet_square(n_side: int, h_over_s: float = 2.0, k: int = 4, eps: float = 0.5,
                      seed: int = 1, wall_band: int = 2) -> NodeSet:
-    """Non-periodic unit square for the heat equation with Dirichlet walls (Sec. 4.1).
+    """Non-periodic unit square for the heat equation with Dirichlet walls (Sec. 5.1).
 
     Lattice spacing s = 1/(n_side - 1) with nodes on the walls, (i s, j s) for i, j = 0 ..
     n_side - 1.  Nodes on a wall (``wall`` mask: their values are prescribed) and the nodes
     within ``wall_band`` lattice rows of a wall stay on the lattice; every other node is
     displaced by independent U(-eps s/sqrt(2), +eps s/sqrt(2)) offsets in x and y, so that
-    no node moves further than eps s (eps is the maximum perturbation distance of Sec. 3.1
+    no node moves further than eps s (eps is the maximum perturbation distance of Sec. 4.1
     over the node spacing).  h = h_over_s * s everywhere.
     """
     m = n_side
@@ -205,7 +206,7 @@ def dirichlet_square(n_side: int, h_over_s: float = 2.0, k: int = 4, eps: float 
 # ----------------------------------------------------------------------------------
 
 def p_of_k(k: int) -> int:
-    """Number of elements of X up to total degree k in 2D: p = (k^2 + 3k)/2 (Sec. 2.1)."""
+    """Number of elements of X up to total degree k in 2D: p = (k^2 + 3k)/2 (Sec. 3.1)."""
     return (k * k + 3 * k) // 2
 
 
@@ -220,7 +221,7 @@ def op_c_vector(name: str, k: int) -> np.ndarray:
 
     ``dx``, ``dy``: first derivatives; ``lap``: Laplacian (elements 3 and 5,
     Sec. 2); ``lap2``: biharmonic, ``lap3``: triharmonic, ``lap4``: nabla^8,
-    each the multinomial expansion of (d_xx + d_yy)^m (Sec. 2.3 gives the
+    each the multinomial expansion of (d_xx + d_yy)^m (Sec. 4.2 gives the
     element positions for m = 2 and m = 3; m = 4 follows the same rule).  The
     hyperviscosity coefficient and its sign are left to the caller.
     """
@@ -333,7 +334,7 @@ def fourier_field(n_modes: int = 16, kmax: int = 32, seed: int = 3) -> FourierFi
 
 class HeatSteadyField(_Field):
     """Steady state of the heat equation on the unit square with u(x, 0) = sin(pi x) and
-    u = 0 on the other walls (Sec. 4.1): u = sinh(pi (1 - y)) sin(pi x) / sinh(pi), a
+    u = 0 on the other walls (Sec. 5.1): u = sinh(pi (1 - y)) sin(pi x) / sinh(pi), a
     harmonic function (its Laplacian vanishes)."""
 
     def value(self, xy):
@@ -353,6 +354,37 @@ class HeatSteadyField(_Field):
         if name.startswith("lap"):
             return np.zeros(xy.shape[0])
         raise ValueError(name)
+
+
+class ColeBurgersSolution:
+    """Exact solution of the periodic Burgers' problem of Sec. 5.3 (Cole 1951): on [0, 1)^2 with
+    u(x, y, 0) = sin(2 pi x), v = 0, the velocity stays v = 0 and
+
+        u(x, t) = (4 pi / Re) sum_n n A_n sin(2 n pi x) E_n / (A_0 + sum_n A_n cos(2 n pi x) E_n),
+        A_0 = e^-z I_0(z),  A_n = 2 e^-z I_n(z),  z = Re / (4 pi),  E_n = exp(-4 n^2 pi^2 t / Re),
+
+    I_n the modified Bessel functions of the first kind.  This is the Cole-Hopf transform
+    u = -(2/Re) phi_x / phi of the heat-equation solution phi with phi(x, 0) = exp(Re cos(2 pi x)
+    / (4 pi)) = I_0(z) + 2 sum_n I_n(z) cos(2 n pi x).  (The paper prints the decay factor as
+    exp(-n^2 pi^2 t / (H^2 Re)); the factor 4 follows from phi_t = phi_xx / Re with wavenumber
+    2 n pi.)  ``nterms`` terms: A_n < 1e-16 for n >= 30 at Re = 100."""
+
+    def __init__(self, Re: float = 100.0, nterms: int = 40):
+        from scipy.special import ive  # exponentially scaled I_n: e^-z I_n(z)
+
+        self.Re = float(Re)
+        z = self.Re / (4.0 * math.pi)
+        self.n = np.arange(1, nterms + 1, dtype=np.float64)
+        self.A0 = float(ive(0, z))
+        self.An = 2.0 * ive(self.n, z)
+
+    def u(self, x, t):
+        x = np.asarray(x, dtype=np.float64)
+        E = np.exp(-4.0 * self.n ** 2 * math.pi ** 2 * t / self.Re)
+        th = 2.0 * math.pi * np.outer(x, self.n)
+        num = (4.0 * math.pi / self.Re) * (np.sin(th) @ (self.n * self.An * E))
+        den = self.A0 + np.cos(th) @ (self.An * E)
+        return num / den
 
 
 class P6Field(_Field):

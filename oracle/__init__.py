@@ -67,6 +67,8 @@ def _configure(lib):
     lib.orc_apply.restype = None
     lib.orc_rk4.argtypes = [_I64, _P, _P, _P, _I, _P, _P, _D, _I64, _P, _I]
     lib.orc_rk4.restype = _I
+    lib.orc_rk4_burgers.argtypes = [_I64, _P, _P, _P, _I, _P, _P, _P, _D, _I64, _P, _I]
+    lib.orc_rk4_burgers.restype = _I
     lib.orc_rbf_derivs.argtypes = [_I, _D, _P]
     lib.orc_rbf_derivs.restype = None
     lib.orc_dr.argtypes = [_D, _D, _I, _P]
@@ -194,7 +196,7 @@ def apply(row_ptr, col, w, f, queries=None, precision="f64", nthreads=0):
 
 
 def rk4(row_ptr, col, w, beta, u0, dt, nsteps, frozen=None, precision="f64", nthreads=0):
-    """Classical RK4 for du/dt = sum_d beta_d L^d(u) over all nodes (Sec. 4.1)."""
+    """Classical RK4 for du/dt = sum_d beta_d L^d(u) over all nodes (Sec. 5.1)."""
     lib = _lib(precision)
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     cl = np.ascontiguousarray(col, dtype=np.int32)
@@ -206,6 +208,23 @@ def rk4(row_ptr, col, w, beta, u0, dt, nsteps, frozen=None, precision="f64", nth
                      int(nsteps), _ptr(fz), int(nthreads))
     assert rc == 0
     return u
+
+
+def rk4_burgers(row_ptr, col, w, beta, u0, v0, dt, nsteps, frozen=None, precision="f64", nthreads=0):
+    """Classical RK4 for Burgers' equation (Sec. 5.3): du/dt = -(u L^0(u) + v L^1(u)) +
+    sum_{d>=2} beta_d L^d(u) and the same for v, operators 0 and 1 being d/dx and d/dy."""
+    lib = _lib(precision)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    u = np.array(u0, dtype=np.float64, copy=True)
+    v = np.array(v0, dtype=np.float64, copy=True)
+    fz = None if frozen is None else np.ascontiguousarray(frozen, dtype=np.uint8)
+    rc = lib.orc_rk4_burgers(u.shape[0], _ptr(rp), _ptr(cl), _ptr(w), w.shape[1], _ptr(beta), _ptr(u), _ptr(v),
+                             float(dt), int(nsteps), _ptr(fz), int(nthreads))
+    assert rc == 0
+    return u, v
 
 
 def operator_matrix(row_ptr, col, w, beta):
@@ -223,7 +242,7 @@ def operator_matrix(row_ptr, col, w, beta):
 
 def steady_state(row_ptr, col, w, beta, u_fixed, frozen):
     """Steady state of du/dt = sum_d beta_d L^d(u) with the frozen (Dirichlet) nodes held at
-    ``u_fixed`` (Sec. 4.1: boundary values prescribed, the equation solved at the internal
+    ``u_fixed`` (Sec. 5.1: boundary values prescribed, the equation solved at the internal
     nodes only): the internal values solve A_II u_I = -A_IB u_B, by a sparse direct solve."""
     import scipy.sparse.linalg as spl
 

@@ -11,17 +11,18 @@
  * blocking, fusion or reordering:
  *   neighbours   all j != i with |r_ji| < 2 h_i, by brute force over j    (Sec. 2)
  *   X_ji         Taylor monomials x^a y^b / (a! b!), degree-major order    (Sec. 2, eq. X)
- *   W_ji         ABFs = D(W0) at r_ji (Sec. 2.2), full chain rule for the
+ *   W_ji         ABFs = D(W0) at r_ji (Sec. 3.2), full chain rule for the
  *                elements 1-9, only the dW0/dr term for elements >= 10
  *                (Appendix A, truncation rule)
  *   M_i          sum_j X_ji (outer) W_ji                                  (Eq. disc_form)
  *   Psi^d        Gaussian elimination with partial pivoting of M Psi = C^d (Eq. lsys)
  *   w_ji^d       W_ji . Psi^d                                             (Eq. w_abf)
  *   L_i^d(f)     sum_j (f_j - f_i) w_ji^d                                 (Eq. general_do)
- *   RK4          the classical four-stage scheme                          (Sec. 4.1)
+ *   RK4          the classical four-stage scheme                          (Sec. 5.1)
+ *   Burgers      RK4 of the viscous Burgers' equation                     (Sec. 5.3)
  *
  * Offsets are evaluated in units of h_i (rhat = r_ji / h_i) and C^d is scaled
- * by h_i^-|alpha| (Sec. 2.2: the elements of X scale with h^|alpha| and the
+ * by h_i^-|alpha| (Sec. 3.2: the elements of X scale with h^|alpha| and the
  * ABFs with h^-|alpha|).  This is the similarity transform
  * M = S Mhat S^-1, S = diag(h^|alpha|), so Psi = S Psihat and the physical
  * weights w = W . Psi = What . Psihat are identical in exact arithmetic.
@@ -58,7 +59,7 @@ typedef ORC_REAL real;
 enum { RBF_WENDLAND_C2 = 0, RBF_QUADRATIC = 1, RBF_CONE = 2, RBF_WENDLAND_C6 = 3, RBF_GAUSSIAN = 4 };
 enum { ST_OK = 0, ST_SINGULAR = 1, ST_UNDERSAMPLED = 2, ST_NONFINITE = 3 };
 
-/* p = (k^2 + 3k)/2, Sec. 2.1 */
+/* p = (k^2 + 3k)/2, Sec. 3.1 */
 int orc_p_of_k(int k) { return (k * k + 3 * k) / 2; }
 
 /* 0-based element e -> (a, b) of x^a y^b: degree n ascending, a from n down to 0 */
@@ -117,7 +118,7 @@ int orc_neighbours(int64_t n, const double *xy, const double *h, int periodic,
 }
 
 /* ---------------------------------------------------------------------------
- * Fundamental RBFs W0(q) (Sec. 2.2 and Appendix A) and their first three
+ * Fundamental RBFs W0(q) (Sec. 3.2 and Appendix A) and their first three
  * derivatives d^m W0 / dq^m at q (m = 0..3).
  * ------------------------------------------------------------------------- */
 
@@ -168,7 +169,7 @@ static poly rbf_poly_t(int rbf)
                         poly_mul(poly_pow(t1, 4), poly_compose_lin(poly_lin(1, 2), 2, -2)));
     case RBF_QUADRATIC: /* 3/(16 pi) (q - 2)^2, Appendix A.1 */
         return poly_mul(poly_const(3 / (16 * pi)), poly_pow(poly_compose_lin(poly_lin(-2, 1), 2, -2), 2));
-    case RBF_CONE: /* 3/(4 pi) (1 - q/2), Sec. 2.2 */
+    case RBF_CONE: /* 3/(4 pi) (1 - q/2), Sec. 3.2 */
         return poly_mul(poly_const(3 / (4 * pi)), t1);
     case RBF_WENDLAND_C6: { /* 78/(28 pi) (1 - q/2)^8 (4 q^3 + 6.25 q^2 + 4 q + 1), Appendix A.2 */
         poly b = poly_const(1); b.deg = 3; b.c[1] = 4; b.c[2] = 6.25; b.c[3] = 4;
@@ -281,7 +282,7 @@ void orc_monomials(double x, double y, int k, double *X)
 }
 
 /* ---------------------------------------------------------------------------
- * ABFs W = D(W0(|r|)) at (x, y) with h = 1 (Sec. 2.2, Appendix A).
+ * ABFs W = D(W0(|r|)) at (x, y) with h = 1 (Sec. 3.2, Appendix A).
  * Elements 1..9 (|alpha| <= 3): the chain rule for W0(r(x, y)) with all of
  * W0', W0'', W0'''; elements >= 10 (|alpha| >= 4): W0'(r) d^alpha r only.
  * With ORC_ABF_DW0_ONLY set in rbf_form, the W0'' and W0''' terms are dropped
@@ -415,7 +416,7 @@ static int build_one(int64_t i, const double *xy, const double *h, int periodic,
     if (mhat_out)
         for (int t = 0; t < p * p; t++) mhat_out[t] = (double)M[t];
     /* a non-finite entry of M (e.g. a neighbour on top of node i, where the ABFs are
-     * singular, Sec. 2.2) makes the node's weights meaningless */
+     * singular, Sec. 3.2) makes the node's weights meaningless */
     for (int t = 0; t < p * p; t++)
         if (!isfinite(M[t])) {
             for (int64_t u = 0; u < ni * n_ops; u++) w[u] = 0;
@@ -502,9 +503,9 @@ void orc_apply(const int64_t *queries, int64_t nq, const int64_t *row_ptr, const
 }
 
 /* ---------------------------------------------------------------------------
- * Classical RK4 (Sec. 4.1) for du/dt = F(u), F(u)_i = sum_d beta_d L_i^d(u),
+ * Classical RK4 (Sec. 5.1) for du/dt = F(u), F(u)_i = sum_d beta_d L_i^d(u),
  * over all n nodes (row_ptr/col/w cover every node).  Nodes with frozen[i]
- * set keep their value (Dirichlet nodes, Sec. 4.1): a fixed boundary value has
+ * set keep their value (Dirichlet nodes, Sec. 5.1): a fixed boundary value has
  * du/dt = 0, so F_i = 0 there in every stage.
  * ------------------------------------------------------------------------- */
 static void rhs_eval(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w, int n_ops,
@@ -548,6 +549,92 @@ int orc_rk4(int64_t n, const int64_t *row_ptr, const int32_t *col, const double 
     }
     for (int64_t i = 0; i < n; i++) u_io[i] = (double)u[i];
     free(u); free(ut); free(k1); free(k2); free(k3); free(k4);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Classical RK4 for the viscous Burgers' equation (Sec. 5.3, eq. burgers),
+ * du/dt + (u . grad) u = (1/Re) nabla^2 u with u = (u, v), written with the
+ * discrete operators as
+ *   du/dt = -(u_i L^0_i(u) + v_i L^1_i(u)) + sum_{d>=2} beta_d L^d_i(u)
+ *   dv/dt = -(u_i L^0_i(v) + v_i L^1_i(v)) + sum_{d>=2} beta_d L^d_i(v)
+ * where operators 0 and 1 are d/dx and d/dy (the caller builds them so) and
+ * beta_2 = 1/Re multiplies the Laplacian.  Frozen nodes keep both values.
+ * ------------------------------------------------------------------------- */
+static real op_sum(const int64_t *row_ptr, const int32_t *col, const double *w, int n_ops, int d, const real *f,
+                   int64_t i)
+{
+    real s = 0;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) s += (f[col[e]] - f[i]) * (real)w[e * n_ops + d];
+    return s;
+}
+
+static void burgers_rhs(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w, int n_ops,
+                        const double *beta, const real *u, const real *v, real *Fu, real *Fv, const uint8_t *frozen)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < n; i++) {
+        real fu = -(u[i] * op_sum(row_ptr, col, w, n_ops, 0, u, i) + v[i] * op_sum(row_ptr, col, w, n_ops, 1, u, i));
+        real fv = -(u[i] * op_sum(row_ptr, col, w, n_ops, 0, v, i) + v[i] * op_sum(row_ptr, col, w, n_ops, 1, v, i));
+        for (int d = 2; d < n_ops; d++) {
+            fu += (real)beta[d] * op_sum(row_ptr, col, w, n_ops, d, u, i);
+            fv += (real)beta[d] * op_sum(row_ptr, col, w, n_ops, d, v, i);
+        }
+        Fu[i] = (frozen && frozen[i]) ? 0 : fu;
+        Fv[i] = (frozen && frozen[i]) ? 0 : fv;
+    }
+}
+
+int orc_rk4_burgers(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w, int n_ops,
+                    const double *beta, double *u_io, double *v_io, double dt, int64_t nsteps, const uint8_t *frozen,
+                    int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    if (n_ops < 2) return -2;
+    real *buf = (real *)malloc(sizeof(real) * n * 12);
+    if (!buf) return -1;
+    real *u = buf, *v = buf + n, *ut = buf + 2 * n, *vt = buf + 3 * n;
+    real *k[4][2];
+    for (int s = 0; s < 4; s++) {
+        k[s][0] = buf + (4 + 2 * s) * n;
+        k[s][1] = buf + (5 + 2 * s) * n;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        u[i] = (real)u_io[i];
+        v[i] = (real)v_io[i];
+    }
+    const real hdt = (real)dt / 2, fdt = (real)dt;
+    for (int64_t st = 0; st < nsteps; st++) {
+        burgers_rhs(n, row_ptr, col, w, n_ops, beta, u, v, k[0][0], k[0][1], frozen);
+        for (int64_t i = 0; i < n; i++) {
+            ut[i] = u[i] + hdt * k[0][0][i];
+            vt[i] = v[i] + hdt * k[0][1][i];
+        }
+        burgers_rhs(n, row_ptr, col, w, n_ops, beta, ut, vt, k[1][0], k[1][1], frozen);
+        for (int64_t i = 0; i < n; i++) {
+            ut[i] = u[i] + hdt * k[1][0][i];
+            vt[i] = v[i] + hdt * k[1][1][i];
+        }
+        burgers_rhs(n, row_ptr, col, w, n_ops, beta, ut, vt, k[2][0], k[2][1], frozen);
+        for (int64_t i = 0; i < n; i++) {
+            ut[i] = u[i] + fdt * k[2][0][i];
+            vt[i] = v[i] + fdt * k[2][1][i];
+        }
+        burgers_rhs(n, row_ptr, col, w, n_ops, beta, ut, vt, k[3][0], k[3][1], frozen);
+        for (int64_t i = 0; i < n; i++) {
+            u[i] = u[i] + fdt / 6 * (k[0][0][i] + 2 * k[1][0][i] + 2 * k[2][0][i] + k[3][0][i]);
+            v[i] = v[i] + fdt / 6 * (k[0][1][i] + 2 * k[1][1][i] + 2 * k[2][1][i] + k[3][1][i]);
+        }
+    }
+    for (int64_t i = 0; i < n; i++) {
+        u_io[i] = (double)u[i];
+        v_io[i] = (double)v[i];
+    }
+    free(buf);
     return 0;
 }
 

@@ -41,7 +41,7 @@ MAX_OPS = 8
 # every symbol include/labfm.h declares
 C_FUNCTIONS = ["labfm_create", "labfm_destroy", "labfm_last_error", "labfm_set_stream", "labfm_build_neighbours",
                "labfm_get_neighbours", "labfm_build_weights", "labfm_get_weights", "labfm_apply", "labfm_step",
-               "labfm_build_neighbours_noalloc"]
+               "labfm_step_burgers", "labfm_build_neighbours_noalloc"]
 NOALLOC_MAX_NODES = 262144  # LABFM_NOALLOC_MAX_NODES
 
 _lib = None
@@ -85,6 +85,8 @@ def load_library(path: str | None = None, build_if_missing: bool = False):
     lib.labfm_apply.restype = I
     lib.labfm_step.argtypes = [P, P, P, I, D, I64, P]
     lib.labfm_step.restype = I
+    lib.labfm_step_burgers.argtypes = [P, P, P, P, I, D, I64, P]
+    lib.labfm_step_burgers.restype = I
     lib.labfm_build_neighbours_noalloc.argtypes = [I, P, I64, P, P, I, P, P, P, P, I64, ct.POINTER(I64)]
     lib.labfm_build_neighbours_noalloc.restype = I
     if path is None:
@@ -255,7 +257,7 @@ class Labfm:
         return out
 
     def step(self, beta, u, dt: float, nsteps: int, frozen=None):
-        """nsteps of classical RK4 for du/dt = sum_d beta_d L^d(u) (Sec. 4.1); u is updated in place."""
+        """nsteps of classical RK4 for du/dt = sum_d beta_d L^d(u) (Sec. 5.1); u is updated in place."""
         torch = _torch()
         b = np.zeros(MAX_OPS)
         bb = np.asarray(beta, dtype=np.float64)
@@ -268,3 +270,24 @@ class Labfm:
         self._sync_stream()
         self._check(self.lib.labfm_step(self._ctx, b.ctypes.data_as(ct.c_void_p), pu, fdt, float(dt), int(nsteps), pz))
         return u
+
+    def step_burgers(self, beta, u, v, dt: float, nsteps: int, frozen=None):
+        """nsteps of classical RK4 for Burgers' equation (Sec. 5.3):
+        du/dt = -(u L^0(u) + v L^1(u)) + sum_{d>=2} beta_d L^d(u), the same for v; operators 0
+        and 1 of the weights must be d/dx and d/dy.  u and v are updated in place."""
+        torch = _torch()
+        b = np.zeros(MAX_OPS)
+        bb = np.asarray(beta, dtype=np.float64)
+        if bb.shape != (self.n_ops,):
+            raise ValueError(f"beta must have {self.n_ops} entries")
+        b[: self.n_ops] = bb
+        fdt = _dtype_code(u)
+        if v.dtype != u.dtype:
+            raise TypeError("u and v must have the same dtype")
+        pu = self._dev(u, u.dtype, "u", self.n)
+        pv = self._dev(v, v.dtype, "v", self.n)
+        pz = None if frozen is None else self._dev(frozen, torch.uint8, "frozen", self.n)
+        self._sync_stream()
+        self._check(self.lib.labfm_step_burgers(self._ctx, b.ctypes.data_as(ct.c_void_p), pu, pv, fdt, float(dt),
+                                                int(nsteps), pz))
+        return u, v

@@ -1,5 +1,5 @@
 // Device evaluation of the Taylor monomials X (Sec. 2) and the anisotropic basis functions
-// W = D(W0)|r (Sec. 2.2, Appendix A) at a scaled offset (x, y) = r_ji / h_i.
+// W = D(W0)|r (Sec. 3.2, Appendix A) at a scaled offset (x, y) = r_ji / h_i.
 //
 // Derivatives of |r|: d^alpha |r| = P_alpha(u, v) |r|^(1 - |alpha|), u = x/|r|, v = y/|r|,
 // where P_alpha is a homogeneous polynomial of degree |alpha| with integer coefficients.

@@ -35,6 +35,7 @@ void StepGraph::release()
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
     u = nullptr;
+    v = nullptr;
     frozen = nullptr;
     dtype = -1;
     nsteps = 0;
@@ -220,9 +221,11 @@ void labfm_destroy(labfm_ctx *ctx)
     DevBuf *bufs[] = {&ctx->node_xy, &ctx->node_h, &ctx->row_ptr, &ctx->col, &ctx->cell_of, &ctx->cell_count, &ctx->cell_start,
                       &ctx->cell_nodes, &ctx->counts, &ctx->scan_tmp, &ctx->misc, &ctx->w,
                       &ctx->status_tmp, &ctx->wtilde, &ctx->mscratch, &ctx->mrecs, &ctx->mwstore, &ctx->wcomb, &ctx->rk_acc,
-                      &ctx->rk_stage_a, &ctx->rk_stage_b};
+                      &ctx->rk_stage_a, &ctx->rk_stage_b, &ctx->wburg, &ctx->bu_acc, &ctx->bu_stage_a,
+                      &ctx->bu_stage_b};
     for (DevBuf *b : bufs) b->release();
     ctx->graph.release();
+    ctx->graph_burgers.release();
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->host_small) cudaFreeHost(ctx->host_small);
     delete ctx;
@@ -235,6 +238,7 @@ labfm_status labfm_set_stream(labfm_ctx *ctx, void *stream)
     if (!ctx) return LABFM_ERR_ARG;
     ctx->stream = (cudaStream_t)stream;
     ctx->graph.release();
+    ctx->graph_burgers.release();
     return LABFM_OK;
 }
 
@@ -295,12 +299,19 @@ labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int unifor
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, LABFM_ERR_CUDA, "cudaSetDevice failed");
     ctx->have_weights = false;
     ctx->wcomb_valid = false;
+    ctx->wburg_valid = false;
     labfm_status st =
         run_build(ctx, order, uniform_order, rbf, n_ops, C, precision, weight_dtype, node_status, n_bad_out);
     if (st == LABFM_OK || st == LABFM_ERR_SINGULAR) {
         ctx->have_weights = true;
         ctx->n_ops = n_ops;
         ctx->wdtype = weight_dtype;
+        // operators 0 and 1 are d/dx and d/dy when their targets are the unit vectors of the
+        // first two elements of D (Sec. 2): what labfm_step_burgers needs
+        bool g = n_ops >= 2;
+        for (int e = 0; e < LABFM_PMAX && g; e++)
+            g = C[e] == (e == 0 ? 1.0 : 0.0) && C[LABFM_PMAX + e] == (e == 1 ? 1.0 : 0.0);
+        ctx->grad01 = g;
     }
     return st;
 }
@@ -341,6 +352,23 @@ labfm_status labfm_step(labfm_ctx *ctx, const double *beta, void *u, int field_d
         if (!std::isfinite(beta[d])) return fail(ctx, LABFM_ERR_ARG, "beta has a non-finite entry");
     if (nsteps == 0) return LABFM_OK;
     return run_step(ctx, beta, u, field_dtype, dt, nsteps, frozen);
+}
+
+labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int field_dtype, double dt,
+                                int64_t nsteps, const uint8_t *frozen)
+{
+    if (!ctx) return LABFM_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->have_weights) return fail(ctx, LABFM_ERR_STATE, "labfm_build_weights must come first");
+    if (!ctx->grad01) return fail(ctx, LABFM_ERR_ARG, "operators 0 and 1 of the weights must be d/dx and d/dy");
+    if (!beta || !u || !v) return fail(ctx, LABFM_ERR_ARG, "null beta, u or v");
+    if (u == v) return fail(ctx, LABFM_ERR_ARG, "u and v must be distinct buffers");
+    if (field_dtype != LABFM_F64 && field_dtype != LABFM_F32) return fail(ctx, LABFM_ERR_ARG, "bad field_dtype");
+    if (!std::isfinite(dt) || nsteps < 0) return fail(ctx, LABFM_ERR_ARG, "dt must be finite and nsteps >= 0");
+    for (int d = 2; d < ctx->n_ops; d++)
+        if (!std::isfinite(beta[d])) return fail(ctx, LABFM_ERR_ARG, "beta has a non-finite entry");
+    if (nsteps == 0) return LABFM_OK;
+    return run_step_burgers(ctx, beta, u, v, field_dtype, dt, nsteps, frozen);
 }
 
 }  // extern "C"

@@ -1,4 +1,4 @@
-// Operator application (Eq. general_do) and the RK4 driver (Sec. 4.1).
+// Operator application (Eq. general_do) and the RK4 driver (Sec. 5.1).
 //
 // Both are streaming gather-sums over the CSR stencils: per stencil entry e of node i, read
 // col[e] and the weights w[e][*] once (HBM), gather f[col[e]] (stays in L2: the field is
@@ -524,6 +524,268 @@ labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int fdt, doub
         g.acc = ctx->rk_acc.ptr;
         g.sa = ctx->rk_stage_a.ptr;
         g.sb = ctx->rk_stage_b.ptr;
+    }
+    LABFM_CUDA_TRY(ctx, cudaGraphLaunch(g.exec, s));
+    return LABFM_OK;
+}
+
+}  // namespace labfm
+
+// ---------------------------------------------------------------------------------------------
+// Burgers' equation (Sec. 5.3, eq. burgers): du/dt = -(u d/dx + v d/dy) u + sum_{d>=2} beta_d L^d u,
+// and the same for v, by the classical RK4 scheme.  The advection coefficients depend on the
+// field, so d/dx and d/dy stay separate sums; the linear operators combine into one weight.
+// ---------------------------------------------------------------------------------------------
+namespace labfm {
+namespace {
+
+// per entry: (w^0, w^1, sum_{d>=2} beta_d w^d), the last summed in double
+template <class WT>
+__global__ void k_burg_combine(int64_t nnz, int n_ops, const WT *__restrict__ w, WT *__restrict__ wb, double b2,
+                               double b3, double b4, double b5, double b6, double b7)
+{
+    const double bb[6] = {b2, b3, b4, b5, b6, b7};
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const WT *we = w + e * n_ops;
+        double s = 0.0;
+        for (int d = 2; d < n_ops; d++) s += bb[d - 2] * (double)we[d];
+        wb[3 * e] = we[0];
+        wb[3 * e + 1] = we[1];
+        wb[3 * e + 2] = (WT)s;
+    }
+}
+
+// One RK4 stage for the pair (u, v).  With the stage's source fields (su, sv):
+//   A_x(s)_i = sum_j (s_j - s_i) w^0,  A_y(s)_i = sum_j (s_j - s_i) w^1,  B(s)_i = sum_j (s_j - s_i) wl
+//   F_u = -(su_i A_x(su) + sv_i A_y(su)) + B(su),   F_v = -(su_i A_x(sv) + sv_i A_y(sv)) + B(sv)
+// (0 on frozen nodes), then the stage updates of k_rk4_stage for both fields; acc and nxt hold
+// u in [0, n) and v in [n, 2n).  Sums in double unless fields and weights are both float.
+template <class FT, class WT, int UNR>
+__global__ void __launch_bounds__(APPLY_THREADS) k_burgers_stage(int64_t n, const int64_t *__restrict__ row_ptr,
+                                                                 const int32_t *__restrict__ col,
+                                                                 const WT *__restrict__ wb, const FT *__restrict__ su,
+                                                                 const FT *__restrict__ sv, FT *__restrict__ u,
+                                                                 FT *__restrict__ v, FT *__restrict__ acc,
+                                                                 FT *__restrict__ nxt,
+                                                                 const uint8_t *__restrict__ frozen, int stage, FT dt,
+                                                                 int lg_g)
+{
+    using AT = typename std::conditional<std::is_same<FT, float>::value && std::is_same<WT, float>::value, float,
+                                         double>::type;
+    const int G = 1 << lg_g;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t i = ((int64_t)blockIdx.x * APPLY_THREADS + threadIdx.x) >> lg_g;
+    const bool live = i < n;
+    int64_t rs = 0, re = 0;
+    AT ui = 0, vi = 0;
+    if (live) {
+        rs = row_ptr[i];
+        re = row_ptr[i + 1];
+        ui = (AT)su[i];
+        vi = (AT)sv[i];
+    }
+    AT s[6] = {0, 0, 0, 0, 0, 0};  // A_x(u), A_y(u), B(u), A_x(v), A_y(v), B(v)
+    for (int64_t base = rs; base < re; base += (int64_t)G * UNR) {
+        int cj[UNR];
+        AT w0[UNR], w1[UNR], wl[UNR];
+#pragma unroll
+        for (int q = 0; q < UNR; q++) {
+            const int64_t e = base + (int64_t)q * G + lane;
+            if (e < re) {
+                cj[q] = __ldcs(col + e);
+                w0[q] = (AT)__ldcs(wb + 3 * e);
+                w1[q] = (AT)__ldcs(wb + 3 * e + 1);
+                wl[q] = (AT)__ldcs(wb + 3 * e + 2);
+            } else {
+                cj[q] = -1;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < UNR; q++) {
+            if (cj[q] >= 0) {
+                const AT du = (AT)su[cj[q]] - ui, dv = (AT)sv[cj[q]] - vi;
+                s[0] = fma(du, w0[q], s[0]);
+                s[1] = fma(du, w1[q], s[1]);
+                s[2] = fma(du, wl[q], s[2]);
+                s[3] = fma(dv, w0[q], s[3]);
+                s[4] = fma(dv, w1[q], s[4]);
+                s[5] = fma(dv, wl[q], s[5]);
+            }
+        }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int t = 0; t < 6; t++) s[t] += __shfl_xor_sync(0xffffffffu, s[t], o);
+    if (!live || lane != 0) return;
+    const bool fz = frozen && frozen[i];
+    const FT Fu = fz ? (FT)0 : (FT)(-(ui * s[0] + vi * s[1]) + s[2]);
+    const FT Fv = fz ? (FT)0 : (FT)(-(ui * s[3] + vi * s[4]) + s[5]);
+    const FT u0 = u[i], v0 = v[i];
+    switch (stage) {
+    case 0:
+        acc[i] = u0 + dt * (FT)(1.0 / 6.0) * Fu;
+        acc[n + i] = v0 + dt * (FT)(1.0 / 6.0) * Fv;
+        nxt[i] = u0 + dt * (FT)0.5 * Fu;
+        nxt[n + i] = v0 + dt * (FT)0.5 * Fv;
+        break;
+    case 1:
+        acc[i] = acc[i] + dt * (FT)(1.0 / 3.0) * Fu;
+        acc[n + i] = acc[n + i] + dt * (FT)(1.0 / 3.0) * Fv;
+        nxt[i] = u0 + dt * (FT)0.5 * Fu;
+        nxt[n + i] = v0 + dt * (FT)0.5 * Fv;
+        break;
+    case 2:
+        acc[i] = acc[i] + dt * (FT)(1.0 / 3.0) * Fu;
+        acc[n + i] = acc[n + i] + dt * (FT)(1.0 / 3.0) * Fv;
+        nxt[i] = u0 + dt * Fu;
+        nxt[n + i] = v0 + dt * Fv;
+        break;
+    default:
+        u[i] = acc[i] + dt * (FT)(1.0 / 6.0) * Fu;
+        v[i] = acc[n + i] + dt * (FT)(1.0 / 6.0) * Fv;
+        break;
+    }
+}
+
+template <class FT, class WT>
+cudaError_t launch_burg_stage_shape(labfm_ctx *ctx, Shape sh, const FT *su, const FT *sv, FT *u, FT *v, FT *acc,
+                                    FT *nxt, const uint8_t *frozen, int stage, double dt, cudaStream_t s)
+{
+    const unsigned blocks = blocks_for(ctx->n, sh.G);
+    auto args = [&](auto kern) {
+        kern<<<blocks, APPLY_THREADS, 0, s>>>(ctx->n, ctx->row_ptr.as<int64_t>(), ctx->col.as<int32_t>(),
+                                              ctx->wburg.as<WT>(), su, sv, u, v, acc, nxt, frozen, stage, (FT)dt,
+                                              log2_of(sh.G));
+    };
+    switch (sh.UNR) {
+    case 2: args(k_burgers_stage<FT, WT, 2>); break;
+    case 8: args(k_burgers_stage<FT, WT, 8>); break;
+    default: args(k_burgers_stage<FT, WT, 4>); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class FT, class WT>
+cudaError_t enqueue_burgers(labfm_ctx *ctx, void *u_, void *v_, int fdt, double dt, int64_t nsteps,
+                            const uint8_t *frozen, cudaStream_t s)
+{
+    const int64_t n = ctx->n;
+    FT *u = (FT *)u_, *v = (FT *)v_;
+    FT *acc = ctx->bu_acc.as<FT>(), *sa = ctx->bu_stage_a.as<FT>(), *sb = ctx->bu_stage_b.as<FT>();
+    // tune on stage 0, which reads u and v and writes only the work buffers
+    Shape sh;
+    cudaError_t e = autotune(
+        ctx, tune_key(ctx, 3, 2, fdt, ctx->wdtype), 1,
+        [&](Shape sp) {
+            return launch_burg_stage_shape<FT, WT>(ctx, sp, u, v, u, v, acc, sa, frozen, 0, dt, ctx->stream);
+        },
+        sh);
+    if (e != cudaSuccess) return e;
+    for (int64_t st = 0; st < nsteps; st++) {
+        if ((e = launch_burg_stage_shape<FT, WT>(ctx, sh, u, v, u, v, acc, sa, frozen, 0, dt, s)) != cudaSuccess)
+            return e;
+        if ((e = launch_burg_stage_shape<FT, WT>(ctx, sh, sa, sa + n, u, v, acc, sb, frozen, 1, dt, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_burg_stage_shape<FT, WT>(ctx, sh, sb, sb + n, u, v, acc, sa, frozen, 2, dt, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_burg_stage_shape<FT, WT>(ctx, sh, sa, sa + n, u, v, acc, (FT *)nullptr, frozen, 3, dt, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_burgers_dt(labfm_ctx *ctx, int fdt, void *u, void *v, double dt, int64_t nsteps,
+                               const uint8_t *frozen, cudaStream_t s)
+{
+    if (fdt == LABFM_F64)
+        return ctx->wdtype == LABFM_F64 ? enqueue_burgers<double, double>(ctx, u, v, fdt, dt, nsteps, frozen, s)
+                                        : enqueue_burgers<double, float>(ctx, u, v, fdt, dt, nsteps, frozen, s);
+    return ctx->wdtype == LABFM_F64 ? enqueue_burgers<float, double>(ctx, u, v, fdt, dt, nsteps, frozen, s)
+                                    : enqueue_burgers<float, float>(ctx, u, v, fdt, dt, nsteps, frozen, s);
+}
+
+}  // namespace
+
+labfm_status run_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int fdt, double dt,
+                              int64_t nsteps, const uint8_t *frozen)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ctx->n, nnz = ctx->nnz;
+    const size_t fsz = fdt == LABFM_F64 ? 8 : 4, wsz = ctx->wdtype == LABFM_F64 ? 8 : 4;
+    bool same_beta = ctx->wburg_valid;
+    for (int d = 2; d < ctx->n_ops && same_beta; d++) same_beta = (ctx->beta_burg[d] == beta[d]);
+    if (!same_beta) {
+        LABFM_CUDA_TRY(ctx, ctx->wburg.reserve(3 * wsz * (nnz > 0 ? nnz : 1)));
+        double b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int d = 2; d < ctx->n_ops; d++) b[d] = beta[d];
+        if (nnz > 0) {
+            const unsigned blocks = (unsigned)std::min<int64_t>((nnz + 255) / 256, (int64_t)ctx->num_sms * 32);
+            if (ctx->wdtype == LABFM_F64)
+                k_burg_combine<double><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<double>(),
+                                                               ctx->wburg.as<double>(), b[2], b[3], b[4], b[5], b[6],
+                                                               b[7]);
+            else
+                k_burg_combine<float><<<blocks, 256, 0, s>>>(nnz, ctx->n_ops, ctx->w.as<float>(),
+                                                              ctx->wburg.as<float>(), b[2], b[3], b[4], b[5], b[6],
+                                                              b[7]);
+            LABFM_CUDA_TRY(ctx, cudaGetLastError());
+        }
+        for (int d = 2; d < ctx->n_ops; d++) ctx->beta_burg[d] = beta[d];
+        ctx->wburg_valid = true;
+    }
+    LABFM_CUDA_TRY(ctx, ctx->bu_acc.reserve(2 * fsz * n));
+    LABFM_CUDA_TRY(ctx, ctx->bu_stage_a.reserve(2 * fsz * n));
+    LABFM_CUDA_TRY(ctx, ctx->bu_stage_b.reserve(2 * fsz * n));
+
+    StepGraph &g = ctx->graph_burgers;
+    const bool same = g.exec && g.u == u && g.v == v && g.frozen == frozen && g.dtype == fdt && g.dt == dt &&
+                      g.nsteps == nsteps && g.n == n && g.nnz == nnz && g.wdtype == ctx->wdtype &&
+                      g.row_ptr == ctx->row_ptr.ptr && g.col == ctx->col.ptr && g.wc == ctx->wburg.ptr &&
+                      g.acc == ctx->bu_acc.ptr && g.sa == ctx->bu_stage_a.ptr && g.sb == ctx->bu_stage_b.ptr;
+    if (!same) {
+        g.release();
+        if (!ctx->capture_stream) {
+            LABFM_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        }
+        LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // the combined weights, before the capture stream reads them
+        {
+            cudaError_t te = enqueue_burgers_dt(ctx, fdt, u, v, dt, 0, frozen, s);  // tuning only
+            if (te != cudaSuccess) return cuda_fail(ctx, te, "Burgers stage tuning");
+            LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        }
+        cudaGraph_t graph = nullptr;
+        LABFM_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_burgers_dt(ctx, fdt, u, v, dt, nsteps, frozen, ctx->capture_stream);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(ctx, e, "Burgers stage capture");
+        }
+        LABFM_CUDA_TRY(ctx, e2);
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
+        g.u = u;
+        g.v = v;
+        g.frozen = frozen;
+        g.dtype = fdt;
+        g.dt = dt;
+        g.nsteps = nsteps;
+        g.n = n;
+        g.nnz = nnz;
+        g.wdtype = ctx->wdtype;
+        g.row_ptr = ctx->row_ptr.ptr;
+        g.col = ctx->col.ptr;
+        g.wc = ctx->wburg.ptr;
+        g.acc = ctx->bu_acc.ptr;
+        g.sa = ctx->bu_stage_a.ptr;
+        g.sb = ctx->bu_stage_b.ptr;
     }
     LABFM_CUDA_TRY(ctx, cudaGraphLaunch(g.exec, s));
     return LABFM_OK;

@@ -1,4 +1,4 @@
-// FP64 weight build (Sec. 2.1-2.2): per node, monomials X and ABFs W of every neighbour,
+// FP64 weight build (Sec. 3.1-2.2): per node, monomials X and ABFs W of every neighbour,
 // M = sum_j X_j (outer) W_j (Eq. disc_form), Gaussian elimination with partial pivoting of
 // M Psi = C^d for all operators at once (Eq. lsys), and w_j^d = W_j . Psi^d (Eq. w_abf).
 //

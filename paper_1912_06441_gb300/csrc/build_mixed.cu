@@ -8,7 +8,7 @@
 //   B  k_mixed_invert (two threads per row, the matrix in shared memory): Gauss-Jordan
 //      inversion of M with partial pivoting (interchanges undone on the columns) -> M^-1.
 //   C  k_mixed_weights (CTA per node): Psi~ = M^-1 C~, w~ = W . Psi~, then `nref` refinement
-//      steps on the residual of the moment conditions of Sec. 2.1
+//      steps on the residual of the moment conditions of Sec. 3.1
 //          r = C~ - sum_j X_j w~_j   (FP64)        w~ <- w~ + W . (M^-1 r)
 //      and the physical weights w = h^-l_d w~.
 // Targets are scaled per operator d by h^(l_d - |alpha|), l_d = highest degree with a non-zero

@@ -31,6 +31,7 @@ struct DevBuf {
 struct StepGraph {
     cudaGraphExec_t exec = nullptr;
     const void *u = nullptr;
+    const void *v = nullptr;  // second field (Burgers' equation)
     const void *frozen = nullptr;
     int dtype = -1;
     double dt = 0;
@@ -76,7 +77,14 @@ struct labfm_ctx {
     int wcomb_dtype = -1;
     bool wcomb_valid = false;
     labfm::StepGraph graph;
-    cudaStream_t capture_stream = nullptr;  // private stream used only to record the RK4 graph
+    cudaStream_t capture_stream = nullptr;  // private stream used only to record the RK4 graphs
+
+    // RK4 of Burgers' equation: per entry (w^0, w^1, sum_{d>=2} beta_d w^d) in the weight type
+    bool grad01 = false;  // operators 0 and 1 of the built weights are d/dx and d/dy
+    labfm::DevBuf wburg, bu_acc, bu_stage_a, bu_stage_b;
+    double beta_burg[LABFM_MAX_OPS] = {0};
+    bool wburg_valid = false;
+    labfm::StepGraph graph_burgers;
 
     // launch shapes chosen by the apply / RK4 autotuner:
     // key (kind, n_ops, dtypes, size class of n, mean stencil size) -> (G << 8) | UNR
@@ -134,6 +142,8 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
 labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops, const double *C,
                        int precision, int weight_dtype, int32_t *node_status, int64_t *n_bad_out);
 cudaError_t launch_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int field_dtype, void *out);
+labfm_status run_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int field_dtype, double dt,
+                              int64_t nsteps, const uint8_t *frozen);
 labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int field_dtype, double dt, int64_t nsteps,
                       const uint8_t *frozen);
 

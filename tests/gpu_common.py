@@ -6,7 +6,7 @@ import numpy as np
 import labfm_synth as S
 import oracle
 
-# k -> h/s used by the order-k parity cases (each above the critical h/dr of Sec. 2.2)
+# k -> h/s used by the order-k parity cases (each above the critical h/dr of Sec. 3.2)
 HS = {1: 1.2, 2: 1.2, 3: 1.3, 4: 1.4, 5: 1.6, 6: 1.8, 7: 2.0, 8: 2.2}
 OPS = {1: ("dx", "dy"), 2: ("dx", "dy", "lap"), 3: ("dx", "dy", "lap"), 4: ("dx", "dy", "lap", "lap2"),
        5: ("dx", "dy", "lap", "lap2"), 6: ("dx", "dy", "lap", "lap3"), 7: ("dx", "dy", "lap", "lap3"),

@@ -1,4 +1,4 @@
-"""The heat equation with Dirichlet walls (Sec. 4.1) on the CUDA path: weights for the Laplacian
+"""The heat equation with Dirichlet walls (Sec. 5.1) on the CUDA path: weights for the Laplacian
 with one-sided stencils at the walls, RK4 through labfm_step with the wall nodes frozen at their
 prescribed values, run to the steady state.
 
@@ -19,7 +19,7 @@ from tests import gpu_common as G
 pytestmark = pytest.mark.gpu
 
 LEVELS = (0.2, 0.1, 0.05, 0.025, 0.0125)  # h/H of the table, h/dr = 2
-PRINTED = {  # Sec. 4.1, Table of steady-state errors: (error, rate) per level
+PRINTED = {  # Sec. 5.1, Table of steady-state errors: (error, rate) per level
     2: [(3.9e-3, None), (7.1e-4, 2.46), (1.1e-4, 2.73), (1.5e-5, 2.83), (2.2e-6, 2.78)],
     3: [(4.6e-4, None), (5.4e-5, 3.08), (9.3e-6, 2.54), (2.0e-6, 2.20), (4.7e-7, 2.10)],
     4: [(1.4e-4, None), (5.6e-6, 4.68), (2.2e-7, 4.67), (8.3e-9, 4.72), (2.9e-10, 4.83)],
@@ -68,7 +68,7 @@ def _spectral_radius(L, wall, iters=100):
 
 def _steady_by_rk4(L, ns, chunk=5000):
     """RK4 from zero interior values to t* = 8 pi^2 t = 100 with the walls frozen; the step is
-    Sec. 4.1's 0.05 h^2 (kappa = 1), or 0.8 x the RK4 stability radius over the spectral radius
+    Sec. 5.1's 0.05 h^2 (kappa = 1), or 0.8 x the RK4 stability radius over the spectral radius
     where that is smaller (the noisy k = 4 sets)."""
     import torch
 
@@ -88,7 +88,7 @@ def _steady_by_rk4(L, ns, chunk=5000):
 def test_heat_parity_small():
     """k = 4, h/H = 0.1: weights against the oracle at the FP64 floor, and 300 RK4 steps with
     the walls frozen at sin(pi x) / 0 against the oracle's RK4.  The step is 0.02 h^2, inside
-    the RK4 region for these sets (rho h^2 <= 110 at k = 4; Sec. 4.1's 0.05 h^2 is not, and a
+    the RK4 region for these sets (rho h^2 <= 110 at k = 4; Sec. 5.1's 0.05 h^2 is not, and a
     growing mode would amplify the rounding differences of the two summation orders)."""
     import torch
 

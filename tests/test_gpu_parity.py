@@ -123,7 +123,7 @@ def test_weights_parity_multi_chunk_stencils(k, hs):
                                       (8, 2.2, "quadratic"), (8, 2.8, "wendland_c2")])
 def test_weights_parity_dw0_form(k, hs, rbf):
     """LABFM_ABF_DW0_ONLY: every ABF element dW0/dr d^alpha|r| (the form the stability results of
-    Sec. 3.3 belong to), FP64 build against the oracle's dw0 form."""
+    Sec. 4.2 belong to), FP64 build against the oracle's dw0 form."""
     ns = S.jittered_lattice(36, hs, k, seed=40 + k, jitter=0.2)
     ops = G.OPS[k]
     _, rp, col, w, status, _ = G.gpu_run(ns, k, ops, rbf=rbf, abf_form="dw0")
@@ -244,11 +244,11 @@ def test_rk4_parity(dtype):
     import torch
 
     k = 4
-    # h/dr = 2 (as in Sec. 4.1) keeps every eigenvalue of this operator in the left half-plane
+    # h/dr = 2 (as in Sec. 5.1) keeps every eigenvalue of this operator in the left half-plane
     ns = S.jittered_lattice(32, 2.0, k, seed=71, jitter=0.2)
     ops = ("dx", "dy", "lap")
     L, rp, col, w, _, _ = G.gpu_run(ns, k, ops)
-    # diffusion-dominated advection-diffusion with the heat-equation step of Sec. 4.1
+    # diffusion-dominated advection-diffusion with the heat-equation step of Sec. 5.1
     # (dt = 0.05 h^2 / kappa): stable, so rounding differences are not amplified
     beta = np.array([-0.1, -0.05, 1.0])
     dt = 0.05 * ns.h[0] ** 2
@@ -270,7 +270,7 @@ def test_rk4_parity(dtype):
 
 def test_rk4_parity_order8_hyperviscosity():
     """The time-stepping operator at order 8: advection + diffusion + the -alpha nabla^8
-    hyperviscosity of Sec. 3.3 (alpha = 1e-3 h^8), quadratic ABFs in the dw0 form on +-0.2 dr
+    hyperviscosity of Sec. 4.2 (alpha = 1e-3 h^8), quadratic ABFs in the dw0 form on +-0.2 dr
     noise, where every eigenvalue has a non-positive real part; 30 steps against the oracle."""
     import torch
 

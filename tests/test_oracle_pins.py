@@ -43,7 +43,7 @@ def _printed_abfs():
 
 
 def _ghost_lattice(n_side, hs, jitter, seed):
-    """Noisy Cartesian nodes on [0,1]^2 plus a ghost strip wider than 2h (Sec. 3.1);
+    """Noisy Cartesian nodes on [0,1]^2 plus a ghost strip wider than 2h (Sec. 4.1);
     returns (xy, h, indices of the nodes inside the unit square)."""
     s = 1.0 / n_side
     g = int(np.ceil(2 * hs)) + 1
@@ -83,7 +83,7 @@ def test_x_vector_printed():
 
 
 def test_c_vectors_and_hyperviscosity_positions():
-    """C^x, C^y, C^L (Sec. 2) and the nabla^4 / nabla^6 element positions (Sec. 2.3)."""
+    """C^x, C^y, C^L (Sec. 2) and the nabla^4 / nabla^6 element positions (Sec. 4.2)."""
     nums = _paper_numbers()
 
     def nz(c):
@@ -103,7 +103,7 @@ def test_c_vectors_and_hyperviscosity_positions():
     assert nz(c8) == [36, 38, 40, 42, 44]
     assert list(c8[np.nonzero(c8)[0]]) == [1.0, 4.0, 6.0, 4.0, 1.0]
     with pytest.raises(ValueError):
-        S.op_c_vector("lap4", 6)  # only up to nabla^k (Sec. 2.3)
+        S.op_c_vector("lap4", 6)  # only up to nabla^k (Sec. 4.2)
 
 
 # ------------------------------------------------------------------------ RBFs
@@ -126,7 +126,7 @@ def _sympy_kernels():
 @pytest.mark.parametrize("rbf", ["cone", "quadratic", "wendland_c2", "wendland_c6", "gaussian"])
 def test_rbf_derivatives_vs_sympy(rbf):
     """W0 and its first three q-derivatives against symbolic differentiation of the
-    kernels as printed (Sec. 2.2, Appendix A; Wendland C2 from its standard form)."""
+    kernels as printed (Sec. 3.2, Appendix A; Wendland C2 from its standard form)."""
     sp, q, ker = _sympy_kernels()
     expr = ker[rbf]
     ders = [expr, sp.diff(expr, q), sp.diff(expr, q, 2), sp.diff(expr, q, 3)]
@@ -184,7 +184,7 @@ def test_r_derivatives_vs_sympy():
 
 @pytest.mark.parametrize("rbf", ["cone", "wendland_c2", "quadratic", "gaussian", "wendland_c6"])
 def test_abfs_match_printed_forms(rbf):
-    """ABF elements 1-14 against the closed forms printed in Sec. 2.2 and Appendix A:
+    """ABF elements 1-14 against the closed forms printed in Sec. 3.2 and Appendix A:
     elements 1-9 carry the dW0/dr, d2W0/dr2 and d3W0/dr3 brackets, elements 10-14
     only the dW0/dr bracket (truncation rule)."""
     rows = _printed_abfs()
@@ -244,7 +244,7 @@ def test_neighbours_vs_kdtree():
 
 def test_lattice_parity_zeros():
     """On an unperturbed lattice M has exact zeros where X_m W_n is odd in x or y
-    (Sec. 2.2: orthogonality of odd and even ABFs and monomials)."""
+    (Sec. 3.2: orthogonality of odd and even ABFs and monomials)."""
     ns = S.jittered_lattice(32, 2.5, 8, jitter=0.0, seed=1)
     q = np.array([0, 517])
     rp, col = oracle.neighbours(ns.xy, ns.h, True, queries=q)
@@ -296,7 +296,7 @@ def test_assembly_and_solve_vs_lapack():
 
 def test_power_of_two_scaling_is_exact():
     """Scaling positions, h and the box by 2 leaves rhat unchanged bit for bit, so the
-    weights of an l-th derivative scale by exactly 2^-l (Sec. 2.1: w ~ h^-l)."""
+    weights of an l-th derivative scale by exactly 2^-l (Sec. 3.1: w ~ h^-l)."""
     ns = S.jittered_lattice(24, 1.8, 6, seed=4)
     q = np.arange(0, ns.n, 7)
     ops = ("dx", "lap", "lap3")
@@ -315,7 +315,7 @@ def test_power_of_two_scaling_is_exact():
                                           (6, 2.0, "wendland_c2", 1e-9), (7, 2.2, "cone", 1e-8),
                                           (8, 2.5, "wendland_c2", 1e-8)])
 def test_polynomial_reproduction(k, hs, rbf, tol):
-    """Exact reproduction of polynomials up to degree k (Sec. 2.1): for a random polynomial
+    """Exact reproduction of polynomials up to degree k (Sec. 3.1): for a random polynomial
     of degree k, sum_j (f_j - f_i) w_ji^d equals C^d . D f at node i to rounding.  The
     tolerance is about 100x the measured FP64 floor of each order; a wrong term anywhere
     in X, M, the solve or the h-scaling gives O(1) errors."""
@@ -349,7 +349,7 @@ def test_polynomial_reproduction(k, hs, rbf, tol):
 
 
 def test_p6_order8_exact_to_rounding():
-    """Eq. (p6) with k = 8 and conic ABFs, h/dr = 2.5, ghost strip (Sec. 3.1): the degree-8
+    """Eq. (p6) with k = 8 and conic ABFs, h/dr = 2.5, ghost strip (Sec. 4.1): the degree-8
     test function is reproduced to rounding.  The error is a rounding floor: the long-double
     build of the same oracle cuts it by more than 100x (the paper quotes ~1e-14 for
     gradients and ~1e-13 for Laplacians, which the long-double build reaches)."""
@@ -378,7 +378,7 @@ def _slopes(errs, hh):
 @pytest.mark.parametrize("k,hs,grad_min,lap_min", [(2, 2.0, 1.8, 0.8), (4, 2.0, 3.7, 2.7),
                                                    (6, 2.0, 5.5, 4.6), (8, 2.5, 7.3, 6.5)])
 def test_convergence_orders(k, hs, grad_min, lap_min):
-    """Sec. 3.1 (Fig. glerror, conic ABFs, h/dr = 2, 2.5 for k = 8): the L2-norm error of
+    """Sec. 4.1 (Fig. glerror, conic ABFs, h/dr = 2, 2.5 for k = 8): the L2-norm error of
     gradients converges with order k and of the Laplacian with order k - 1 on noisy
     Cartesian nodes, here f = sin(2 pi x) cos(2 pi y) on the periodic unit square."""
     f = S.sincos_field()
@@ -400,7 +400,7 @@ def test_convergence_orders(k, hs, grad_min, lap_min):
 
 @pytest.mark.parametrize("k,hs,grad_min,lap_min", [(2, 2.0, 1.5, 1.5), (4, 3.0, 3.4, 2.6)])
 def test_one_sided_stencils_keep_order(k, hs, grad_min, lap_min):
-    """Sec. 3.1 / 4.1: at walls without ghost nodes the stencils are one-sided and, with a
+    """Sec. 4.1 / 4.1: at walls without ghost nodes the stencils are one-sided and, with a
     large enough h/dr, keep the interior order up to k = 4 (gradient ~k, Laplacian ~k-1).
     The error measure is the median over the wall band (the typical stencil): a few
     undersampled one-sided stencils dominate an L2 norm there, which the paper's own
@@ -424,7 +424,7 @@ def test_one_sided_stencils_keep_order(k, hs, grad_min, lap_min):
 
 
 def test_sph_limit():
-    """k = 1 collapses to SPH (Sec. 2, Sec. 5): on an unperturbed lattice, w^x_ji tends to
+    """k = 1 collapses to SPH (Sec. 2, Sec. 6): on an unperturbed lattice, w^x_ji tends to
     dV dW_ij/dx with the normalised kernel W = W0/h^2, and the gap shrinks with h/dr.  For
     the printed quadratic kernel (which integrates to 1/2) LABFM matches SPH with twice
     that kernel, as the weights do not depend on a constant factor of W0."""
@@ -474,7 +474,7 @@ def test_status_undersampled_and_collinear():
 
 
 def test_rk4_linear_system_is_taylor_polynomial():
-    """Classical RK4 (Sec. 4.1) on the linear system du/dt = A u advances by the degree-4
+    """Classical RK4 (Sec. 5.1) on the linear system du/dt = A u advances by the degree-4
     Taylor polynomial of exp(dt A)."""
     ns = S.jittered_lattice(8, 1.4, 2, seed=2)
     rp, col = oracle.neighbours(ns.xy, ns.h, True)
@@ -514,7 +514,7 @@ def test_rk4_linear_system_is_taylor_polynomial():
 @pytest.mark.parametrize("rbf", ["cone", "wendland_c2", "quadratic", "gaussian", "wendland_c6"])
 def test_abfs_dw0_form_is_the_printed_dW0_bracket(rbf):
     """abf_form "dw0" (every element truncated to dW0/dr d^alpha|r|): elements 1-14 equal dW0/dr
-    times the printed dW0/dr bracket of Sec. 2.2 / Appendix A, for every kernel."""
+    times the printed dW0/dr bracket of Sec. 3.2 / Appendix A, for every kernel."""
     rows = [r for r in _printed_abfs() if r[1] == "d1"]
     assert sorted(e for e, _, _ in rows) == list(range(1, 15))
     for x, y in [(0.3, 0.5), (-1.1, 0.4), (0.9, -1.2), (-0.2, -0.35)]:
@@ -531,7 +531,7 @@ def test_abfs_dw0_form_is_the_printed_dW0_bracket(rbf):
 
 
 def _global_matrix(n, rp, col, w):
-    """A with (A f)_i = sum_j (f_j - f_i) w_ji (the global derivative matrix of Sec. 3.3)."""
+    """A with (A f)_i = sum_j (f_j - f_i) w_ji (the global derivative matrix of Sec. 4.2)."""
     A = np.zeros((n, n))
     node = np.repeat(np.arange(n), np.diff(rp))
     np.add.at(A, (node, col), w)
@@ -559,7 +559,7 @@ def _noise_limits():
 
 @pytest.mark.parametrize("k,hdr,limit", _noise_limits())
 def test_laplacian_noise_limits_dw0_form(k, hdr, limit):
-    """Sec. 3.3, Table of noise limits: with the quadratic ABFs the Laplacian has no growing mode
+    """Sec. 4.2, Table of noise limits: with the quadratic ABFs the Laplacian has no growing mode
     for noise below the printed limit.  Checked at half the limit (at most 0.5 dr of displacement;
     each coordinate uniform in +-eps/sqrt(2), so no node moves further than eps) on two node sets:
     the largest real part of the spectrum stays at rounding level."""
@@ -572,7 +572,7 @@ def test_laplacian_noise_limits_dw0_form(k, hdr, limit):
 
 def test_chain_form_breaks_the_noise_limits():
     """The same points with the chain-rule terms kept in elements 1-9 (Appendix A as printed)
-    have modes that grow at rates far above rounding level: the stability results of Sec. 3.3
+    have modes that grow at rates far above rounding level: the stability results of Sec. 4.2
     are those of the dW0/dr-only form.  (Records why both forms exist.)"""
     for k, hdr, limit in _noise_limits():
         eps = min(0.5, limit / 2)
@@ -581,7 +581,7 @@ def test_chain_form_breaks_the_noise_limits():
 
 
 def test_convective_spectrum_on_a_regular_lattice():
-    """Sec. 3.3 (eigenvalues of the convective operator, regular lattice, h/dr = 2): the
+    """Sec. 4.2 (eigenvalues of the convective operator, regular lattice, h/dr = 2): the
     real parts are at rounding level for the quadratic and Wendland ABFs, larger by orders of
     magnitude (yet small) for the Gaussian, and substantial for the cone, whose dW0/dr does not
     vanish at q = 2.  At h/dr = 2 lattice neighbours sit on the support edge, so only kernels
@@ -600,7 +600,7 @@ def test_convective_spectrum_on_a_regular_lattice():
     assert ratio("quadratic", 4, form="chain") > 0.1
 
 
-# ------------------------------------------------------------- heat equation (Sec. 4.1)
+# ------------------------------------------------------------- heat equation (Sec. 5.1)
 
 
 def _heat_table():
@@ -614,7 +614,7 @@ def _heat_table():
 
 
 def heat_steady_errors(k, levels, seed):
-    """Oracle steady states of the Dirichlet heat problem of Sec. 4.1 (quadratic ABFs in the
+    """Oracle steady states of the Dirichlet heat problem of Sec. 5.1 (quadratic ABFs in the
     dW0/dr form, h/dr = 2, interior noise eps/dr = 0.5) at the given h/H, as relative L2 errors
     against sinh(pi (1 - y)) sin(pi x) / sinh(pi) over all nodes."""
     field = S.HeatSteadyField()
@@ -633,7 +633,7 @@ def heat_steady_errors(k, levels, seed):
 
 @pytest.mark.parametrize("k", [2, 3, 4])
 def test_heat_steady_state_table(k):
-    """Sec. 4.1, Table of steady-state errors (inhomogeneous Dirichlet walls): the oracle's
+    """Sec. 5.1, Table of steady-state errors (inhomogeneous Dirichlet walls): the oracle's
     errors at h/H = 0.2 ... 0.025 fall at the printed rates (k = 2, 4: each rate within 0.7 of
     the printed one; k = 3, whose printed rates drift from 3.1 to 2.1: each within [2, 3.6])
     and lie within a factor 5 of the printed errors (the node sets are random draws of the same
@@ -653,7 +653,7 @@ def test_heat_steady_state_table(k):
 
 
 def test_heat_frozen_rk4_reaches_the_steady_state():
-    """RK4 with the wall nodes frozen at their prescribed values (Sec. 4.1), run from zero
+    """RK4 with the wall nodes frozen at their prescribed values (Sec. 5.1), run from zero
     interior values to t* = 8 pi^2 t = 100, lands on the sparse direct solution of the same
     semi-discrete steady problem: two independent routes to one answer."""
     k = 4
@@ -663,8 +663,60 @@ def test_heat_frozen_rk4_reaches_the_steady_state():
                              rbf="quadratic", abf_form="dw0")["w"]
     ub = S.HeatSteadyField().boundary(ns.xy, ns.wall)
     uss = oracle.steady_state(rp, col, w, [1.0], ub, ns.wall)
-    dt = 0.05 * ns.h[0] ** 2  # Sec. 4.1: 0.05 h^2 / kappa, kappa = 1
+    dt = 0.05 * ns.h[0] ** 2  # Sec. 5.1: 0.05 h^2 / kappa, kappa = 1
     nsteps = int(math.ceil(100.0 / (8.0 * math.pi ** 2) / dt))
     u = oracle.rk4(rp, col, w, np.array([1.0]), ub, dt, nsteps, frozen=ns.wall.astype(np.uint8))
     assert np.array_equal(u[ns.wall], ub[ns.wall])
     assert np.abs(u - uss).max() < 1e-9 * np.abs(uss).max()
+
+
+# --------------------------------------------------------- Burgers' equation (Sec. 5.3)
+
+
+def test_cole_solution_solves_burgers():
+    """The exact solution used for the periodic Burgers' problem: u(x, 0) = sin(2 pi x), the
+    printed truncation (A_n < 1e-16 for n >= 30 at Re = 100), and the PDE
+    u_t + u u_x = u_xx / Re itself by central differences at points across the steepening front,
+    relative to the size of its terms (the series loses ~7 digits to cancellation near x = 1/2,
+    where the denominator is ~e^-2z; the printed decay factor, 4 times smaller, leaves a
+    residual of the order of the terms)."""
+    sol = S.ColeBurgersSolution(Re=100.0)
+    x = np.linspace(0.0, 1.0, 41)
+    assert np.abs(sol.u(x, 0.0) - np.sin(2 * np.pi * x)).max() < 1e-9
+    assert np.all(sol.An[29:] < 1e-16) and sol.An[0] > 1e-3
+    d = 1e-4
+    for t in (0.1, 0.3, 0.6):
+        xs = np.array([0.05, 0.21, 0.4, 0.47, 0.55, 0.8])
+        ut = (sol.u(xs, t + d) - sol.u(xs, t - d)) / (2 * d)
+        ux = (sol.u(xs + d, t) - sol.u(xs - d, t)) / (2 * d)
+        uxx = (sol.u(xs + d, t) - 2 * sol.u(xs, t) + sol.u(xs - d, t)) / d ** 2
+        scale = np.abs(ut) + np.abs(sol.u(xs, t) * ux) + np.abs(uxx / 100.0)
+        assert np.all(np.abs(ut + sol.u(xs, t) * ux - uxx / 100.0) <= 1e-3 * scale + 1e-6), t
+
+
+def _burgers_error(k, nside, T, Re=100.0, eps=0.2, seed=7):
+    ns = S.jittered_lattice(nside, 2.0, k, jitter=eps / math.sqrt(2), seed=seed)
+    rp, col = oracle.neighbours(ns.xy, ns.h, True)
+    C = np.stack([S.op_c_vector(o, k) for o in ("dx", "dy", "lap")])
+    w = oracle.build_weights(ns.xy, ns.h, True, rp, col, C, k=k, rbf="quadratic", abf_form="dw0")["w"]
+    h = ns.h[0]
+    dt = min(0.2 * h / 1.0, 0.05 * h * h * Re)  # Eq. (tstep), max|u| = 1
+    nsteps = int(math.ceil(T / dt))
+    u0 = np.sin(2 * np.pi * ns.xy[:, 0])
+    u, v = oracle.rk4_burgers(rp, col, w, [0.0, 0.0, 1.0 / Re], u0, np.zeros(ns.n), T / nsteps, nsteps)
+    ex = S.ColeBurgersSolution(Re).u(ns.xy[:, 0], T)
+    return np.linalg.norm(u - ex) / np.linalg.norm(ex), np.abs(v).max()
+
+
+def test_burgers_periodic_convergence():
+    """Sec. 5.3, periodic Burgers' problem at Re = 100 (quadratic ABFs in the dW0/dr form,
+    h/dr = 2, eps/dr = 0.2, RK4 with the time step of Eq. (tstep)): at t = 0.4, as the front
+    steepens, the error against Cole's solution falls between h/H = 2/81 and 2/161 at rates near
+    k (the paper: between k - 1 and k; measured 2.8, 3.9, 5.7 for k = 2, 4, 6), and v stays 0."""
+    bands = {2: (1.5, 3.5), 4: (3.0, 4.8), 6: (5.0, 6.8)}
+    for k, (lo, hi) in bands.items():
+        e1, v1 = _burgers_error(k, 81, 0.4)
+        e2, v2 = _burgers_error(k, 161, 0.4)
+        rate = math.log(e1 / e2) / math.log(161 / 81)
+        assert lo <= rate <= hi, (k, e1, e2, rate)
+        assert v1 == 0.0 and v2 == 0.0
