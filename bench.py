@@ -31,8 +31,8 @@ import labfm_synth as S  # noqa: E402
 
 METRIC = "order-8 weight build Mnodes/s; apply GB/s vs HBM; mixed vs FP64 at ≤1e-8 err"
 N_SIDE, HS, K, JITTER = 512, 2.2, 8, 0.3
-SKIP_LARGE = False  # --skip-large: leave out the heat-equation and Burgers runs (graph-replayed
-                    # steps), the 4.2M-node RK4 and the 1M-node wall workloads
+SKIP_LARGE = False  # --skip-large: leave out the heat-equation, Burgers and Poisson runs (thousands
+                    # of small launches), the 4.2M-node RK4 and the 1M-node wall workloads
 OPS = ("dx", "dy", "lap", "lap4")
 def workload_name():
     return (f"2D periodic jittered lattice {N_SIDE}x{N_SIDE} (+-{JITTER}s), h={HS}s, Wendland C2, order {K} "
@@ -302,6 +302,7 @@ def extra_measurements(torch, P, dev, local_rank, ns, field, hbm):
     if not SKIP_LARGE:
         out["heat_dirichlet_k4"] = heat_dirichlet(torch, P, dev, local_rank)
         out["burgers_cole_k4"] = burgers_cole(torch, P, dev, local_rank)
+        out["poisson_periodic_k4"] = poisson_periodic(torch, P, dev, local_rank)
         out["rk4_2048"] = rk4_large(torch, P, dev, local_rank)
         out["walls_1m_variable_order"] = walls_variable_order(torch, P, dev, local_rank)
     return out
@@ -390,6 +391,40 @@ def burgers_cole(torch, P, dev, local_rank, k=4, nside=161, Re=100.0, T=1.0, chu
            "steps": nsteps, "dt": dt, "ms": ms, "steps_per_s": nsteps / (ms * 1e-3), "us_per_step": ms * 1e3 / nsteps,
            "l2_err_vs_cole": float(np.linalg.norm(got - ex) / np.linalg.norm(ex)),
            "max_abs_v": float(v.abs().max())}
+    L.close()
+    return res
+
+
+def poisson_periodic(torch, P, dev, local_rank, k=4, nside=512, tol=1e-10):
+    """The periodic Poisson problem of Sec. 5.2 at 512 x 512 nodes (h/dr = 2, eps/dr = 0.5,
+    quadratic ABFs in the dW0/dr form, order 4): phi = sin 2 pi x sin 2 pi y, node 0 fixed,
+    solved by labfm_solve (Jacobi-preconditioned BiCGStab, FP64) from zero to a relative
+    residual of 1e-10; error against the exact solution."""
+    ns = S.jittered_lattice(nside, 2.0, k, jitter=0.5 / math.sqrt(2), seed=3)
+    L = P.Labfm(local_rank)
+    L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), True)
+    nbad = L.build_weights(np.stack([S.op_c_vector("lap", k)]), uniform_order=k, rbf="quadratic", abf_form="dw0",
+                           node_status=torch.zeros(ns.n, dtype=torch.int32, device=dev))
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    ex = np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    f = -8 * np.pi ** 2 * ex
+    f[0] = ex[0]
+    dm = np.zeros(ns.n, np.uint8)
+    dm[0] = 1
+    fd, dmd = torch.from_numpy(f).to(dev), torch.from_numpy(dm).to(dev)
+    phi = torch.zeros(ns.n, dtype=torch.float64, device=dev)
+    L.solve(0, fd, phi, dmd, tol=tol, max_iter=100000)  # warm (allocations, first launches)
+    phi.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters, resid = L.solve(0, fd, phi, dmd, tol=tol, max_iter=100000)  # synchronises at the end
+    ms = (time.perf_counter() - t0) * 1e3
+    got = phi.cpu().numpy()
+    spmv_bytes = L.nnz * (4 + 8) + ns.n * (8 + 8 + 8 + 8)  # col, w; row_ptr, x_i, out, one dot operand
+    res = {"nodes": ns.n, "nnz": int(L.nnz), "order": k, "flagged_nodes": int(nbad), "tol": tol, "iterations": iters,
+           "true_rel_residual": resid, "ms": ms, "us_per_iteration": ms * 1e3 / max(iters, 1),
+           "l2_err_vs_exact": float(np.linalg.norm(got - ex) / np.linalg.norm(ex)),
+           "spmv_bytes": spmv_bytes, "timing": "host wall clock around the call (it synchronises)"}
     L.close()
     return res
 
@@ -695,7 +730,7 @@ def run_labfm(args, rank, world, local_rank):
 
 
 PROFILE_CASES = ("apply_f32_512", "apply_f64_512", "stage_df_1024", "stage_f32_1024", "build_fp64_256",
-                 "build_mixed_256", "build_mixed_tc_256")
+                 "build_mixed_256", "build_mixed_tc_256", "solve_poisson_512")
 
 
 def profile_case(name):
@@ -707,7 +742,21 @@ def profile_case(name):
 
     dev = torch.device("cuda", 0)
     L = P.Labfm(0)
-    if name.startswith("apply") or name.startswith("build"):
+    if name == "solve_poisson_512":
+        # the periodic Poisson workload of bench.py, 40 BiCGStab iterations (stopped short on purpose)
+        ns = S.jittered_lattice(512, 2.0, 4, jitter=0.5 / math.sqrt(2), seed=3)
+        L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), True)
+        L.build_weights(np.stack([S.op_c_vector("lap", 4)]), uniform_order=4, rbf="quadratic", abf_form="dw0")
+        f = torch.from_numpy(-8 * np.pi ** 2 * np.sin(2 * np.pi * ns.xy[:, 0]) * np.sin(2 * np.pi * ns.xy[:, 1])).to(dev)
+        dm = torch.zeros(ns.n, dtype=torch.uint8, device=dev)
+        dm[0] = 1
+        for _ in range(2):
+            phi = torch.zeros(ns.n, dtype=torch.float64, device=dev)
+            try:
+                L.solve(0, f, phi, dm, tol=1e-14, max_iter=40)
+            except P.LabfmError:
+                pass
+    elif name.startswith("apply") or name.startswith("build"):
         n_side = 512 if name.startswith("apply") else 256
         ns = S.jittered_lattice(n_side, HS, K, jitter=JITTER, seed=2)
         C = np.stack([S.op_c_vector(o, K) for o in OPS])
@@ -749,7 +798,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-large", action="store_true",
-                    help="leave out the heat-equation, Burgers, 2048^2 RK4 and 1000^2 wall workloads (profiler captures)")
+                    help="leave out the heat-equation, Burgers, Poisson, 2048^2 RK4 and 1000^2 wall workloads (profiler captures)")
     ap.add_argument("--n-side", type=int, default=512,
                     help="lattice side (default 512; smaller sizes are for profiler captures only)")
     ap.add_argument("--profile", choices=PROFILE_CASES, default=None,

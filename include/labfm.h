@@ -43,7 +43,8 @@ typedef enum {
     LABFM_ERR_CAPACITY = 4, /* a size limit of this build was exceeded (message says which) */
     LABFM_ERR_SINGULAR = 5, /* weights built, but >= 1 node was flagged (see node_status) */
     LABFM_ERR_TIMEOUT = 6,  /* a bounded device wait gave up */
-    LABFM_ERR_STATE = 7     /* call out of order (e.g. apply before build_weights) */
+    LABFM_ERR_STATE = 7,    /* call out of order (e.g. apply before build_weights) */
+    LABFM_ERR_NOT_CONVERGED = 8 /* an iterative solve stopped short of its tolerance */
 } labfm_status;
 
 /* Fundamental RBFs W0(q), q = |r|/h, support [0, 2] (Sec. 3.2, Appendix A). */
@@ -236,6 +237,32 @@ labfm_status labfm_step(labfm_ctx *ctx, const double *beta, void *u, int field_d
  */
 labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int field_dtype,
                                 double dt, int64_t nsteps, const uint8_t *frozen);
+
+/*
+ * Solve the global linear system of Sec. 5.2 (eq. poisson_system), A Phi = F, whose rows are the
+ * local operators of operator `op`: A_ij = w^op_ji for j != i and A_ii = -sum_j w^op_ji, so that
+ * (A Phi)_i = L^op_i(Phi) (e.g. op = the Laplacian: Poisson's equation, eq. poisson).  Where
+ * dirichlet[i] != 0 the row is replaced by the identity (Sec. 5.2, Dirichlet rows: A_ii = 1,
+ * A_ij = 0, F_i = g_i), so that Phi_i = f[i] there.  The matrix is not formed: its products are
+ * stencil sums over the context's stencils.  Stabilised bi-conjugate gradients (van der Vorst
+ * 1992) with a Jacobi preconditioner (diag A), as in Sec. 5.2; all vectors and scalars in FP64 and
+ * in device memory, iterations enqueued in chunks of 16 with one host read of the state per chunk.
+ * Stops when ||F - A Phi|| <= tol ||F|| (the recurrence residual), or after max_iter iterations.
+ * With a periodic node set A has the constants in its null space: fix at least one node with the
+ * Dirichlet mask.
+ *   op          operator index (0 <= op < n_ops), weights of either dtype
+ *   f           device double[n]: F (the values g_i at Dirichlet nodes)
+ *   phi         device double[n]: the initial guess in (its Dirichlet entries are set to f on
+ *               entry, and then stay exact), the solution out (distinct from f)
+ *   dirichlet   device uint8[n] or NULL
+ *   tol         relative residual target, > 0;  max_iter >= 1
+ *   iters_out   host, may be NULL: iterations taken
+ *   resid_out   host, may be NULL: the true relative residual ||F - A Phi|| / ||F|| at exit
+ * Returns LABFM_ERR_NOT_CONVERGED on breakdown or when max_iter ends the iteration (phi holds the
+ * last iterate).  Synchronises the context stream.  LABFM_ERR_STATE before labfm_build_weights.
+ */
+labfm_status labfm_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet,
+                         double tol, int max_iter, int *iters_out, double *resid_out);
 
 /*
  * Stencil search that allocates nothing.  (The paper has no counterpart: this is an interface

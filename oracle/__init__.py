@@ -254,6 +254,25 @@ def steady_state(row_ptr, col, w, beta, u_fixed, frozen):
     return u
 
 
+def solve_operator(row_ptr, col, w, op, f, dirichlet=None):
+    """The global system of Sec. 5.2 (eq. poisson_system): A Phi = F with A_ij = w^op_ji (j != i),
+    A_ii = -sum_j w^op_ji, and identity rows (Phi_i = f_i) where ``dirichlet`` is set; by a sparse
+    direct solve."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+
+    w = np.asarray(w, dtype=np.float64)
+    beta = np.zeros(w.shape[1])
+    beta[op] = 1.0
+    A = operator_matrix(row_ptr, col, w, beta).tolil()
+    b = np.array(f, dtype=np.float64, copy=True)
+    if dirichlet is not None:
+        for i in np.nonzero(np.asarray(dirichlet))[0]:
+            A.rows[i] = [int(i)]
+            A.data[i] = [1.0]
+    return spl.spsolve(sp.csc_matrix(A), b)
+
+
 def rbf_derivs(rbf, q, precision="f64"):
     d = np.zeros(4)
     _lib(precision).orc_rbf_derivs(RBF[rbf], float(q), _ptr(d))

@@ -34,14 +34,14 @@ def precision_code(precision: str, refine: int | None = None) -> int:
 DTYPE = {"f64": 0, "f32": 1}
 NODE = {"ok": 0, "singular": 1, "undersampled": 2, "nonfinite": 3}
 STATUS = {0: "LABFM_OK", 1: "LABFM_ERR_ARG", 2: "LABFM_ERR_CUDA", 3: "LABFM_ERR_NOMEM", 4: "LABFM_ERR_CAPACITY",
-          5: "LABFM_ERR_SINGULAR", 6: "LABFM_ERR_TIMEOUT", 7: "LABFM_ERR_STATE"}
+          5: "LABFM_ERR_SINGULAR", 6: "LABFM_ERR_TIMEOUT", 7: "LABFM_ERR_STATE", 8: "LABFM_ERR_NOT_CONVERGED"}
 PMAX = 44
 MAX_OPS = 8
 
 # every symbol include/labfm.h declares
 C_FUNCTIONS = ["labfm_create", "labfm_destroy", "labfm_last_error", "labfm_set_stream", "labfm_build_neighbours",
                "labfm_get_neighbours", "labfm_build_weights", "labfm_get_weights", "labfm_apply", "labfm_step",
-               "labfm_step_burgers", "labfm_build_neighbours_noalloc"]
+               "labfm_step_burgers", "labfm_solve", "labfm_build_neighbours_noalloc"]
 NOALLOC_MAX_NODES = 262144  # LABFM_NOALLOC_MAX_NODES
 
 _lib = None
@@ -87,6 +87,8 @@ def load_library(path: str | None = None, build_if_missing: bool = False):
     lib.labfm_step.restype = I
     lib.labfm_step_burgers.argtypes = [P, P, P, P, I, D, I64, P]
     lib.labfm_step_burgers.restype = I
+    lib.labfm_solve.argtypes = [P, I, P, P, P, D, I, ct.POINTER(I), ct.POINTER(D)]
+    lib.labfm_solve.restype = I
     lib.labfm_build_neighbours_noalloc.argtypes = [I, P, I64, P, P, I, P, P, P, P, I64, ct.POINTER(I64)]
     lib.labfm_build_neighbours_noalloc.restype = I
     if path is None:
@@ -291,3 +293,20 @@ class Labfm:
         self._check(self.lib.labfm_step_burgers(self._ctx, b.ctypes.data_as(ct.c_void_p), pu, pv, fdt, float(dt),
                                                 int(nsteps), pz))
         return u, v
+
+    def solve(self, op: int, f, phi, dirichlet=None, tol: float = 1e-10, max_iter: int = 10000):
+        """Solve A Phi = F (Sec. 5.2, eq. poisson_system) with the rows of operator `op` and
+        identity rows where ``dirichlet`` is set, by Jacobi-preconditioned BiCGStab; phi (float64,
+        the initial guess) is overwritten.  Returns (iterations, true relative residual); raises
+        LabfmError(LABFM_ERR_NOT_CONVERGED) if the tolerance is not reached."""
+        torch = _torch()
+        pf = self._dev(f, torch.float64, "f", self.n)
+        pp = self._dev(phi, torch.float64, "phi", self.n)
+        pd = None if dirichlet is None else self._dev(dirichlet, torch.uint8, "dirichlet", self.n)
+        self._sync_stream()
+        iters, resid = ct.c_int(0), ct.c_double(0.0)
+        st = self.lib.labfm_solve(self._ctx, int(op), pf, pp, pd, float(tol), int(max_iter), ct.byref(iters),
+                                  ct.byref(resid))
+        self.last_solve = (iters.value, resid.value)
+        self._check(st)
+        return iters.value, resid.value

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblabfm.so")
-SOURCES = ["api.cu", "neighbours.cu", "build_fp64.cu", "build_mixed.cu", "apply.cu"]
+SOURCES = ["api.cu", "neighbours.cu", "build_fp64.cu", "build_mixed.cu", "apply.cu", "solve.cu"]
 HEADERS = ["labfm_internal.cuh", "abf.cuh", "df64.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -222,7 +222,7 @@ void labfm_destroy(labfm_ctx *ctx)
                       &ctx->cell_nodes, &ctx->counts, &ctx->scan_tmp, &ctx->misc, &ctx->w,
                       &ctx->status_tmp, &ctx->wtilde, &ctx->mscratch, &ctx->mrecs, &ctx->mwstore, &ctx->wcomb, &ctx->rk_acc,
                       &ctx->rk_stage_a, &ctx->rk_stage_b, &ctx->wburg, &ctx->bu_acc, &ctx->bu_stage_a,
-                      &ctx->bu_stage_b};
+                      &ctx->bu_stage_b, &ctx->sol_w, &ctx->sol_vec, &ctx->sol_part};
     for (DevBuf *b : bufs) b->release();
     ctx->graph.release();
     ctx->graph_burgers.release();
@@ -352,6 +352,19 @@ labfm_status labfm_step(labfm_ctx *ctx, const double *beta, void *u, int field_d
         if (!std::isfinite(beta[d])) return fail(ctx, LABFM_ERR_ARG, "beta has a non-finite entry");
     if (nsteps == 0) return LABFM_OK;
     return run_step(ctx, beta, u, field_dtype, dt, nsteps, frozen);
+}
+
+labfm_status labfm_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet, double tol,
+                         int max_iter, int *iters_out, double *resid_out)
+{
+    if (!ctx) return LABFM_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->have_weights) return fail(ctx, LABFM_ERR_STATE, "labfm_build_weights must come first");
+    if (op < 0 || op >= ctx->n_ops) return fail(ctx, LABFM_ERR_ARG, "op must index a built operator");
+    if (!f || !phi) return fail(ctx, LABFM_ERR_ARG, "null f or phi");
+    if ((const void *)f == (const void *)phi) return fail(ctx, LABFM_ERR_ARG, "f and phi must be distinct buffers");
+    if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(ctx, LABFM_ERR_ARG, "need tol > 0 and max_iter >= 1");
+    return run_solve(ctx, op, f, phi, dirichlet, tol, max_iter, iters_out, resid_out);
 }
 
 labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int field_dtype, double dt,

@@ -86,6 +86,9 @@ struct labfm_ctx {
     bool wburg_valid = false;
     labfm::StepGraph graph_burgers;
 
+    // implicit solves (BiCGStab): operator weights as one FP64 stream, nine vectors, partial sums
+    labfm::DevBuf sol_w, sol_vec, sol_part;
+
     // launch shapes chosen by the apply / RK4 autotuner:
     // key (kind, n_ops, dtypes, size class of n, mean stencil size) -> (G << 8) | UNR
     std::unordered_map<uint64_t, uint32_t> tuned;
@@ -142,6 +145,8 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
 labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops, const double *C,
                        int precision, int weight_dtype, int32_t *node_status, int64_t *n_bad_out);
 cudaError_t launch_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int field_dtype, void *out);
+labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet, double tol,
+                       int max_iter, int *iters_out, double *resid_out);
 labfm_status run_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int field_dtype, double dt,
                               int64_t nsteps, const uint8_t *frozen);
 labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int field_dtype, double dt, int64_t nsteps,

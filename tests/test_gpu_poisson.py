@@ -1,0 +1,117 @@
+"""Implicit solves (Sec. 5.2): labfm_solve's Jacobi-preconditioned BiCGStab on the global operator
+matrix against the oracle's sparse direct solve of the same system, periodic (one node fixed) and
+with Dirichlet walls, and the even-order convergence pattern of the periodic Poisson problem."""
+import math
+
+import numpy as np
+import pytest
+
+import labfm_synth as S
+import oracle
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1912_06441_gb300 as P
+
+    P.load_library()
+
+
+def _periodic_problem(k, nside, hdr=2.0, eps=0.5, seed=3, weight_dtype="f64"):
+    ns = S.jittered_lattice(nside, hdr, k, jitter=eps / math.sqrt(2), seed=seed)
+    L, rp, col, w, status, _ = G.gpu_run(ns, k, ("lap",), rbf="quadratic", abf_form="dw0", weight_dtype=weight_dtype)
+    assert (status == 0).all()
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    ex = np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    f = -8 * np.pi ** 2 * ex
+    dm = np.zeros(ns.n, np.uint8)
+    dm[0] = 1
+    f[0] = ex[0]
+    return ns, L, ex, f, dm
+
+
+def _gpu_solve(L, f, dm, tol=1e-13, max_iter=20000):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    phi = torch.zeros(len(f), dtype=torch.float64, device=dev)
+    iters, resid = L.solve(0, torch.from_numpy(f).to(dev), phi, torch.from_numpy(dm).to(dev), tol=tol,
+                           max_iter=max_iter)
+    return phi.cpu().numpy(), iters, resid
+
+
+def _oracle_solve(ns, k, f, dm):
+    rp, col = oracle.neighbours(ns.xy, ns.h, ns.periodic, ns.lo, ns.hi)
+    w = oracle.build_weights(ns.xy, ns.h, ns.periodic, rp, col, G.c_matrix(k, ("lap",)), k=k, rbf="quadratic",
+                             abf_form="dw0", lo=ns.lo, hi=ns.hi)["w"]
+    return oracle.solve_operator(rp, col, w, 0, f, dm)
+
+
+@pytest.mark.parametrize("weight_dtype", ["f64", "f32"])
+def test_poisson_periodic_matches_oracle(weight_dtype):
+    """k = 4, 40^2 nodes, node 0 fixed: BiCGStab to a relative residual of 1e-13 equals the
+    oracle's direct solution on the oracle's weights to 1e-8 (FP64 weights; FP32 weights change
+    the operator by ~1e-7 relative, which the solution follows at 1e-4)."""
+    ns, L, ex, f, dm = _periodic_problem(4, 40, weight_dtype=weight_dtype)
+    phi, iters, resid = _gpu_solve(L, f, dm)
+    assert resid <= 1e-12 and 0 < iters < 20000
+    ref = _oracle_solve(ns, 4, f, dm)
+    tol = 1e-8 if weight_dtype == "f64" else 1e-4
+    assert np.abs(phi - ref).max() <= tol * np.abs(ref).max(), np.abs(phi - ref).max()
+    assert phi[0] == pytest.approx(ex[0], abs=1e-13)
+
+
+def test_poisson_dirichlet_walls_matches_oracle():
+    """Dirichlet rows (Sec. 5.2): the heat-equation node set with walls (k = 4, 41^2 nodes),
+    phi = sin(2 pi x) sin(2 pi y) + x y prescribed on the walls, f = nabla^2 phi inside."""
+    k = 4
+    ns = S.dirichlet_square(41, 2.0, k, 0.5, seed=304)
+    L, rp, col, w, status, _ = G.gpu_run(ns, k, ("lap",), rbf="quadratic", abf_form="dw0")
+    assert (status == 0).all()
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    ex = np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y) + x * y
+    f = np.where(ns.wall, ex, -8 * np.pi ** 2 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y))
+    dm = ns.wall.astype(np.uint8)
+    phi, iters, resid = _gpu_solve(L, f, dm)
+    ref = _oracle_solve(ns, k, f, dm)
+    assert np.abs(phi - ref).max() <= 1e-8 * np.abs(ref).max()
+    assert np.array_equal(phi[ns.wall], ex[ns.wall])
+    assert np.linalg.norm(phi - ex) / np.linalg.norm(ex) < 1e-4  # order-4 one-sided stencils at the walls
+
+
+def test_poisson_even_order_pattern_on_gpu():
+    """The periodic convergence orders of Sec. 5.2 from the GPU solves: 2 for k = 3, 4 for k = 5
+    (odd k gives the order of k - 1), between h/H = 2/20 and 2/80."""
+    for k, (lo, hi) in {3: (1.8, 2.3), 5: (3.6, 4.4)}.items():
+        errs = []
+        for nside in (20, 80):
+            ns, L, ex, f, dm = _periodic_problem(k, nside)
+            phi, _, _ = _gpu_solve(L, f, dm, tol=1e-12)
+            errs.append(np.linalg.norm(phi - ex) / np.linalg.norm(ex))
+            L.close()
+        rate = math.log2(errs[0] / errs[1]) / 2.0
+        assert lo <= rate <= hi, (k, errs, rate)
+
+
+def test_solve_reports_non_convergence_and_bad_arguments():
+    import torch
+
+    from paper_1912_06441_gb300 import LabfmError
+
+    ns, L, ex, f, dm = _periodic_problem(4, 24)
+    dev = torch.device("cuda", 0)
+    phi = torch.zeros(ns.n, dtype=torch.float64, device=dev)
+    fd = torch.from_numpy(f).to(dev)
+    with pytest.raises(LabfmError) as ei:
+        L.solve(0, fd, phi, torch.from_numpy(dm).to(dev), tol=1e-14, max_iter=3)
+    assert "NOT_CONVERGED" in str(ei.value) and L.last_solve[0] == 3
+    with pytest.raises(LabfmError):
+        L.solve(1, fd, phi)  # only one operator was built
+    with pytest.raises(LabfmError):
+        L.solve(0, fd, fd)  # f and phi the same buffer

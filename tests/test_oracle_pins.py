@@ -720,3 +720,37 @@ def test_burgers_periodic_convergence():
         rate = math.log(e1 / e2) / math.log(161 / 81)
         assert lo <= rate <= hi, (k, e1, e2, rate)
         assert v1 == 0.0 and v2 == 0.0
+
+
+# ------------------------------------------------------------ Poisson's equation (Sec. 5.2)
+
+
+def poisson_periodic_error(k, nside, hdr, seed=3, eps=0.5):
+    """Periodic Poisson problem of Sec. 5.2 (phi = sin 2 pi x sin 2 pi y, quadratic ABFs in the
+    dW0/dr form): the global system A^L Phi = F by the oracle's direct solve, with node 0 held
+    at its exact value to fix the constant of the periodic null space."""
+    ns = S.jittered_lattice(nside, hdr, k, jitter=eps / math.sqrt(2), seed=seed)
+    rp, col = oracle.neighbours(ns.xy, ns.h, True)
+    w = oracle.build_weights(ns.xy, ns.h, True, rp, col, S.op_c_vector("lap", k)[None, :], k=k, rbf="quadratic",
+                             abf_form="dw0")["w"]
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    ex = np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    f = -8 * np.pi ** 2 * ex
+    dm = np.zeros(ns.n, np.uint8)
+    dm[0] = 1
+    f[0] = ex[0]
+    phi = oracle.solve_operator(rp, col, w, 0, f, dm)
+    return np.linalg.norm(phi - ex) / np.linalg.norm(ex)
+
+
+def test_poisson_periodic_even_order_pattern():
+    """Sec. 5.2, periodic test case: the solution converges at order 2 for k = 2 and 3, 4 for
+    k = 4 and 5, and 8 for k = 8 (h/dr = 3 there): odd k gives the order of k - 1.  Rates from
+    h/H = 2/20 to 2/80 (overall), noise eps/dr = 0.5; bands from the printed orders (k = 4 reads
+    3.3 - 4.8 across node draws, single stencils set the finest errors)."""
+    bands = {2: (1.8, 2.3), 3: (1.8, 2.3), 4: (3.3, 5.0), 5: (3.6, 4.4), 8: (7.0, 9.5)}
+    for k, (lo, hi) in bands.items():
+        hdr = 2.0 if k <= 6 else 3.0
+        e20, e80 = poisson_periodic_error(k, 20, hdr), poisson_periodic_error(k, 80, hdr)
+        rate = math.log2(e20 / e80) / 2.0
+        assert lo <= rate <= hi, (k, e20, e80, rate)
