@@ -143,7 +143,7 @@ labfm_status labfm_get_neighbours(labfm_ctx *ctx, const int64_t **row_ptr, const
                                   int64_t *n, int64_t *nnz);
 
 /*
- * Weights (Sec. 3.1-2.2): per node i, build M_i = sum_j X_ji (outer) W_ji
+ * Weights (Sec. 3.1-3.2): per node i, build M_i = sum_j X_ji (outer) W_ji
  * (Eq. disc_form) from the Taylor monomials X (Sec. 2) and the ABFs
  * W = D(W0)|r_ji (Sec. 3.2; elements >= 10 keep only the dW0/dr term, Appendix A),
  * solve M_i Psi^d = C^d (Eq. lsys) by Gaussian elimination with partial pivoting,

@@ -1,4 +1,4 @@
-// FP64 weight build (Sec. 3.1-2.2): per node, monomials X and ABFs W of every neighbour,
+// FP64 weight build (Sec. 3.1-3.2): per node, monomials X and ABFs W of every neighbour,
 // M = sum_j X_j (outer) W_j (Eq. disc_form), Gaussian elimination with partial pivoting of
 // M Psi = C^d for all operators at once (Eq. lsys), and w_j^d = W_j . Psi^d (Eq. w_abf).
 //
@@ -6,7 +6,9 @@
 // memory in chunks of NB neighbours: Xs[j][m], Ws[j][n] (row stride LDX, a multiple of 4 so
 // that a thread's 4 consecutive W values are one 32-byte load).  The p x p assembly is tiled
 // 2 x 4 per thread in registers across chunks.  The augmented matrix [M | Chat] (Chat_alpha =
-// C_alpha h^-|alpha|) is eliminated in shared memory, one column per step.
+// C_alpha h^-|alpha|) is then eliminated in shared memory, one column per step, in the space of
+// the X staging (X is not read again), which keeps a CTA within a quarter of the SM's shared
+// memory: four CTAs per SM.
 #include <cmath>
 #include <vector>
 
@@ -25,7 +27,9 @@ template <int K> struct Cfg {
     static constexpr int RG = (P + TM - 1) / TM, CG = (P + TN - 1) / TN;
     static_assert(RG * CG <= BUILD_THREADS, "assembly tile grid exceeds the CTA");
     static constexpr int LDA = P + MAX_OPS + 1;  // augmented row stride (odd: fewer bank conflicts)
-    static constexpr size_t smem_bytes = sizeof(double) * ((size_t)2 * NB * LDX + (size_t)P * LDA);
+    // the augmented matrix reuses the X staging (X is not read after the assembly)
+    static_assert((size_t)P * LDA <= (size_t)NB * LDX, "augmented matrix fits the X staging");
+    static constexpr size_t smem_bytes = sizeof(double) * ((size_t)2 * NB * LDX);
 };
 
 struct BuildArgs {
@@ -47,14 +51,15 @@ struct BuildArgs {
 };
 
 template <int K>
-__global__ void __launch_bounds__(BUILD_THREADS, 3) k_build_fp64(BuildArgs A)
+__global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64(BuildArgs A)
 {
     using C = Cfg<K>;
     constexpr int P = C::P, LDX = C::LDX, NB = C::NB, LDA = C::LDA, TM = C::TM, TN = C::TN;
     extern __shared__ __align__(16) double smem[];
     double *Xs = smem;                 // [NB][LDX]
     double *Ws = Xs + NB * LDX;        // [NB][LDX]
-    double *Am = Ws + NB * LDX;        // [P][LDA]  augmented [M | Chat]
+    double *Am = Xs;                   // [P][LDA]  augmented [M | Chat], over the X staging
+    __shared__ double s_psi[PMAX * MAX_OPS];  // Psi^d, kept while X and W are staged again
     __shared__ int s_piv;
     __shared__ double s_inv;
     __shared__ double s_invpiv[P];  // 1 / pivot of each column, reused by the back substitution
@@ -227,6 +232,11 @@ __global__ void __launch_bounds__(BUILD_THREADS, 3) k_build_fp64(BuildArgs A)
             __syncthreads();
         }
         const bool singular = (s_flag & 5) != 0;  // no weights from a failed elimination
+        for (int t = tid; t < P * n_ops; t += BUILD_THREADS) {
+            const int m = t / n_ops, d = t - m * n_ops;
+            s_psi[m * MAX_OPS + d] = Am[m * LDA + P + d];
+        }
+        __syncthreads();
 
         // weights w_j^d = W_j . Psi^d
         for (int ch = 0; ch < nchunks; ch++) {
@@ -253,7 +263,7 @@ __global__ void __launch_bounds__(BUILD_THREADS, 3) k_build_fp64(BuildArgs A)
                 if (!singular) {
                     const double *W = Ws + j * LDX;
 #pragma unroll 4
-                    for (int m = 0; m < P; m++) s = fma(W[m], Am[m * LDA + P + d], s);
+                    for (int m = 0; m < P; m++) s = fma(W[m], s_psi[m * MAX_OPS + d], s);
                     if (!isfinite(s)) {
                         atomicOr(&s_flag, 2);
                         s = 0.0;
