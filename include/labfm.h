@@ -246,7 +246,10 @@ labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, voi
  * A_ij = 0, F_i = g_i), so that Phi_i = f[i] there.  The matrix is not formed: its products are
  * stencil sums over the context's stencils.  Stabilised bi-conjugate gradients (van der Vorst
  * 1992) with a Jacobi preconditioner (diag A), as in Sec. 5.2; all vectors and scalars in FP64 and
- * in device memory, iterations enqueued in chunks of 16 with one host read of the state per chunk.
+ * in device memory, iterations recorded in chunks of 16 into a CUDA graph with one host read of the
+ * state per chunk.  The product's launch shape (lanes per node x entries in flight, 3 x 3 shapes)
+ * is timed once per problem class (floor(log2 n), mean stencil size) on a context, as for
+ * labfm_apply (n >= 4096, stream not capturing).
  * Stops when ||F - A Phi|| <= tol ||F|| (the recurrence residual), or after max_iter iterations.
  * With a periodic node set A has the constants in its null space: fix at least one node with the
  * Dirichlet mask.

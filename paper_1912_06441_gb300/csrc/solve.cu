@@ -8,9 +8,10 @@
 //   rho = (r^, r); beta = (rho / rho_old)(alpha / omega); p = r + beta (p - omega v); y = M^-1 p
 //   v = A y; alpha = rho / (r^, v); s = r - alpha v; z = M^-1 s; t = A z
 //   omega = (t, s) / (t, t); x += alpha y + omega z; r = s - omega t
-// Every scalar stays in device memory: per-block partial dot products, then a one-block kernel
-// that forms the scalars, so an iteration is eight launches with no host round trip (16 of them
-// recorded once per call into a CUDA graph and replayed).  A device flag ends the iteration
+// Every scalar stays in device memory: each reducing launch writes per-block partial dot
+// products and its last block (an atomic ticket) sums them in a fixed order and forms the
+// scalars, so an iteration is five launches with no host round trip (16 iterations recorded once
+// per call into a CUDA graph and replayed).  A device flag ends the iteration
 // (converged, breakdown, iteration limit); later launches see it and return at once, so the host
 // reads the flag once per chunk.
 #include <algorithm>
@@ -23,9 +24,8 @@ namespace labfm {
 namespace {
 
 constexpr int SOLVE_THREADS = 256;
-constexpr int SOLVE_G = 4;    // lanes per node in the stencil sums
-constexpr int SOLVE_UNR = 4;  // stencil entries in flight per lane
-constexpr int SCALAR_THREADS = 1024;
+constexpr int SOLVE_G = 4;      // lanes per node in the setup
+constexpr int SOLVE_G_MAX = 16; // the product's lanes per node are tuned in {4, 8, 16} x entries in flight {2, 4, 8}
 constexpr int SOLVE_VEC_MAX_BLOCKS = 1024;
 
 // device-resident solver state
@@ -37,6 +37,7 @@ struct SolveState {
     int skip;          // ||s|| already within the tolerance: omega = 0, x += alpha y, r = s
     int iters;
     int max_iter;
+    unsigned int ticket;  // blocks of the current launch that have written their partial sums
 };
 
 // sum over the block (fixed order: deterministic); the result is valid in thread 0
@@ -51,6 +52,81 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     if (threadIdx.x == 0)
         for (int w = 0; w < SOLVE_THREADS / 32; w++) s += sh[w];
     return s;
+}
+
+// The scalars of the step that follows a reduction (thread 0 of the reducing block):
+//   step 0 (after the setup):       rnorm2, bnorm2, rho = rnorm2, alpha = omega = rho_old = 1, beta = 0
+//   step 2 (after v = A y):         alpha = rho / (rhat, v)
+//   step 4 (after t = A z):         skip = (s, s) <= tol2; omega = (t, s) / (t, t)
+//   step 5 (after the x, r update): rho_old = rho, rho = (rhat, r), rnorm2, iters++, convergence,
+//                                   beta of the next iteration
+// s0..s2: the sums of the three partial slots; s3: the sum of part2 (the (s, s) of phase 2).
+__device__ void form_scalars(int step, double s0, double s1, double s2, double s3, SolveState *st)
+{
+    switch (step) {
+    case 0:
+        st->rnorm2 = s0;
+        st->bnorm2 = s1;
+        st->tol2 *= s1 > 0.0 ? s1 : 1.0;
+        st->rho = s0;
+        st->rho_old = st->alpha = st->omega = 1.0;
+        st->beta = 0.0;
+        st->iters = 0;
+        st->done = (s0 <= st->tol2) ? 1 : 0;
+        break;
+    case 2:
+        st->alpha = st->rho / s0;
+        if (s0 == 0.0 || !isfinite(st->alpha)) st->done = 2;
+        break;
+    case 4:
+        st->snorm2 = s3;
+        st->skip = s3 <= st->tol2 ? 1 : 0;
+        st->omega = st->skip ? 0.0 : (s2 > 0.0 ? s0 / s2 : 0.0);
+        if (!isfinite(st->omega)) st->done = 2;
+        break;
+    default:
+        st->rho_old = st->rho;
+        st->rho = s0;
+        st->rnorm2 = s1;
+        st->iters += 1;
+        if (s1 <= st->tol2) st->done = 1;
+        else if (st->rho == 0.0 || st->omega == 0.0 || !isfinite(s1)) st->done = 2;
+        else if (st->iters >= st->max_iter) st->done = 3;
+        else {
+            st->beta = (st->rho / st->rho_old) * (st->alpha / st->omega);
+            if (!isfinite(st->beta)) st->done = 2;
+        }
+        break;
+    }
+}
+
+// Called by every block after thread 0 has written the block's partials: the last block to
+// arrive sums all partials in a fixed order (deterministic) and forms the scalars of `step`.
+// The partials are read through L2 (__ldcg) after the other blocks' fence-then-ticket.
+__device__ void last_block_scalars(int nblk, int step, const double *part, int nblk2, const double *part2,
+                                   SolveState *st, double *sh)
+{
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->ticket, 1u) == (unsigned)(nblk - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;  // uniform per block
+    __threadfence();
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += SOLVE_THREADS) {
+        a += __ldcg(part + 3 * k);
+        b += __ldcg(part + 3 * k + 1);
+        c += __ldcg(part + 3 * k + 2);
+    }
+    if (part2)
+        for (int k = threadIdx.x; k < nblk2; k += SOLVE_THREADS) d += __ldcg(part2 + 3 * k);
+    const double s0 = block_sum(a, sh), s1 = block_sum(b, sh), s2 = block_sum(c, sh), s3 = block_sum(d, sh);
+    if (threadIdx.x == 0) {
+        form_scalars(step, s0, s1, s2, s3, st);
+        st->ticket = 0u;  // the next reduction starts from zero (it is a later launch)
+    }
 }
 
 // weights of operator d as one contiguous FP64 stream, the Jacobi scaling 1 / A_ii, and the
@@ -83,9 +159,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_setup(int64_t n, const 
 }
 
 // out = A x with the matrix in its global form (Sec. 5.2): out_i = A_ii x_i + sum_j w_ji x_j, one
-// FP64 multiply-add per stencil entry (Dirichlet rows: out_i = x_i); SOLVE_G lanes per node with
-// SOLVE_UNR entries in flight per lane; fused partial dot products (a1 . out), (out . out) into
+// FP64 multiply-add per stencil entry (Dirichlet rows: out_i = x_i); G lanes per node with UNR
+// entries in flight per lane; fused partial dot products (a1 . out), (out . out) into
 // part[3 block + 0, 2]
+template <int G, int UNR>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const int64_t *__restrict__ row_ptr,
                                                              const int32_t *__restrict__ col,
                                                              const double *__restrict__ wd,
@@ -93,12 +170,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const i
                                                              const uint8_t *__restrict__ dirichlet,
                                                              const double *__restrict__ x, double *__restrict__ out,
                                                              const double *__restrict__ a1, double *__restrict__ part,
-                                                             const SolveState *__restrict__ st)
+                                                             int step, int nblk2, const double *__restrict__ part2,
+                                                             SolveState *__restrict__ st)
 {
     if (st && st->done) return;
     __shared__ double sh[SOLVE_THREADS / 32];
-    const int lane = threadIdx.x & (SOLVE_G - 1);
-    const int64_t i = ((int64_t)blockIdx.x * SOLVE_THREADS + threadIdx.x) / SOLVE_G;
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t i = ((int64_t)blockIdx.x * SOLVE_THREADS + threadIdx.x) / G;
     const bool live = i < n;
     int64_t rs = 0, re = 0;
     double xi = 0.0;
@@ -108,20 +186,20 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const i
         xi = x[i];
     }
     double acc = 0.0;
-    for (int64_t base = rs; base < re; base += SOLVE_G * SOLVE_UNR) {
-        int cj[SOLVE_UNR];
-        double wv[SOLVE_UNR];
+    for (int64_t base = rs; base < re; base += G * UNR) {
+        int cj[UNR];
+        double wv[UNR];
 #pragma unroll
-        for (int q = 0; q < SOLVE_UNR; q++) {
-            const int64_t e = base + q * SOLVE_G + lane;
+        for (int q = 0; q < UNR; q++) {
+            const int64_t e = base + q * G + lane;
             cj[q] = e < re ? __ldcs(col + e) : -1;
             wv[q] = e < re ? __ldcs(wd + e) : 0.0;
         }
 #pragma unroll
-        for (int q = 0; q < SOLVE_UNR; q++)
+        for (int q = 0; q < UNR; q++)
             if (cj[q] >= 0) acc = fma(x[cj[q]], wv[q], acc);
     }
-    for (int o = SOLVE_G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     double d1 = 0.0, d3 = 0.0;
     if (live && lane == 0) {
         const double yi = (dirichlet && dirichlet[i]) ? xi : fma(adiag[i], xi, acc);
@@ -137,6 +215,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const i
         part[3 * blockIdx.x + 1] = 0.0;
         part[3 * blockIdx.x + 2] = s3;
     }
+    if (step >= 0) last_block_scalars(gridDim.x, step, part, nblk2, part2, st, sh);
 }
 
 // the element-wise updates of one iteration, by phase
@@ -151,11 +230,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_vec(int64_t n, int phas
                                                             double *__restrict__ s, double *__restrict__ z,
                                                             const double *__restrict__ t,
                                                             const double *__restrict__ dinv,
-                                                            double *__restrict__ part, const SolveState *__restrict__ st)
+                                                            double *__restrict__ part, SolveState *__restrict__ st)
 {
     if (phase != 0 && st->done) return;
     __shared__ double sh[SOLVE_THREADS / 32];
-    const double alpha = st->alpha, omega = st->omega, beta = st->beta;
+    const double alpha = st ? st->alpha : 0.0, omega = st ? st->omega : 0.0, beta = st ? st->beta : 0.0;
     double d1 = 0.0, d2 = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         switch (phase) {
@@ -200,75 +279,34 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_vec(int64_t n, int phas
         part[3 * blockIdx.x + 1] = s2;
         part[3 * blockIdx.x + 2] = 0.0;
     }
+    // phase 0 forms the starting scalars, phase 3 those of the next iteration; the (s, s) of
+    // phase 2 is read with omega after t = A z
+    if (st && (phase == 0 || phase == 3)) last_block_scalars(gridDim.x, phase == 0 ? 0 : 5, part, 0, nullptr, st, sh);
 }
 
-// one block: sum the partials in a fixed order and form the scalars
-//   step 0 (after the setup):       rnorm2, bnorm2, rho = rnorm2, alpha = omega = rho_old = 1, beta = 0
-//   step 2 (after v = A y):         alpha = rho / (rhat, v)
-//   step 4 (after t = A z):         skip = (s, s) <= tol2 [part2]; omega = (t, s) / (t, t)
-//   step 5 (after the x, r update): rho_old = rho, rho = (rhat, r), rnorm2, iters++, convergence,
-//                                   beta of the next iteration
-__global__ void __launch_bounds__(SCALAR_THREADS) k_solve_scalars(int nblk, int step, const double *__restrict__ part,
-                                                                 int nblk2, const double *__restrict__ part2,
-                                                                 SolveState *__restrict__ st)
+template <int G, int UNR>
+cudaError_t launch_spmv_t(int64_t n, const int64_t *rp, const int32_t *cl, const double *wd, const double *adiag,
+                          const uint8_t *dirichlet, const double *x, double *out, const double *a1, double *part,
+                          int step, int nblk2, const double *part2, SolveState *st, cudaStream_t q)
 {
-    if (step != 0 && st->done) return;
-    __shared__ double sh[4][SCALAR_THREADS];
-    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
-    for (int k = threadIdx.x; k < nblk; k += SCALAR_THREADS) {
-        a += part[3 * k];
-        b += part[3 * k + 1];
-        c += part[3 * k + 2];
-    }
-    if (part2)
-        for (int k = threadIdx.x; k < nblk2; k += SCALAR_THREADS) d += part2[3 * k];
-    sh[0][threadIdx.x] = a;
-    sh[1][threadIdx.x] = b;
-    sh[2][threadIdx.x] = c;
-    sh[3][threadIdx.x] = d;
-    __syncthreads();
-    for (int h = SCALAR_THREADS / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h)
-            for (int q = 0; q < 4; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const double s0 = sh[0][0], s1 = sh[1][0], s2 = sh[2][0], s3 = sh[3][0];
-    switch (step) {
-    case 0:
-        st->rnorm2 = s0;
-        st->bnorm2 = s1;
-        st->tol2 *= s1 > 0.0 ? s1 : 1.0;
-        st->rho = s0;
-        st->rho_old = st->alpha = st->omega = 1.0;
-        st->beta = 0.0;
-        st->iters = 0;
-        st->done = (s0 <= st->tol2) ? 1 : 0;
-        break;
-    case 2:
-        st->alpha = st->rho / s0;  // s0 = (rhat, v)
-        if (s0 == 0.0 || !isfinite(st->alpha)) st->done = 2;
-        break;
-    case 4:
-        st->snorm2 = s3;  // (s, s) from the update of s
-        st->skip = s3 <= st->tol2 ? 1 : 0;
-        st->omega = st->skip ? 0.0 : (s2 > 0.0 ? s0 / s2 : 0.0);  // (s, t) / (t, t)
-        if (!isfinite(st->omega)) st->done = 2;
-        break;
-    default:
-        st->rho_old = st->rho;
-        st->rho = s0;
-        st->rnorm2 = s1;
-        st->iters += 1;
-        if (s1 <= st->tol2) st->done = 1;
-        else if (st->rho == 0.0 || st->omega == 0.0 || !isfinite(s1)) st->done = 2;
-        else if (st->iters >= st->max_iter) st->done = 3;
-        else {
-            st->beta = (st->rho / st->rho_old) * (st->alpha / st->omega);
-            if (!isfinite(st->beta)) st->done = 2;
-        }
-        break;
-    }
+    const unsigned blocks = (unsigned)((n * G + SOLVE_THREADS - 1) / SOLVE_THREADS);
+    k_solve_spmv<G, UNR><<<blocks, SOLVE_THREADS, 0, q>>>(n, rp, cl, wd, adiag, dirichlet, x, out, a1, part, step,
+                                                          nblk2, part2, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(int G, int UNR, int64_t n, const int64_t *rp, const int32_t *cl, const double *wd,
+                        const double *adiag, const uint8_t *dirichlet, const double *x, double *out, const double *a1,
+                        double *part, int step, int nblk2, const double *part2, SolveState *st, cudaStream_t q)
+{
+#define LABFM_SPMV_CASE(g, u)                                                                                   \
+    if (G == g && UNR == u) return launch_spmv_t<g, u>(n, rp, cl, wd, adiag, dirichlet, x, out, a1, part, step, \
+                                                       nblk2, part2, st, q);
+    LABFM_SPMV_CASE(4, 2) LABFM_SPMV_CASE(4, 4) LABFM_SPMV_CASE(4, 8)
+    LABFM_SPMV_CASE(8, 2) LABFM_SPMV_CASE(8, 4) LABFM_SPMV_CASE(8, 8)
+    LABFM_SPMV_CASE(16, 2) LABFM_SPMV_CASE(16, 4) LABFM_SPMV_CASE(16, 8)
+#undef LABFM_SPMV_CASE
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -278,9 +316,9 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
 {
     cudaStream_t s = ctx->stream;
     const int64_t n = ctx->n, nnz = ctx->nnz;
-    const int nblk_mv = (int)((n * SOLVE_G + SOLVE_THREADS - 1) / SOLVE_THREADS);
+    const int nblk_setup = (int)((n * SOLVE_G + SOLVE_THREADS - 1) / SOLVE_THREADS);
     const int nblk_vec = (int)std::min<int64_t>((n + SOLVE_THREADS - 1) / SOLVE_THREADS, SOLVE_VEC_MAX_BLOCKS);
-    const size_t npart = 3 * (size_t)std::max(nblk_mv, nblk_vec);
+    const size_t npart = 3 * (size_t)std::max<int64_t>((n * SOLVE_G_MAX + SOLVE_THREADS - 1) / SOLVE_THREADS, nblk_vec);
     LABFM_CUDA_TRY(ctx, ctx->sol_w.reserve(sizeof(double) * (nnz > 0 ? nnz : 1)));
     LABFM_CUDA_TRY(ctx, ctx->sol_vec.reserve(sizeof(double) * 10 * n));
     LABFM_CUDA_TRY(ctx, ctx->sol_part.reserve(sizeof(double) * (npart + 3 * (size_t)nblk_vec) + sizeof(SolveState)));
@@ -294,44 +332,84 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
     const int32_t *cl = ctx->col.as<int32_t>();
     const double *wd = ctx->sol_w.as<double>();
     if (ctx->wdtype == LABFM_F64)
-        k_solve_setup<double><<<nblk_mv, SOLVE_THREADS, 0, s>>>(n, rp, ctx->w.as<double>(), ctx->n_ops, op,
+        k_solve_setup<double><<<nblk_setup, SOLVE_THREADS, 0, s>>>(n, rp, ctx->w.as<double>(), ctx->n_ops, op,
                                                                ctx->sol_w.as<double>(), dinv, adiag, dirichlet, f, phi);
     else
-        k_solve_setup<float><<<nblk_mv, SOLVE_THREADS, 0, s>>>(n, rp, ctx->w.as<float>(), ctx->n_ops, op,
+        k_solve_setup<float><<<nblk_setup, SOLVE_THREADS, 0, s>>>(n, rp, ctx->w.as<float>(), ctx->n_ops, op,
                                                               ctx->sol_w.as<double>(), dinv, adiag, dirichlet, f, phi);
     LABFM_CUDA_TRY(ctx, cudaGetLastError());
     SolveState init{};
     init.tol2 = tol * tol;
     init.max_iter = max_iter;
     LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(st, &init, sizeof(SolveState), cudaMemcpyHostToDevice, s));
-    auto spmv = [&](cudaStream_t q, const double *x, double *out, const double *a1, const SolveState *gate) {
-        k_solve_spmv<<<nblk_mv, SOLVE_THREADS, 0, q>>>(n, rp, cl, wd, adiag, dirichlet, x, out, a1, part, gate);
+    // the product's launch shape: tuned once per problem class on this context (not while the
+    // caller's stream is being captured, nor below 4096 nodes), kept in the context's table
+    int G = 4, UNR = 4;
+    {
+        const int64_t deg = n > 0 ? (nnz + n / 2) / n : 0;
+        int64_t lg = 0;
+        while (lg < 62 && ((int64_t)1 << (lg + 1)) <= n) lg++;
+        const uint64_t key = ((uint64_t)(deg > 0xffff ? 0xffff : deg) << 40) | ((uint64_t)lg << 32) | (4ull << 24);
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) {
+            G = (int)(it->second >> 8);
+            UNR = (int)(it->second & 0xff);
+        } else {
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            LABFM_CUDA_TRY(ctx, cudaStreamIsCapturing(s, &cap));
+            if (cap == cudaStreamCaptureStatusNone && n >= 4096) {
+                cudaEvent_t e0, e1;
+                LABFM_CUDA_TRY(ctx, cudaEventCreate(&e0));
+                LABFM_CUDA_TRY(ctx, cudaEventCreate(&e1));
+                float best = 1e30f;
+                const int gs[3] = {4, 8, 16}, us[3] = {2, 4, 8};
+                cudaError_t te = cudaSuccess;
+                for (int gi = 0; gi < 3 && te == cudaSuccess; gi++)
+                    for (int ui = 0; ui < 3 && te == cudaSuccess; ui++) {
+                        for (int rep = 0; rep < 2 && te == cudaSuccess; rep++) {  // warm-up, then timed
+                            if (rep) cudaEventRecord(e0, s);
+                            te = launch_spmv(gs[gi], us[ui], n, rp, cl, wd, adiag, dirichlet, f, t, nullptr, part, -1,
+                                             0, nullptr, nullptr, s);
+                            if (rep) cudaEventRecord(e1, s);
+                        }
+                        float ms = 0.0f;
+                        if (te == cudaSuccess) te = cudaEventSynchronize(e1);
+                        if (te == cudaSuccess) te = cudaEventElapsedTime(&ms, e0, e1);
+                        if (te == cudaSuccess && ms < best) {
+                            best = ms;
+                            G = gs[gi];
+                            UNR = us[ui];
+                        }
+                    }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (te != cudaSuccess) return cuda_fail(ctx, te, "solver launch-shape tuning");
+                ctx->tuned[key] = ((uint32_t)G << 8) | (uint32_t)UNR;
+            }
+        }
+    }
+    // step: the scalars the last block forms (-1: none, and no gating on the state)
+    auto spmv = [&](cudaStream_t q, const double *x, double *out, const double *a1, int step) {
+        launch_spmv(G, UNR, n, rp, cl, wd, adiag, dirichlet, x, out, a1, part, step, step == 4 ? nblk_vec : 0,
+                    step == 4 ? part2 : nullptr, step >= 0 ? st : nullptr, q);
     };
     auto vec = [&](cudaStream_t q, int phase) {
         k_solve_vec<<<nblk_vec, SOLVE_THREADS, 0, q>>>(n, phase, f, phi, r, rhat, p, v, y, sv, z, t, dinv,
                                                        phase == 2 ? part2 : part, st);
     };
-    auto scalars = [&](cudaStream_t q, int nblk, int step) {
-        k_solve_scalars<<<1, SCALAR_THREADS, 0, q>>>(nblk, step, part, step == 4 ? nblk_vec : 0,
-                                                    step == 4 ? part2 : nullptr, st);
-    };
     // r = b - A x, r^ = r
-    spmv(s, phi, r, nullptr, nullptr);
-    vec(s, 0);
-    scalars(s, nblk_vec, 0);
+    spmv(s, phi, r, nullptr, -1);
+    vec(s, 0);                                // + the starting scalars
     LABFM_CUDA_TRY(ctx, cudaGetLastError());
     // one chunk of iterations, recorded once per call into a CUDA graph and replayed
     constexpr int CHUNK = 16;
     auto enqueue_chunk = [&](cudaStream_t q) {
         for (int it = 0; it < CHUNK; it++) {
             vec(q, 1);                        // p, y
-            spmv(q, y, v, rhat, st);          // v = A y, (rhat, v)
-            scalars(q, nblk_mv, 2);           // alpha
+            spmv(q, y, v, rhat, 2);           // v = A y, (rhat, v) -> alpha
             vec(q, 2);                        // s, z, (s, s)
-            spmv(q, z, t, sv, st);            // t = A z, (s, t), (t, t)
-            scalars(q, nblk_mv, 4);           // omega
-            vec(q, 3);                        // x, r, (rhat, r), (r, r)
-            scalars(q, nblk_vec, 5);          // rho, beta, convergence
+            spmv(q, z, t, sv, 4);             // t = A z, (s, t), (t, t) -> omega
+            vec(q, 3);                        // x, r, (rhat, r), (r, r) -> rho, beta, convergence
         }
     };
     if (!ctx->capture_stream)
@@ -359,9 +437,9 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
     cudaGraphExecDestroy(exec);
     if (le != cudaSuccess) return cuda_fail(ctx, le, "BiCGStab iterations");
     // the true residual ||b - A x|| / ||b||: t = A x, then phase 0 on scratch copies
-    spmv(s, phi, t, nullptr, nullptr);
+    spmv(s, phi, t, nullptr, -1);
     k_solve_vec<<<nblk_vec, SOLVE_THREADS, 0, s>>>(n, 0, f, nullptr, t, sv, z, y, nullptr, nullptr, nullptr, nullptr,
-                                                   nullptr, part, st);
+                                                   nullptr, part, nullptr);
     LABFM_CUDA_TRY(ctx, cudaGetLastError());
     std::vector<double> hp(3 * (size_t)nblk_vec);
     LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s));
