@@ -40,9 +40,10 @@ template <int K> struct MCfg {
     static_assert(RG * CG <= MIX_THREADS, "assembly tile grid exceeds the CTA");
     // kernel A: Xf, Wf (df) + neighbour records
     static constexpr size_t smemA = 8 * ((size_t)2 * NB * LDX + (size_t)NB * NREC);
-    // kernel C: Xd (double), Wf (df), M^-1 (df), records, Psi/rhs (df) and residual (double)
+    // kernel C: Xd (double), Wf (df), records, Psi/rhs (df) and residual (double); M^-1 is read
+    // from global memory (through L1), which keeps three CTAs per SM
     static constexpr size_t smemC =
-        8 * ((size_t)2 * NB * LDX + (size_t)P * P + (size_t)NB * NREC + (size_t)2 * P * MAX_OPS + (size_t)NB * MAX_OPS);
+        8 * ((size_t)2 * NB * LDX + (size_t)NB * NREC + (size_t)2 * P * MAX_OPS + (size_t)NB * MAX_OPS);
 };
 
 struct DfTables {
@@ -894,15 +895,14 @@ __global__ void __launch_bounds__(InvCfg<p_of_k(K)>::NT) k_mixed_invert(MixedArg
 // C: Psi~ = M^-1 C~, w~ = W . Psi~, FP64 residual refinement, physical weights
 // ------------------------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(MIX_THREADS, 2) k_mixed_weights(MixedArgs A)
+__global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
 {
     using C = MCfg<K>;
     constexpr int P = C::P, LDX = C::LDX, NB = C::NB;
     extern __shared__ __align__(16) double smem_d[];
     double *Xd = smem_d;                                     // [NB][LDX]
     df *Wf = reinterpret_cast<df *>(Xd + NB * LDX);          // [NB][LDX]
-    df *Mi = Wf + NB * LDX;                                  // [P][P] M^-1
-    df *Nrec = Mi + P * P;                                   // [NB][NREC]
+    df *Nrec = Wf + NB * LDX;                                // [NB][NREC]
     df *Rhs = Nrec + NB * NREC;                              // [P][MAX_OPS] right-hand sides
     df *Psi = Rhs + P * MAX_OPS;                             // [P][MAX_OPS]
     double *Wt = reinterpret_cast<double *>(Psi + P * MAX_OPS);  // [NB][MAX_OPS] w~ of the chunk
@@ -947,8 +947,7 @@ __global__ void __launch_bounds__(MIX_THREADS, 2) k_mixed_weights(MixedArgs A)
             }
             s_flag = 0;
         }
-        const df *Mg = A.Mg + li * (int64_t)P * P;
-        for (int t = tid; t < P * P; t += MIX_THREADS) Mi[t] = Mg[t];
+        const df *__restrict__ Mi = A.Mg + li * (int64_t)P * P;  // M^-1 of the node (global)
         __syncthreads();
         // scaled targets C~_alpha = C_alpha h^(l_d - |alpha|)
         for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
