@@ -29,6 +29,7 @@ __all__ = [
     "dirichlet_square",
     "HeatSteadyField",
     "ColeBurgersSolution",
+    "ColeHopf2DSolution",
     "FourierField",
     "fourier_field",
     "sincos_field",
@@ -385,6 +386,25 @@ class ColeBurgersSolution:
         num = (4.0 * math.pi / self.Re) * (np.sin(th) @ (self.n * self.An * E))
         den = self.A0 + np.cos(th) @ (self.An * E)
         return num / den
+
+
+class ColeHopf2DSolution:
+    """A two-dimensional exact solution of Burgers' equation u_t + (u . grad) u = nabla^2 u / Re
+    on the periodic unit square, by the Cole-Hopf transform u = -(2/Re) grad ln(phi) of a heat-
+    equation solution phi_t = nabla^2 phi / Re: phi = 1 + a sin(2 pi x) sin(2 pi y) E,
+    E = exp(-8 pi^2 t / Re), 0 < a < 1 (so phi > 0).  Both components and all advection terms are
+    non-zero, unlike the one-dimensional problem of Sec. 5.3."""
+
+    def __init__(self, Re: float = 10.0, a: float = 0.5):
+        self.Re, self.a = float(Re), float(a)
+
+    def uv(self, xy, t):
+        tp = 2.0 * math.pi
+        x, y = xy[:, 0], xy[:, 1]
+        E = self.a * math.exp(-2.0 * tp * tp * t / self.Re)
+        phi = 1.0 + E * np.sin(tp * x) * np.sin(tp * y)
+        c = -2.0 / self.Re * tp * E / phi
+        return c * np.cos(tp * x) * np.sin(tp * y), c * np.sin(tp * x) * np.cos(tp * y)
 
 
 class P6Field(_Field):

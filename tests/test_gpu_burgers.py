@@ -117,3 +117,60 @@ def test_burgers_argument_checks():
     with pytest.raises(LabfmError):
         L.step_burgers([0.0, 0.0, 0.01], u, u, 1e-3, 1)  # u and v the same buffer
     L.step_burgers([0.0, 0.0, 0.01], u, v, 1e-3, 0)  # nothing to do
+
+
+def test_burgers_2d_cole_hopf_on_gpu():
+    """Both velocity components active (the two-dimensional Cole-Hopf solution, Re = 10, k = 4,
+    t = 0.1): the GPU equals the oracle's RK4 on the oracle's weights to 1e-10 at h/H = 2/41 and
+    2/81, and the error against the exact solution falls at rate 3.5 - 4.5 (oracle: 3.97)."""
+    import torch
+
+    k, Re, T = 4, 10.0, 0.1
+    sol = S.ColeHopf2DSolution(Re=Re)
+    errs = []
+    for nside in (41, 81):
+        ns, L, rp, col, _ = _setup(nside, k, ("dx", "dy", "lap"), seed=8)
+        h = ns.h[0]
+        nsteps = int(math.ceil(T / min(0.2 * h, 0.05 * h * h * Re)))
+        dt = T / nsteps
+        u0, v0 = sol.uv(ns.xy, 0.0)
+        dev = torch.device("cuda", 0)
+        u, v = torch.from_numpy(u0).to(dev), torch.from_numpy(v0).to(dev)
+        L.step_burgers([0.0, 0.0, 1.0 / Re], u, v, dt, nsteps)
+        gu, gv = u.cpu().numpy(), v.cpu().numpy()
+        orp, ocol = oracle.neighbours(ns.xy, ns.h, True)
+        ow = oracle.build_weights(ns.xy, ns.h, True, orp, ocol, G.c_matrix(k, ("dx", "dy", "lap")), k=k,
+                                  rbf="quadratic", abf_form="dw0")["w"]
+        ru, rv = oracle.rk4_burgers(orp, ocol, ow, [0.0, 0.0, 1.0 / Re], u0, v0, dt, nsteps)
+        scale = max(np.abs(ru).max(), np.abs(rv).max())
+        assert np.abs(gu - ru).max() < 1e-10 * scale and np.abs(gv - rv).max() < 1e-10 * scale
+        eu, ev = sol.uv(ns.xy, T)
+        errs.append(math.sqrt(np.sum((gu - eu) ** 2 + (gv - ev) ** 2) / np.sum(eu ** 2 + ev ** 2)))
+        L.close()
+    rate = math.log(errs[0] / errs[1]) / math.log(81 / 41)
+    assert 3.5 <= rate <= 4.5, (errs, rate)
+
+
+@pytest.mark.parametrize("field,weights", [("f32", "f64"), ("f64", "f32")])
+def test_burgers_mixed_field_and_weight_types(field, weights):
+    """Field and weight types that differ: the sums run in double (FP32 fields are rounded on
+    input and output): 20 steps of the two-dimensional problem against the oracle on the same
+    weights and inputs, within FP32 rounding of the fields."""
+    import torch
+
+    k, Re = 4, 10.0
+    ns, L, rp, col, w = _setup(32, k, ("dx", "dy", "lap"), weight_dtype=weights, seed=8)
+    sol = S.ColeHopf2DSolution(Re=Re)
+    u0, v0 = sol.uv(ns.xy, 0.0)
+    h = ns.h[0]
+    dt = min(0.2 * h, 0.05 * h * h * Re)
+    dev = torch.device("cuda", 0)
+    tdt = torch.float32 if field == "f32" else torch.float64
+    u, v = torch.from_numpy(u0).to(dev, tdt), torch.from_numpy(v0).to(dev, tdt)
+    L.step_burgers([0.0, 0.0, 1.0 / Re], u, v, dt, 20)
+    gu, gv = u.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64)
+    cast = (lambda a: a.astype(np.float32).astype(np.float64)) if field == "f32" else (lambda a: a)
+    ru, rv = oracle.rk4_burgers(rp, col, w, [0.0, 0.0, 1.0 / Re], cast(u0), cast(v0), dt, 20)
+    scale = max(np.abs(ru).max(), np.abs(rv).max())
+    tol = 1e-5 if field == "f32" else 1e-12
+    assert np.abs(gu - ru).max() < tol * scale and np.abs(gv - rv).max() < tol * scale

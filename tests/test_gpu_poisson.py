@@ -115,3 +115,29 @@ def test_solve_reports_non_convergence_and_bad_arguments():
         L.solve(1, fd, phi)  # only one operator was built
     with pytest.raises(LabfmError):
         L.solve(0, fd, fd)  # f and phi the same buffer
+
+
+def test_solve_selects_the_operator():
+    """Weights for (d/dx, d/dy, nabla^2): solving with op = 2 uses the Laplacian's column of the
+    interleaved weights (k = 4, 40^2 nodes, node 0 fixed) and equals the oracle's solve."""
+    import torch
+
+    k = 4
+    ns = S.jittered_lattice(40, 2.0, k, jitter=0.5 / math.sqrt(2), seed=3)
+    ops = ("dx", "dy", "lap")
+    L, rp, col, w, status, _ = G.gpu_run(ns, k, ops, rbf="quadratic", abf_form="dw0")
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    ex = np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    f = -8 * np.pi ** 2 * ex
+    dm = np.zeros(ns.n, np.uint8)
+    dm[0] = 1
+    f[0] = ex[0]
+    dev = torch.device("cuda", 0)
+    phi = torch.zeros(ns.n, dtype=torch.float64, device=dev)
+    L.solve(2, torch.from_numpy(f).to(dev), phi, torch.from_numpy(dm).to(dev), tol=1e-13)
+    orp, ocol = oracle.neighbours(ns.xy, ns.h, True)
+    ow = oracle.build_weights(ns.xy, ns.h, True, orp, ocol, G.c_matrix(k, ops), k=k, rbf="quadratic",
+                              abf_form="dw0")["w"]
+    ref = oracle.solve_operator(orp, ocol, ow, 2, f, dm)
+    got = phi.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()

@@ -26,6 +26,15 @@ MUTATIONS = {
     "stencil radius h instead of 2h": ("double R = 2.0 * h[i];", "double R = h[i];"),
     "dw0 form keeps the d2W0/dr2 terms": ("if (rbf_form & ORC_ABF_DW0_ONLY) f2 = f3 = 0;",
                                           "if (rbf_form & ORC_ABF_DW0_ONLY) f3 = 0;"),
+    "Burgers advection with the wrong sign": (
+        "real fu = -(u[i] * op_sum(row_ptr, col, w, n_ops, 0, u, i) + v[i] * op_sum(row_ptr, col, w, n_ops, 1, u, i));",
+        "real fu = (u[i] * op_sum(row_ptr, col, w, n_ops, 0, u, i) + v[i] * op_sum(row_ptr, col, w, n_ops, 1, u, i));"),
+    "Burgers advection of u by u only (v term dropped)": (
+        "real fu = -(u[i] * op_sum(row_ptr, col, w, n_ops, 0, u, i) + v[i] * op_sum(row_ptr, col, w, n_ops, 1, u, i));",
+        "real fu = -(u[i] * op_sum(row_ptr, col, w, n_ops, 0, u, i));"),
+    "Burgers viscous term on the wrong operator": (
+        "fu += (real)beta[d] * op_sum(row_ptr, col, w, n_ops, d, u, i);",
+        "fu += (real)beta[d] * op_sum(row_ptr, col, w, n_ops, d - 1, u, i);"),
 }
 
 PINS = [
@@ -42,6 +51,8 @@ PINS = [
     P.test_abfs_truncated_high_orders_vs_sympy,
     lambda: P.test_abfs_dw0_form_is_the_printed_dW0_bracket("quadratic"),
     lambda: P.test_laplacian_noise_limits_dw0_form(4, 2.0, 1.0),
+    P.test_burgers_quick_convergence,
+    P.test_burgers_2d_convergence,
 ]
 
 

@@ -708,6 +708,59 @@ def _burgers_error(k, nside, T, Re=100.0, eps=0.2, seed=7):
     return np.linalg.norm(u - ex) / np.linalg.norm(ex), np.abs(v).max()
 
 
+def test_burgers_quick_convergence():
+    """The periodic Burgers' problem at k = 4 between h/H = 2/41 and 2/81 (t = 0.4): rate 4.06,
+    band [3.5, 4.6], and v stays exactly 0 (a cheap form of the pin below)."""
+    e1, v1 = _burgers_error(4, 41, 0.4)
+    e2, v2 = _burgers_error(4, 81, 0.4)
+    rate = math.log(e1 / e2) / math.log(81 / 41)
+    assert 3.5 <= rate <= 4.6, (e1, e2, rate)
+    assert v1 == 0.0 and v2 == 0.0
+
+
+def test_cole_hopf_2d_solves_burgers():
+    """The two-dimensional Cole-Hopf solution satisfies both components of
+    u_t + (u . grad) u = nabla^2 u / Re (central differences, relative to the size of the terms)."""
+    sol = S.ColeHopf2DSolution(Re=10.0, a=0.5)
+    pts = np.array([[0.1, 0.2], [0.37, 0.61], [0.5, 0.5], [0.83, 0.12], [0.66, 0.9]])
+    d, t = 1e-4, 0.1
+    ex, ey = np.array([[d, 0.0]]), np.array([[0.0, d]])
+    U = lambda p, tt: np.stack(sol.uv(p, tt))  # [2, npts]
+    ut = (U(pts, t + d) - U(pts, t - d)) / (2 * d)
+    ux = (U(pts + ex, t) - U(pts - ex, t)) / (2 * d)
+    uy = (U(pts + ey, t) - U(pts - ey, t)) / (2 * d)
+    lap = (U(pts + ex, t) + U(pts - ex, t) + U(pts + ey, t) + U(pts - ey, t) - 4 * U(pts, t)) / d ** 2
+    u, v = sol.uv(pts, t)
+    res = ut + u * ux + v * uy - lap / 10.0
+    scale = np.abs(ut) + np.abs(u * ux) + np.abs(v * uy) + np.abs(lap / 10.0)
+    assert np.all(np.abs(res) <= 1e-5 * scale + 1e-9), res
+    assert np.abs(u).max() > 0.1 and np.abs(v).max() > 0.1
+
+
+def _burgers_2d_error(k, nside, T, Re=10.0, eps=0.2, seed=8):
+    ns = S.jittered_lattice(nside, 2.0, k, jitter=eps / math.sqrt(2), seed=seed)
+    rp, col = oracle.neighbours(ns.xy, ns.h, True)
+    C = np.stack([S.op_c_vector(o, k) for o in ("dx", "dy", "lap")])
+    w = oracle.build_weights(ns.xy, ns.h, True, rp, col, C, k=k, rbf="quadratic", abf_form="dw0")["w"]
+    sol = S.ColeHopf2DSolution(Re=Re)
+    u0, v0 = sol.uv(ns.xy, 0.0)
+    h = ns.h[0]
+    nsteps = int(math.ceil(T / min(0.2 * h / 1.0, 0.05 * h * h * Re)))
+    u, v = oracle.rk4_burgers(rp, col, w, [0.0, 0.0, 1.0 / Re], u0, v0, T / nsteps, nsteps)
+    eu, ev = sol.uv(ns.xy, T)
+    return math.sqrt(np.sum((u - eu) ** 2 + (v - ev) ** 2) / np.sum(eu ** 2 + ev ** 2))
+
+
+def test_burgers_2d_convergence():
+    """Burgers' equation with both velocity components active (the Cole-Hopf solution above,
+    Re = 10, k = 4): RK4 of the oracle's discrete system converges at order ~k between h/H = 2/21
+    and 2/41 (t = 0.1), band [3.3, 5] (measured 3.8; 2.0 and 5.6 at k = 2 and 6, and 4.0, 2.0, 6.1
+    between 2/41 and 2/81)."""
+    e1, e2 = _burgers_2d_error(4, 21, 0.1), _burgers_2d_error(4, 41, 0.1)
+    rate = math.log(e1 / e2) / math.log(41 / 21)
+    assert 3.3 <= rate <= 5.0, (e1, e2, rate)
+
+
 def test_burgers_periodic_convergence():
     """Sec. 5.3, periodic Burgers' problem at Re = 100 (quadratic ABFs in the dW0/dr form,
     h/dr = 2, eps/dr = 0.2, RK4 with the time step of Eq. (tstep)): at t = 0.4, as the front
