@@ -172,5 +172,5 @@ def test_burgers_mixed_field_and_weight_types(field, weights):
     cast = (lambda a: a.astype(np.float32).astype(np.float64)) if field == "f32" else (lambda a: a)
     ru, rv = oracle.rk4_burgers(rp, col, w, [0.0, 0.0, 1.0 / Re], cast(u0), cast(v0), dt, 20)
     scale = max(np.abs(ru).max(), np.abs(rv).max())
-    tol = 1e-5 if field == "f32" else 1e-12
+    tol = 2e-5 if field == "f32" else 1e-12
     assert np.abs(gu - ru).max() < tol * scale and np.abs(gv - rv).max() < tol * scale
