@@ -153,9 +153,10 @@ def test_burgers_2d_cole_hopf_on_gpu():
 
 @pytest.mark.parametrize("field,weights", [("f32", "f64"), ("f64", "f32")])
 def test_burgers_mixed_field_and_weight_types(field, weights):
-    """Field and weight types that differ: the sums run in double (FP32 fields are rounded on
-    input and output): 20 steps of the two-dimensional problem against the oracle on the same
-    weights and inputs, within FP32 rounding of the fields."""
+    """Field and weight types that differ: the sums run in double.  20 steps of the two-
+    dimensional problem against the oracle on the same weights and inputs: FP32 fields are rounded
+    at every stage (2e-5); with FP32 weights the combined linear weight sum_d beta_d w^d is summed
+    in double and kept as a float, one more rounding of ~6e-8 of it (1e-6)."""
     import torch
 
     k, Re = 4, 10.0
@@ -172,5 +173,5 @@ def test_burgers_mixed_field_and_weight_types(field, weights):
     cast = (lambda a: a.astype(np.float32).astype(np.float64)) if field == "f32" else (lambda a: a)
     ru, rv = oracle.rk4_burgers(rp, col, w, [0.0, 0.0, 1.0 / Re], cast(u0), cast(v0), dt, 20)
     scale = max(np.abs(ru).max(), np.abs(rv).max())
-    tol = 2e-5 if field == "f32" else 1e-12
+    tol = 2e-5 if field == "f32" else 1e-6
     assert np.abs(gu - ru).max() < tol * scale and np.abs(gv - rv).max() < tol * scale
