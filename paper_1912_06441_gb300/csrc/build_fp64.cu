@@ -9,6 +9,7 @@
 // C_alpha h^-|alpha|) is then eliminated in shared memory, one column per step, in the space of
 // the X staging (X is not read again), which keeps a CTA within a quarter of the SM's shared
 // memory: four CTAs per SM.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -50,21 +51,39 @@ struct BuildArgs {
     double C[MAX_OPS * PMAX];  // target vectors, row d = C^d (physical units)
 };
 
+// Shared memory of one CTA beyond the X/W staging: the scalars and small arrays of the node being
+// built, carved from the dynamic allocation (so that a kernel holding several orders allocates
+// them once, not once per order).
+struct NodeShared {
+    double psi[PMAX * MAX_OPS];  // Psi^d, kept while X and W are staged again
+    double invpiv[PMAX];         // 1 / pivot of each column, reused by the back substitution
+    double hpow[KMAX + 1];       // h^-n
+    double inv;
+    int piv;
+    int flag;  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
+};
+
+template <int K> constexpr size_t node_smem_bytes() { return Cfg<K>::smem_bytes + sizeof(NodeShared); }
+constexpr size_t max_node_smem_bytes()
+{
+    return std::max({node_smem_bytes<1>(), node_smem_bytes<2>(), node_smem_bytes<3>(), node_smem_bytes<4>(),
+                     node_smem_bytes<5>(), node_smem_bytes<6>(), node_smem_bytes<7>(), node_smem_bytes<8>()});
+}
+
+// The whole build of node i at order K by the CTA: stage X and W, assemble M, eliminate
+// [M | Chat], weights.  Ends synchronised (the shared memory is reused by the next node).
 template <int K>
-__global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64(BuildArgs A)
+__device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double *smem)
 {
     using C = Cfg<K>;
     constexpr int P = C::P, LDX = C::LDX, NB = C::NB, LDA = C::LDA, TM = C::TM, TN = C::TN;
-    extern __shared__ __align__(16) double smem[];
     double *Xs = smem;                 // [NB][LDX]
     double *Ws = Xs + NB * LDX;        // [NB][LDX]
     double *Am = Xs;                   // [P][LDA]  augmented [M | Chat], over the X staging
-    __shared__ double s_psi[PMAX * MAX_OPS];  // Psi^d, kept while X and W are staged again
-    __shared__ int s_piv;
-    __shared__ double s_inv;
-    __shared__ double s_invpiv[P];  // 1 / pivot of each column, reused by the back substitution
-    __shared__ double s_hpow[KMAX + 1];  // h^-n
-    __shared__ int s_flag;  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
+    NodeShared &sh = *reinterpret_cast<NodeShared *>(Ws + NB * LDX);
+    double *s_psi = sh.psi, *s_invpiv = sh.invpiv, *s_hpow = sh.hpow;
+    int &s_piv = sh.piv, &s_flag = sh.flag;
+    double &s_inv = sh.inv;
 
     const int tid = threadIdx.x;
     const int n_ops = A.n_ops;
@@ -72,8 +91,7 @@ __global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64(BuildArgs A)
     const int rg = tid / C::CG, cg = tid % C::CG;
     const bool tile_active = tid < C::RG * C::CG;
 
-    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
-        const int64_t i = A.list ? (int64_t)A.list[li] : li;
+    {
         const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
         const int ni = (int)(re - rs);
         if (ni < P) {
@@ -85,7 +103,7 @@ __global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64(BuildArgs A)
                 if (A.node_status) A.node_status[i] = LABFM_NODE_UNDERSAMPLED;
                 atomicAdd(A.n_bad, 1ull);
             }
-            continue;
+            return;
         }
         const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], hi = A.h[i];
         const double ihi = 1.0 / hi;
@@ -294,20 +312,65 @@ __global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64(BuildArgs A)
     }
 }
 
+// One order for all listed nodes (persistent over the list).
+template <int K>
+__global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64(BuildArgs A)
+{
+    extern __shared__ __align__(16) double smem[];
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x)
+        build_node<K>(A, A.list ? (int64_t)A.list[li] : li, smem);
+}
+
+// Every order in one persistent launch (per-node order, Sec. 4.1 walls and variable resolution):
+// the list holds the nodes by ascending order, and CTAs take them from the end, so that the
+// costliest nodes go first and the cheap ones fill the tail.
+__global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64_orders(BuildArgs A, const int8_t *__restrict__ order)
+{
+    extern __shared__ __align__(16) double smem[];
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
+        const int64_t i = A.list[A.n_list - 1 - li];
+        switch (order[i]) {
+        case 1: build_node<1>(A, i, smem); break;
+        case 2: build_node<2>(A, i, smem); break;
+        case 3: build_node<3>(A, i, smem); break;
+        case 4: build_node<4>(A, i, smem); break;
+        case 5: build_node<5>(A, i, smem); break;
+        case 6: build_node<6>(A, i, smem); break;
+        case 7: build_node<7>(A, i, smem); break;
+        default: build_node<8>(A, i, smem); break;
+        }
+    }
+}
+
 template <int K>
 static cudaError_t launch_k(const BuildArgs &a, int num_sms, cudaStream_t s)
 {
     using C = Cfg<K>;
-    cudaError_t e = cudaFuncSetAttribute(k_build_fp64<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::smem_bytes);
+    constexpr size_t smem = node_smem_bytes<K>();
+    cudaError_t e = cudaFuncSetAttribute(k_build_fp64<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_fp64<K>, BUILD_THREADS, C::smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_fp64<K>, BUILD_THREADS, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = std::min<int64_t>(a.n_list, (int64_t)num_sms * per_sm);
     if (grid < 1) return cudaSuccess;
-    k_build_fp64<K><<<(unsigned)grid, BUILD_THREADS, C::smem_bytes, s>>>(a);
+    k_build_fp64<K><<<(unsigned)grid, BUILD_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_all_orders(const BuildArgs &a, const int8_t *order, int num_sms, cudaStream_t s)
+{
+    constexpr size_t smem = max_node_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_build_fp64_orders, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_fp64_orders, BUILD_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = std::min<int64_t>(a.n_list, (int64_t)num_sms * per_sm);
+    if (grid < 1) return cudaSuccess;
+    k_build_fp64_orders<<<(unsigned)grid, BUILD_THREADS, smem, s>>>(a, order);
     return cudaGetLastError();
 }
 
@@ -473,9 +536,16 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(dmisc + 11, hs, sizeof(base), cudaMemcpyHostToDevice, s));
         k_order_scatter<<<nb, 256, 0, s>>>(n, order, dmisc + 11, dmisc + 20, list);
         LABFM_CUDA_TRY(ctx, cudaGetLastError());
-        for (int k = KMAX; k >= 1; k--) {
-            if (!cnt[k]) continue;
-            LABFM_CUDA_TRY(ctx, launch(k, list + base[k], (int64_t)cnt[k]));
+        if (!mixed) {
+            // every order in one persistent launch over the whole (ascending-order) list
+            a.list = list;
+            a.n_list = (int64_t)acc;
+            LABFM_CUDA_TRY(ctx, launch_all_orders(a, order, ctx->num_sms, s));
+        } else {
+            for (int k = KMAX; k >= 1; k--) {
+                if (!cnt[k]) continue;
+                LABFM_CUDA_TRY(ctx, launch(k, list + base[k], (int64_t)cnt[k]));
+            }
         }
     }
     LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, 32 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
