@@ -141,3 +141,18 @@ def test_solve_selects_the_operator():
     ref = oracle.solve_operator(orp, ocol, ow, 2, f, dm)
     got = phi.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_solve_all_dirichlet_rows_is_exact_and_immediate():
+    """Degenerate system: every row a Dirichlet row (the identity).  The initial guess takes f
+    at those nodes, the residual is exactly zero and the solve returns after no iteration with
+    phi == f bit for bit."""
+    import torch
+
+    ns, L, ex, f, dm = _periodic_problem(4, 24)
+    dev = torch.device("cuda", 0)
+    phi = torch.full((ns.n,), 7.0, dtype=torch.float64, device=dev)
+    allrows = torch.ones(ns.n, dtype=torch.uint8, device=dev)
+    iters, resid = L.solve(0, torch.from_numpy(f).to(dev), phi, allrows, tol=1e-12)
+    assert iters == 0 and resid == 0.0
+    assert np.array_equal(phi.cpu().numpy(), f)
