@@ -179,25 +179,42 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_rk4_stage(int64_t n, const in
     }
     AT acc = 0;
     df accd{0.0f, 0.0f};
+    // FP32 weights: the stencil stream is software-pipelined (the next batch of UNR entries per
+    // lane is loaded before the gathers of the current one, so its latency overlaps them: +8 % at
+    // 2048^2); with double-float weights the second batch's registers cost more than the overlap
+    // gains (-11 %), so those load each batch just before its gathers
+    constexpr bool PIPE = CW == CW_F32;
+    int cn[UNR];
+    WT wn[UNR];
+    auto load_batch = [&](int64_t base) {
+#pragma unroll
+        for (int q = 0; q < UNR; q++) {
+            const int64_t e = base + (int64_t)q * G + lane;
+            if (e < re) {
+                if constexpr (CW == CW_F64) {
+                    cn[q] = __ldcs(col + e);
+                    wn[q] = __ldcs(wcd + e);
+                } else {
+                    const int2 pr = __ldcs(wcp + e);  // stencil index and (high part of the) weight
+                    cn[q] = pr.x;
+                    wn[q] = make_float2(__int_as_float(pr.y), CW == CW_DF ? __ldcs(wc_lo + e) : 0.0f);
+                }
+            } else {
+                cn[q] = -1;
+            }
+        }
+    };
+    if (PIPE && rs < re) load_batch(rs);
     for (int64_t base = rs; base < re; base += (int64_t)G * UNR) {
+        if (!PIPE) load_batch(base);
         int cj[UNR];
         WT wv[UNR];
 #pragma unroll
         for (int q = 0; q < UNR; q++) {
-            int64_t e = base + (int64_t)q * G + lane;
-            if (e < re) {
-                if constexpr (CW == CW_F64) {
-                    cj[q] = __ldcs(col + e);
-                    wv[q] = __ldcs(wcd + e);
-                } else {
-                    const int2 pr = __ldcs(wcp + e);  // stencil index and (high part of the) weight
-                    cj[q] = pr.x;
-                    wv[q] = make_float2(__int_as_float(pr.y), CW == CW_DF ? __ldcs(wc_lo + e) : 0.0f);
-                }
-            } else {
-                cj[q] = -1;
-            }
+            cj[q] = cn[q];
+            wv[q] = wn[q];
         }
+        if (PIPE && base + (int64_t)G * UNR < re) load_batch(base + (int64_t)G * UNR);
 #pragma unroll
         for (int q = 0; q < UNR; q++) {
             if (cj[q] >= 0) {
