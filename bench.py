@@ -713,7 +713,7 @@ def run_labfm(args, rank, world, local_rank):
                            "fp64_pipe": {"achieved_tflops": nnz * (1 + 2 * len(OPS)) / (apply_ms * 1e-3) / 1e12,
                                          "peak_tflops": fp64_peak,
                                          "frac": nnz * (1 + 2 * len(OPS)) / (apply_ms * 1e-3) / 1e12 / fp64_peak},
-                           "f32_variant": "extra.apply_f32 (HBM-bound: k_apply<4,float,float>)"},
+                           "f32_variant": None},
         "build_mnodes_per_s": n / (build_ms * 1e-3) / 1e6,
         "e2e": {"value": replicas_throughput(world, n, e2e_ms), "unit": "Mnodes/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -723,6 +723,12 @@ def run_labfm(args, rank, world, local_rank):
         "clocks": clk,
     }
     line["extra"] = extra_measurements(torch, P, dev, local_rank, ns, field, hbm)
+    a32 = line["extra"].get("apply_f32")
+    if a32:  # the HBM-bound variant of the apply, beside the FP64-pipe-bound one above
+        line["apply_roofline"]["f32_variant"] = {
+            "kernel": a32["kernel"], "achieved": a32["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+            "frac": a32["frac_of_hbm"], "algorithmic_bytes": a32["algorithmic_bytes"], "timing": a32["timing"],
+            "at_4M_nodes_frac": line["extra"].get("rk4_2048", {}).get("apply_f32", {}).get("frac_of_hbm")}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ns, field, C, sample=args.cpu_sample)
     print(json.dumps(line), flush=True)
