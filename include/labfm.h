@@ -161,6 +161,8 @@ labfm_status labfm_get_neighbours(labfm_ctx *ctx, const int64_t **row_ptr, const
  *                layout [nnz][n_ops] (entry e of the CSR, operator d at e*n_ops + d)
  *   node_status  device int32[n] receiving LABFM_NODE_* per node, or NULL
  *   n_bad_out    host, receives the number of flagged nodes (may be NULL)
+ * With per-node orders the nodes are bucketed by order; the FP64 build then runs every order in
+ * one persistent launch (highest order first), the mixed builds one launch per order.
  * Flagged nodes get zero weights.  Returns LABFM_ERR_SINGULAR if any node was
  * flagged (the weights of all other nodes are valid), LABFM_ERR_STATE if no
  * stencils were built, LABFM_ERR_TIMEOUT if a bounded wait for the tensor cores
