@@ -153,8 +153,8 @@ def test_weights_variable_order_and_walls():
 
 def test_weights_random_orders_one_launch():
     """Every order 1..8 mixed at random over a periodic set (h = 2.2 s, enough neighbours for
-    order 8): the one-launch build over all orders equals the oracle node by node, including the
-    undersampled status where a low-order node's stencil is fine and a high-order one is not."""
+    order 8): the one-launch build over all orders equals the oracle node by node (statuses and
+    weights)."""
     ns = S.jittered_lattice(36, 2.2, 8, seed=61)
     order = (1 + np.floor(S.uniform01(62, ns.n) * 8)).astype(np.int8)
     ops = ("dx", "dy")
