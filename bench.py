@@ -19,6 +19,7 @@ import math
 import os
 import shutil
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -90,7 +91,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples (the JSON line carries their summary); LABFM_CLOCKS_DIR keeps them
+        self.path = os.path.join(os.environ.get("LABFM_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 f"labfm_clocks_{os.getpid()}.csv")
 
     def start(self):
         if not shutil.which("nvidia-smi"):

@@ -40,7 +40,7 @@ typedef enum {
     LABFM_ERR_ARG = 1,      /* invalid argument, detected on the host */
     LABFM_ERR_CUDA = 2,     /* a CUDA runtime call failed */
     LABFM_ERR_NOMEM = 3,    /* device allocation failed */
-    LABFM_ERR_CAPACITY = 4, /* a size limit of this build was exceeded (message says which) */
+    LABFM_ERR_CAPACITY = 4, /* a size limit of the library was exceeded (message says which) */
     LABFM_ERR_SINGULAR = 5, /* weights built, but >= 1 node was flagged (see node_status) */
     LABFM_ERR_TIMEOUT = 6,  /* a bounded device wait gave up */
     LABFM_ERR_STATE = 7,    /* call out of order (e.g. apply before build_weights) */
@@ -98,7 +98,7 @@ enum {
     LABFM_NODE_NONFINITE = 3     /* a weight came out NaN or infinite */
 };
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define LABFM_MAX_ORDER 8 /* k <= 8, p <= 44 */
 #define LABFM_MAX_OPS 8   /* operators per build */
 #define LABFM_PMAX 44     /* p(8) = (8^2 + 3*8)/2, Sec. 3.1 */

@@ -638,5 +638,5 @@ int orc_rk4_burgers(int64_t n, const int64_t *row_ptr, const int32_t *col, const
     return 0;
 }
 
-/* precision of this build, in bits of significand */
+/* precision of the real type this file was compiled with, in bits of significand */
 int orc_real_mant_bits(void) { return sizeof(real) == sizeof(double) ? DBL_MANT_DIG : LDBL_MANT_DIG; }

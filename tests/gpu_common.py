@@ -12,7 +12,7 @@ OPS = {1: ("dx", "dy"), 2: ("dx", "dy", "lap"), 3: ("dx", "dy", "lap"), 4: ("dx"
        5: ("dx", "dy", "lap", "lap2"), 6: ("dx", "dy", "lap", "lap3"), 7: ("dx", "dy", "lap", "lap3"),
        8: ("dx", "dy", "lap", "lap4")}
 
-# Absolute floors of the weight/derivative tolerance (the benchmark spec's 1e-11 where FP64 allows it)
+# Absolute floors of the weight/derivative tolerance (1e-11 relative, where FP64 allows it)
 TOL_FLOOR_MAX = 1e-11
 TOL_FLOOR_MEDIAN = 1e-12
 # The GPU's rounding error is of the same kind as the FP64 oracle's (same algorithm, other
