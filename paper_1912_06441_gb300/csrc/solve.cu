@@ -40,18 +40,32 @@ struct SolveState {
     unsigned int ticket;  // blocks of the current launch that have written their partial sums
 };
 
-// sum over the block (fixed order: deterministic); the result is valid in thread 0
-__device__ __forceinline__ double block_sum(double v, double *sh)
+// Two sums over the block at once, of values held by the threads whose index is a multiple of
+// STRIDE (the others' are ignored), in a fixed order (deterministic); the results are valid in
+// warp 0.  The values go through shared memory and warp 0 alone adds them: on GB300 every FP64
+// add is scarce, and a shuffle tree in every warp would cost each warp five adds per sum, about
+// as many FP64 instructions as a product's stencil entries.  sh: 2 x SOLVE_THREADS / STRIDE.
+template <int STRIDE>
+__device__ __forceinline__ void block_sum2(double a, double b, double *sh, double &sa, double &sb)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NV = SOLVE_THREADS / STRIDE;
+    __syncthreads();  // sh is free (an earlier sum may still be reading it)
+    if (threadIdx.x % STRIDE == 0) {
+        sh[threadIdx.x / STRIDE] = a;
+        sh[NV + threadIdx.x / STRIDE] = b;
+    }
     __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < SOLVE_THREADS / 32; w++) s += sh[w];
-    return s;
+    sa = sb = 0.0;
+    if (threadIdx.x < 32) {
+        for (int k = threadIdx.x; k < NV; k += 32) {
+            sa += sh[k];
+            sb += sh[NV + k];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+    }
 }
 
 // The scalars of the step that follows a reduction (thread 0 of the reducing block):
@@ -122,7 +136,9 @@ __device__ void last_block_scalars(int nblk, int step, const double *part, int n
     }
     if (part2)
         for (int k = threadIdx.x; k < nblk2; k += SOLVE_THREADS) d += __ldcg(part2 + 3 * k);
-    const double s0 = block_sum(a, sh), s1 = block_sum(b, sh), s2 = block_sum(c, sh), s3 = block_sum(d, sh);
+    double s0, s1, s2, s3;
+    block_sum2<1>(a, b, sh, s0, s1);
+    block_sum2<1>(c, d, sh, s2, s3);
     if (threadIdx.x == 0) {
         form_scalars(step, s0, s1, s2, s3, st);
         st->ticket = 0u;  // the next reduction starts from zero (it is a later launch)
@@ -174,7 +190,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const i
                                                              SolveState *__restrict__ st)
 {
     if (st && st->done) return;
-    __shared__ double sh[SOLVE_THREADS / 32];
+    __shared__ double sh[2 * SOLVE_THREADS];
     const int lane = threadIdx.x & (G - 1);
     const int64_t i = ((int64_t)blockIdx.x * SOLVE_THREADS + threadIdx.x) / G;
     const bool live = i < n;
@@ -208,8 +224,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const i
         d3 = yi * yi;
     }
     if (!part) return;
-    const double s1 = block_sum(d1, sh);
-    const double s3 = block_sum(d3, sh);
+    double s1, s3;
+    block_sum2<G>(d1, d3, sh, s1, s3);
     if (threadIdx.x == 0) {
         part[3 * blockIdx.x] = s1;
         part[3 * blockIdx.x + 1] = 0.0;
@@ -233,7 +249,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_vec(int64_t n, int phas
                                                             double *__restrict__ part, SolveState *__restrict__ st)
 {
     if (phase != 0 && st->done) return;
-    __shared__ double sh[SOLVE_THREADS / 32];
+    __shared__ double sh[2 * SOLVE_THREADS];
     const double alpha = st ? st->alpha : 0.0, omega = st ? st->omega : 0.0, beta = st ? st->beta : 0.0;
     double d1 = 0.0, d2 = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -272,8 +288,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_vec(int64_t n, int phas
         }
     }
     if (phase == 1) return;
-    const double s1 = block_sum(d1, sh);
-    const double s2 = block_sum(d2, sh);
+    double s1, s2;
+    block_sum2<1>(d1, d2, sh, s1, s2);
     if (threadIdx.x == 0) {
         part[3 * blockIdx.x] = s1;
         part[3 * blockIdx.x + 1] = s2;
