@@ -93,17 +93,32 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_apply(int64_t n, const int64_
             }
         }
     }
+    // Reduce-scatter over the node's G lanes (G >= NP, NOPS padded to the power of two NP): at
+    // offsets G/2, G/4, ... each lane keeps one half of its operators and adds the partner's
+    // half, until it holds one operator's partial, d = lane / (G / NP); the remaining offsets
+    // add that one value.  NP - 1 + log2(G / NP) adds per lane instead of NOPS log2(G) (FP64
+    // adds are scarce), in a fixed order.
+    constexpr int NP = NOPS <= 1 ? 1 : NOPS <= 2 ? 2 : NOPS <= 4 ? 4 : 8;
+    AT v[NP];
 #pragma unroll
-    for (int d = 0; d < NOPS; d++)
-        for (int o = G >> 1; o > 0; o >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
-    if (live) {
+    for (int d = 0; d < NP; d++) v[d] = d < NOPS ? acc[d] : (AT)0;
+    int o = G >> 1;
 #pragma unroll
-        for (int d = 0; d < NOPS; d++) {
-            if (lane == d && ((mask >> d) & 1u)) {
-                int row = __popc(mask & ((1u << d) - 1u));
-                out[(int64_t)row * n + i] = (FT)acc[d];
-            }
+    for (int m = NP; m > 1; m >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < m / 2; j++) {
+            const AT send = upper ? v[j] : v[j + m / 2];
+            const AT keep = upper ? v[j + m / 2] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
+    }
+    for (; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    const int per = G / NP;  // lanes holding the same operator's sum
+    const int d = lane / per;
+    if (live && (lane & (per - 1)) == 0 && d < NOPS && ((mask >> d) & 1u)) {
+        const int row = __popc(mask & ((1u << d) - 1u));
+        out[(int64_t)row * n + i] = (FT)v[0];
     }
 }
 
@@ -390,7 +405,7 @@ uint64_t tune_key(const labfm_ctx *ctx, int kind, int nops, int fdt, int wdt)
 template <int NOPS, class FT, class WT>
 cudaError_t launch_apply_t(labfm_ctx *ctx, uint32_t mask, const void *f, int fdt, void *out)
 {
-    const int min_g = NOPS <= 4 ? 4 : 8;  // lane d writes operator d
+    const int min_g = NOPS <= 4 ? 4 : 8;  // the reduce-scatter needs G >= NOPS rounded up to 2^k
     Shape sh;
     cudaError_t e = autotune(
         ctx, tune_key(ctx, 1, NOPS, fdt, ctx->wdtype), min_g,
