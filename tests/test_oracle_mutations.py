@@ -1,5 +1,9 @@
 """Each pin must be able to fail: plant one plausible mistake at a time in a copy of
-the oracle (compiled separately, on the CPU) and check that at least one pin rejects it."""
+the oracle (the C part compiled separately, on the CPU; the Python solvers of Sec. 5.1-5.2
+re-executed from their mutated source) and check that at least one pin rejects it."""
+import inspect
+import textwrap
+
 import pytest
 
 import oracle
@@ -72,3 +76,49 @@ def test_planted_mistake_is_caught(name, tmp_path, monkeypatch):
         except Exception:  # a crash (e.g. a bad stencil size) also rejects the mutant
             caught.append(pin)
     assert caught, f"no pin caught: {name}"
+
+
+# the global matrix, the steady state and the direct solve (oracle/__init__.py): (function, old, new)
+PY_MUTATIONS = {
+    "global matrix diagonal with the wrong sign": ("operator_matrix", "return (A - sp.diags(", "return (A + sp.diags("),
+    "global matrix transposed (w_ij for w_ji)": (
+        "operator_matrix", "(wb, (node, np.asarray(col, dtype=np.int64)))",
+        "(wb, (np.asarray(col, dtype=np.int64), node))"),
+    "beta ignored (first operator only)": (
+        "operator_matrix", "wb = np.asarray(w, dtype=np.float64) @ np.asarray(beta, dtype=np.float64)",
+        "wb = np.asarray(w, dtype=np.float64)[:, 0]"),
+    "steady state with the boundary term's sign flipped": ("steady_state", "-(A[I][:, B] @ u[B])",
+                                                            "(A[I][:, B] @ u[B])"),
+    "steady state from the transposed interior block": ("steady_state", "spl.spsolve(A[I][:, I].tocsc()",
+                                                        "spl.spsolve(A[I][:, I].T.tocsc()"),
+    "Dirichlet rows ignored": ("solve_operator", "for i in np.nonzero(np.asarray(dirichlet))[0]:",
+                               "for i in np.nonzero(np.asarray(dirichlet))[0][:0]:"),
+    "operator index ignored": ("solve_operator", "beta[op] = 1.0", "beta[0] = 1.0"),
+}
+
+PY_PINS = [  # cheapest first; the first pin that fails ends the search
+    P.test_global_matrix_and_direct_solve_vs_apply,
+    P.test_heat_frozen_rk4_reaches_the_steady_state,
+    lambda: P.test_heat_steady_state_table(2),
+    P.test_poisson_periodic_even_order_pattern,
+]
+
+
+def _mutated(func, old, new):
+    src = textwrap.dedent(inspect.getsource(func))
+    assert src.count(old) == 1, (func.__name__, old)
+    ns = dict(func.__globals__)
+    exec(compile(src.replace(old, new), f"<mutant {func.__name__}>", "exec"), ns)
+    return ns[func.__name__]
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_planted_mistake_in_the_python_solvers_is_caught(name, monkeypatch):
+    fname, old, new = PY_MUTATIONS[name]
+    monkeypatch.setattr(oracle, fname, _mutated(getattr(oracle, fname), old, new))
+    for pin in PY_PINS:
+        try:
+            pin()
+        except Exception:  # an assertion, or a failed solve of a singular system
+            return
+    pytest.fail(f"no pin caught: {name}")

@@ -796,6 +796,35 @@ def poisson_periodic_error(k, nside, hdr, seed=3, eps=0.5):
     return np.linalg.norm(phi - ex) / np.linalg.norm(ex)
 
 
+def test_global_matrix_and_direct_solve_vs_apply():
+    """The global matrix of Sec. 5.2 (eq. poisson_system) against the oracle's stencil apply
+    (Eq. general_do), an independent code path: (A u)_i = sum_d beta_d sum_j (u_j - u_i) w_ji^d
+    for three operators and a random beta; and the direct solve of operator 2 (the Laplacian)
+    with two Dirichlet rows satisfies L^2(phi)_i = f_i off those rows (residual through the
+    apply) and phi_b = f_b on them.  A transposed matrix, a wrong diagonal, an ignored beta or
+    operator index, or dropped Dirichlet rows each fail here."""
+    k = 2
+    ns = S.jittered_lattice(16, 2.0, k, jitter=0.2, seed=11)
+    rp, col = oracle.neighbours(ns.xy, ns.h, True)
+    C = np.stack([S.op_c_vector(o, k) for o in ("dx", "dy", "lap")])
+    r = oracle.build_weights(ns.xy, ns.h, True, rp, col, C, k=k, rbf="quadratic", abf_form="dw0")
+    assert (r["status"] == 0).all()
+    w = r["w"]
+    rng = np.random.default_rng(5)
+    beta, u = rng.standard_normal(3), rng.standard_normal(ns.n)
+    ref = beta @ oracle.apply(rp, col, w, u)
+    got = oracle.operator_matrix(rp, col, w, beta) @ u
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    f = rng.standard_normal(ns.n)
+    dm = np.zeros(ns.n, np.uint8)
+    dm[[0, 37]] = 1
+    phi = oracle.solve_operator(rp, col, w, 2, f, dm)
+    free = dm == 0
+    lap = oracle.apply(rp, col, w, phi)[2]
+    assert np.abs(lap[free] - f[free]).max() <= 1e-9 * np.abs(f).max()
+    assert np.abs(phi[~free] - f[~free]).max() <= 1e-12 * np.abs(f).max()
+
+
 def test_poisson_periodic_even_order_pattern():
     """Sec. 5.2, periodic test case: the solution converges at order 2 for k = 2 and 3, 4 for
     k = 4 and 5, and 8 for k = 8 (h/dr = 3 there): odd k gives the order of k - 1.  Rates from
