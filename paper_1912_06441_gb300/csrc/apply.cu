@@ -6,7 +6,8 @@
 // (f_j - f_i) w.  A group of G lanes shares one node: the lanes read consecutive entries, so
 // every weight and index load of a warp is a contiguous, fully used segment; UNR entries per
 // lane are in flight before the first use.  The partial sums of a group are combined with
-// butterfly shuffles.
+// shuffles: by a reduce-scatter over the operators in the apply (each lane ends with one
+// operator's sum), by a butterfly tree in the RK4 and Burgers stages.
 //
 // (G, UNR) is chosen per context by a small autotuner: the first apply (or RK4 run) for a
 // given operator count, data types and problem class times every shape once on the real
