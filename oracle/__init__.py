@@ -4,9 +4,10 @@ TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
 baseline of ``bench.py`` use this package.  The library under
 ``paper_1912_06441_gb300`` never imports it, and it imports nothing from there.
 
-The numerics live in ``labfm_oracle.c`` (plain C, FP64; a second build in
-``long double`` measures the FP64 rounding floor).  This module compiles it
-with gcc on first use and marshals numpy arrays through ctypes.
+The numerics live in ``labfm_oracle.c`` (plain C, FP64; further builds of the
+same source in ``long double`` and in IEEE binary128 measure the FP64 rounding
+floor).  This module compiles it with gcc on first use and marshals numpy
+arrays through ctypes.
 """
 from __future__ import annotations
 
@@ -36,16 +37,27 @@ def lib_path(precision: str = "f64") -> str:
     return os.path.join(_BUILD, f"liblabfm_oracle_{precision}.so")
 
 
+def _real_flags(precision: str):
+    """gcc flags of one instantiation: ``f64`` double, ``ld`` long double (80-bit extended on
+    x86-64, IEEE binary128 on aarch64), ``q`` _Float128 (IEEE binary128 on both)."""
+    if precision == "f64":
+        return ["-std=c11", "-DORC_REAL=double"]
+    if precision == "ld":
+        return ["-std=c11", "-DORC_REAL=long double"]
+    if precision == "q":
+        return ["-std=gnu11", "-D__STDC_WANT_IEC_60559_TYPES_EXT__", "-DORC_REAL=_Float128", "-DORC_MANT_DIG=113"]
+    raise ValueError(precision)
+
+
 def build(precision: str = "f64", force: bool = False) -> str:
-    """Compile the oracle (``f64`` or ``ld`` = long double) into ``oracle/_build``."""
+    """Compile the oracle (``f64``, ``ld`` = long double or ``q`` = binary128) into ``oracle/_build``."""
     out = lib_path(precision)
     if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
         return out
     os.makedirs(_BUILD, exist_ok=True)
-    real = "double" if precision == "f64" else "long double"
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
-           f"-DORC_REAL={real}", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", *_real_flags(precision), "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+           "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
@@ -97,9 +109,8 @@ def compile_variant(source_text: str, out_path: str, precision: str = "f64"):
     src = out_path + ".c"
     with open(src, "w") as fh:
         fh.write(source_text)
-    real = "double" if precision == "f64" else "long double"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
-                    f"-DORC_REAL={real}", "-o", out_path, src, "-lm"], check=True)
+    subprocess.run(["gcc", "-O2", *_real_flags(precision), "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                    "-o", out_path, src, "-lm"], check=True)
     return _configure(ct.CDLL(out_path))
 
 

@@ -33,8 +33,9 @@
  * t = 1 - q/2 (compact kernels) or as polynomial * exp(-9 q^2) (Gaussian) and
  * differentiating term by term.
  *
- * ORC_REAL selects the working precision: double (default) or long double
- * (used only to measure the rounding floor of the double build).
+ * ORC_REAL selects the working precision: double (default), long double or
+ * _Float128 (IEEE binary128, compiled with ORC_MANT_DIG=113); the wider ones are
+ * used only to measure the rounding floor of the double build.
  * Compile with -ffp-contract=off so that no multiply-add is fused: the
  * neighbour predicate must round exactly as written.
  */
@@ -639,4 +640,7 @@ int orc_rk4_burgers(int64_t n, const int64_t *row_ptr, const int32_t *col, const
 }
 
 /* precision of the real type this file was compiled with, in bits of significand */
-int orc_real_mant_bits(void) { return sizeof(real) == sizeof(double) ? DBL_MANT_DIG : LDBL_MANT_DIG; }
+#ifndef ORC_MANT_DIG
+#define ORC_MANT_DIG (sizeof(real) == sizeof(double) ? DBL_MANT_DIG : LDBL_MANT_DIG)
+#endif
+int orc_real_mant_bits(void) { return ORC_MANT_DIG; }

@@ -352,14 +352,15 @@ def test_p6_order8_exact_to_rounding():
     """Eq. (p6) with k = 8 and conic ABFs, h/dr = 2.5, ghost strip (Sec. 4.1): the degree-8
     test function is reproduced to rounding.  The error is a rounding floor: the long-double
     build of the same oracle cuts it by more than 100x (the paper quotes ~1e-14 for
-    gradients and ~1e-13 for Laplacians, which the long-double build reaches)."""
+    gradients and ~1e-13 for Laplacians, which the long-double build reaches), and so does the
+    binary128 build (on every host; its inputs and the exact values are doubles)."""
     f = S.p6_field()
     xy, h, q = _ghost_lattice(16, 2.5, 0.25, seed=11)
     rp, col = oracle.neighbours(xy, h, False, *BIG, queries=q)
     ops = ("dx", "dy", "lap")
     C = np.stack([S.op_c_vector(o, 8) for o in ops])
     errs = {}
-    for prec in ("f64", "ld"):
+    for prec in ("f64", "ld", "q"):
         r = oracle.build_weights(xy, h, False, rp, col, C, k=8, queries=q, rbf="cone",
                                  lo=BIG[0], hi=BIG[1], precision=prec)
         out = oracle.apply(rp, col, r["w"], f.value(xy), queries=q, precision=prec)
@@ -369,6 +370,8 @@ def test_p6_order8_exact_to_rounding():
     assert max(errs["ld"][:2]) < 1e-12 and errs["ld"][2] < 1e-11, errs
     if oracle.mant_bits("ld") > 53:
         assert max(errs["ld"]) < max(errs["f64"]) / 30, errs
+    assert oracle.mant_bits("q") == 113
+    assert max(errs["q"]) < max(errs["f64"]) / 100, errs
 
 
 def _slopes(errs, hh):
