@@ -121,6 +121,46 @@ def jittered_lattice(n_side: int, h_over_s: float, k: int, jitter: float = 0.3,
                    lo=(0.0, 0.0), hi=(1.0, 1.0))
 
 
+def lattice_clusters(n_side: int, h_over_s: float, corners, extent: float, jitter: float = 0.3,
+                     seed: int = 1) -> NodeSet:
+    """Dense jittered-lattice blocks in an otherwise empty, non-periodic unit box: one
+    n_side x n_side block (spacing extent / n_side, h = h_over_s x spacing) with its lower-left
+    corner at each point of `corners`.  The stencil radius is then tiny against the box, so a
+    cell grid of side 2h would hold many more cells than nodes; a search that caps its cell
+    count ends up with coarse cells holding hundreds of nodes each."""
+    blocks = []
+    for c, (cx, cy) in enumerate(corners):
+        b = jittered_lattice(n_side, h_over_s, 4, jitter=jitter, seed=seed + c, periodic=False)
+        blocks.append(np.stack([cx + b.xy[:, 0] * extent, cy + b.xy[:, 1] * extent], axis=1))
+    xy = np.ascontiguousarray(np.concatenate(blocks))
+    n = xy.shape[0]
+    s = extent / n_side
+    return NodeSet(xy=xy, h=np.full(n, h_over_s * s), s=np.full(n, s), order=np.full(n, 4, dtype=np.int8),
+                   periodic=False, lo=(0.0, 0.0), hi=(1.0, 1.0))
+
+
+def three_ring_stencil(delta: float, h: float = 0.05, seed: int = 7) -> NodeSet:
+    """A node at (0.5, 0.5) whose 66 neighbours lie on three circles about it (radii 0.55 h,
+    1.1 h and 1.6 h; 14, 22 and 30 nodes at jittered angles), each radius scaled by
+    1 + delta U(-1, 1) per node; non-periodic unit box, uniform h.  On the exact circles
+    x (r^2 - a^2)(r^2 - b^2)(r^2 - c^2) vanishes at every neighbour, a polynomial of degree 7
+    without constant term, so the moment matrix of order k >= 7 is singular; the radial
+    noise delta makes it merely ill conditioned, with a condition number growing as delta^-2."""
+    u = uniform01(seed, 200)
+    pts = [(0.5, 0.5)]
+    t = 0
+    for rad, cnt in zip((0.55 * h, 1.1 * h, 1.6 * h), (14, 22, 30)):
+        for a in range(cnt):
+            th = 2.0 * np.pi * (a + 0.5 * u[t]) / cnt
+            rr = rad * (1.0 + delta * (2.0 * u[t + 100] - 1.0))
+            t += 1
+            pts.append((0.5 + rr * np.cos(th), 0.5 + rr * np.sin(th)))
+    xy = np.ascontiguousarray(np.array(pts))
+    n = xy.shape[0]
+    return NodeSet(xy=xy, h=np.full(n, h), s=np.full(n, h / 2.2), order=np.full(n, 8, dtype=np.int8),
+                   periodic=False, lo=(0.0, 0.0), hi=(1.0, 1.0))
+
+
 # h/s per order for the variable-resolution set (each above the critical h/dr of Sec. 3.2).
 H_OVER_S_BY_ORDER = {2: 1.0, 3: 1.1, 4: 1.4, 5: 1.6, 6: 1.8, 7: 2.0, 8: 2.2}
 

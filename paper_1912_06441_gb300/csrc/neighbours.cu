@@ -294,8 +294,7 @@ constexpr size_t NA_SCAN_ELEMS = 4096;
 constexpr size_t NA_BYTES = na_align(NA_OFF_SCAN + 8 * NA_SCAN_ELEMS);  // about 10 MB
 
 constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_na_mutex;
-void *g_na_ptr[NA_MAX_DEVICES] = {};  // device address of the scratch array, per device
+std::mutex g_na_mutex;  // serialises the address lookup (the array itself is not guarded)
 
 struct DeviceGuard {
     int prev = -1;
@@ -330,15 +329,16 @@ extern "C" labfm_status labfm_build_neighbours_noalloc(int device, void *stream,
         if (cudaSetDevice(device) != cudaSuccess) return LABFM_ERR_CUDA;
         guard.changed = true;
     }
+    // The array's device address, looked up on every call with the device current: in host code
+    // g_noalloc_scratch names a host-side stand-in, and an address kept from an earlier call would
+    // be stale after the device's primary context was reset (the module is then loaded again).
+    // The first call on a device also loads the library's device code there.
     char *base;
     {
         std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_ptr[device]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LABFM_ERR_CUDA;
-            g_na_ptr[device] = p;
-        }
-        base = static_cast<char *>(g_na_ptr[device]);
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LABFM_ERR_CUDA;
+        base = static_cast<char *>(p);
     }
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *misc = reinterpret_cast<unsigned long long *>(base + NA_OFF_MISC);

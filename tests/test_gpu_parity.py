@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Stencils must match bit for bit.  Weights and derivatives are compared per node with the
-long-double oracle, within max(1e-11, 30 x the FP64 oracle's own error) -- the FP64 floor is
+binary128 oracle, within max(1e-11, 30 x the FP64 oracle's own error) -- the FP64 floor is
 ~1e-13 at k = 4 but ~1e-8 (worst node) at k = 8, where two correct FP64 computations that
 differ only in summation order already disagree (see tests/gpu_common.py).
 """
@@ -34,6 +34,9 @@ NBR_CASES = [
     ("lattice8_two_cells_periodic", lambda: S.jittered_lattice(8, 1.8, 4, seed=4)),
     ("lattice6_one_cell_periodic", lambda: S.jittered_lattice(6, 3.0, 4, seed=5)),
     ("variable_spacing_walls", lambda: S.variable_wall_nodes(48, seed=4)),
+    # radius tiny against the box: the search caps its grid at 4n + 64 cells (coarse cells of
+    # ~100 nodes each)
+    ("cluster_capped_grid_walls", lambda: S.lattice_clusters(40, 1.4, [(0.3, 0.3)], 0.04, seed=21)),
 ]
 
 
@@ -53,6 +56,32 @@ def test_neighbours_bit_exact(name, make):
     assert nnz == len(ocol)
     assert np.array_equal(rp.cpu().numpy(), orp)
     assert np.array_equal(col.cpu().numpy(), ocol)
+
+
+def test_neighbours_capped_grid_two_clusters():
+    """100,352 nodes in two dense blocks at opposite corners of the unit box (spacing 1e-4,
+    h = 1.4e-4): a grid of side 2h would have 12.8 M cells, the search caps it at 4n + 64 and
+    its cells hold ~350 nodes each.  Sampled rows (both blocks' edges included) against the
+    oracle's brute force, bit for bit; no row reaches across the gap between the blocks."""
+    import torch
+
+    from paper_1912_06441_gb300 import Labfm
+
+    ns = S.lattice_clusters(224, 1.4, [(0.05, 0.05), (0.9, 0.9)], 0.0224, seed=22)
+    dev = torch.device("cuda", 0)
+    L = Labfm(0)
+    L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), False, ns.lo, ns.hi)
+    rp_d, col_d = L.get_neighbours()
+    rp, col = rp_d.cpu().numpy(), col_d.cpu().numpy()
+    half = ns.n // 2
+    q = np.unique(np.concatenate([(S.uniform01(23, 300) * ns.n).astype(np.int64),
+                                  np.arange(0, 224), np.arange(half - 224, half + 224), np.arange(ns.n - 224, ns.n)]))
+    rp_q, col_q, _ = G.rows_of(rp, col, q)
+    orp, ocol = oracle.neighbours(ns.xy, ns.h, False, ns.lo, ns.hi, queries=q)
+    assert np.array_equal(rp_q, orp) and np.array_equal(col_q, ocol)
+    # rows never cross between the blocks
+    node = np.repeat(np.arange(ns.n), np.diff(rp))
+    assert np.array_equal(node < half, col < half)
 
 
 def test_neighbours_single_node_and_empty_rows():
@@ -220,11 +249,11 @@ def test_apply_parity(k):
     absterm = np.abs(f[col] - np.repeat(f, np.diff(rp)))[:, None] * np.abs(w)
     bound = np.add.reduceat(absterm, rp[:-1], axis=0).T  # [n_ops, n]
     assert np.all(np.abs(out - ref_same) <= 1e-14 * bound + 1e-300)
-    # (b) end to end against the long-double oracle, bounded by the FP64 oracle's own error
+    # (b) end to end against the binary128 oracle, bounded by the FP64 oracle's own error
     q = np.arange(0, ns.n, 4)
     rp_q, col_q, idx = G.rows_of(rp, col, q)
     r64, rld = G.oracle_refs(ns, k, ops, q, rp_q, col_q)
-    d_ld = oracle.apply(rp_q, col_q, rld["w"], f, queries=q, precision="ld")
+    d_ld = oracle.apply(rp_q, col_q, rld["w"], f, queries=q, precision=G.REF_PRECISION)
     d_64 = oracle.apply(rp_q, col_q, r64["w"], f, queries=q)
     sc = np.abs(d_ld).max(axis=1)
     e_gpu = (np.abs(out[:, q] - d_ld).max(axis=1)) / sc

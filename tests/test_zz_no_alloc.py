@@ -82,3 +82,73 @@ def test_noalloc_reports_capacity_and_size_limits():
     assert big.n > P.NOALLOC_MAX_NODES
     st, _, _, _ = _noalloc(lib, big, capacity=1)
     assert st == 4
+
+
+def test_noalloc_allocates_nothing_after_its_first_call():
+    """The call that exists so that a caller need not allocate must not allocate either: once
+    the first call on the device has loaded the library's device code (the fixed array with it),
+    a second call leaves the device's free memory unchanged."""
+    import torch
+
+    import paper_1912_06441_gb300 as P
+
+    lib = P.load_library()
+    ns = S.jittered_lattice(128, 2.2, 8, seed=12)
+    rp_ref, col_ref = _reference(ns)
+    dev = torch.device("cuda", 0)
+    xy = torch.from_numpy(ns.xy).to(dev)
+    h = torch.from_numpy(ns.h).to(dev)
+    row_ptr = torch.empty(ns.n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(len(col_ref), dtype=torch.int32, device=dev)
+    lo = (ct.c_double * 2)(*ns.lo)
+    hi = (ct.c_double * 2)(*ns.hi)
+    nnz = ct.c_int64(-1)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def call():
+        return lib.labfm_build_neighbours_noalloc(0, ct.c_void_p(stream), ns.n, ct.c_void_p(xy.data_ptr()),
+                                                  ct.c_void_p(h.data_ptr()), int(ns.periodic), lo, hi,
+                                                  ct.c_void_p(row_ptr.data_ptr()), ct.c_void_p(col.data_ptr()),
+                                                  len(col_ref), ct.byref(nnz))
+
+    assert call() == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for _ in range(3):
+        assert call() == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0, (free0, free1)
+    assert np.array_equal(row_ptr.cpu().numpy(), rp_ref) and np.array_equal(col.cpu().numpy(), col_ref)
+
+
+def test_noalloc_capped_grid_matches_the_oracle():
+    """Node sets whose radius is tiny against the box, so that the cell grid is capped: at
+    4n + 64 cells (1,600 nodes in one dense block), and at the fixed array's cell limit (100,352
+    nodes in two blocks: the allocating entry point then uses a finer grid than this one).  The
+    stencils must be the oracle's, bit for bit (all rows of the small set, sampled rows of the
+    large one), and the allocating entry point's on every row."""
+    import oracle
+
+    import paper_1912_06441_gb300 as P
+
+    lib = P.load_library()
+    small = S.lattice_clusters(40, 1.4, [(0.3, 0.3)], 0.04, seed=21)
+    st, nnz, rp, col = _noalloc(lib, small, capacity=200000)
+    assert st == 0
+    orp, ocol = oracle.neighbours(small.xy, small.h, False, small.lo, small.hi)
+    assert np.array_equal(rp, orp) and np.array_equal(col[:nnz], ocol)
+
+    big = S.lattice_clusters(224, 1.4, [(0.05, 0.05), (0.9, 0.9)], 0.0224, seed=22)
+    assert 4 * big.n + 64 > P.NOALLOC_MAX_NODES  # the fixed array's limit is the binding cap
+    rp_ref, col_ref = _reference(big)
+    st, nnz, rp, col = _noalloc(lib, big, capacity=len(col_ref))
+    assert st == 0 and nnz == len(col_ref)
+    assert np.array_equal(rp, rp_ref) and np.array_equal(col, col_ref)
+    q = np.unique(np.concatenate([(S.uniform01(24, 300) * big.n).astype(np.int64), np.arange(0, 224),
+                                  np.arange(big.n - 224, big.n)]))
+    lens = rp[q + 1] - rp[q]
+    sub = np.concatenate([[0], np.cumsum(lens)])
+    idx = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in q])
+    orp, ocol = oracle.neighbours(big.xy, big.h, False, big.lo, big.hi, queries=q)
+    assert np.array_equal(sub, orp) and np.array_equal(col[idx], ocol)
