@@ -442,36 +442,62 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "BiCGStab chunk capture");
     }
+    // Chunks of iterations until the device flag ends them; then the true residual.  The
+    // recurrence residual drifts from the true one in finite precision: when the recurrence
+    // says converged but the true residual is above tol, BiCGStab restarts from the current
+    // iterate (r = F - A Phi, r^ = r), at most MAX_RESTARTS times within max_iter in total.
+    constexpr int MAX_RESTARTS = 4;
     SolveState h{};
+    int total = 0, restarts = 0;
+    double resid = 0.0;
+    std::vector<double> hp(3 * (size_t)nblk_vec);
     cudaError_t le = cudaSuccess;
-    for (int it = 0; it < max_iter && le == cudaSuccess; it += CHUNK) {
-        le = cudaGraphLaunch(exec, s);  // the iteration limit stops the last chunk early (done = 3)
-        if (le == cudaSuccess) le = cudaMemcpyAsync(&h, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s);
+    while (true) {
+        for (int it = 0; it < max_iter - total && le == cudaSuccess; it += CHUNK) {
+            le = cudaGraphLaunch(exec, s);  // the iteration limit stops the last chunk early (done = 3)
+            if (le == cudaSuccess) le = cudaMemcpyAsync(&h, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s);
+            if (le == cudaSuccess) le = cudaStreamSynchronize(s);
+            if (h.done) break;
+        }
+        if (le != cudaSuccess) break;
+        total += h.iters;
+        // the true residual ||b - A x|| / ||b||: t = A x, then phase 0 on scratch copies
+        spmv(s, phi, t, nullptr, -1);
+        k_solve_vec<<<nblk_vec, SOLVE_THREADS, 0, s>>>(n, 0, f, nullptr, t, sv, z, y, nullptr, nullptr, nullptr,
+                                                       nullptr, nullptr, part, nullptr);
+        le = cudaGetLastError();
+        if (le == cudaSuccess)
+            le = cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s);
         if (le == cudaSuccess) le = cudaStreamSynchronize(s);
-        if (h.done) break;
+        if (le != cudaSuccess) break;
+        double rr = 0.0, bb = 0.0;
+        for (int k = 0; k < nblk_vec; k++) {
+            rr += hp[3 * k];
+            bb += hp[3 * k + 1];
+        }
+        resid = std::sqrt(rr) / (bb > 0.0 ? std::sqrt(bb) : 1.0);
+        if (h.done == 1 && std::isfinite(resid) && resid > tol && restarts < MAX_RESTARTS && total < max_iter) {
+            restarts++;
+            init.max_iter = max_iter - total;
+            le = cudaMemcpyAsync(st, &init, sizeof(SolveState), cudaMemcpyHostToDevice, s);
+            if (le != cudaSuccess) break;
+            spmv(s, phi, r, nullptr, -1);
+            vec(s, 0);
+            le = cudaGetLastError();
+            if (le != cudaSuccess) break;
+            continue;
+        }
+        break;
     }
     cudaGraphExecDestroy(exec);
     if (le != cudaSuccess) return cuda_fail(ctx, le, "BiCGStab iterations");
-    // the true residual ||b - A x|| / ||b||: t = A x, then phase 0 on scratch copies
-    spmv(s, phi, t, nullptr, -1);
-    k_solve_vec<<<nblk_vec, SOLVE_THREADS, 0, s>>>(n, 0, f, nullptr, t, sv, z, y, nullptr, nullptr, nullptr, nullptr,
-                                                   nullptr, part, nullptr);
-    LABFM_CUDA_TRY(ctx, cudaGetLastError());
-    std::vector<double> hp(3 * (size_t)nblk_vec);
-    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s));
-    LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    double rr = 0.0, bb = 0.0;
-    for (int k = 0; k < nblk_vec; k++) {
-        rr += hp[3 * k];
-        bb += hp[3 * k + 1];
-    }
-    const double resid = std::sqrt(rr) / (bb > 0.0 ? std::sqrt(bb) : 1.0);
-    if (iters_out) *iters_out = h.iters;
+    if (iters_out) *iters_out = total;
     if (resid_out) *resid_out = resid;
-    if (h.done == 1 && std::isfinite(resid)) return LABFM_OK;
+    if (h.done == 1 && std::isfinite(resid) && resid <= tol) return LABFM_OK;
     return fail(ctx, LABFM_ERR_NOT_CONVERGED,
-                h.done == 2 ? "BiCGStab breakdown (rho, alpha or omega vanished or was not finite)"
-                            : "BiCGStab did not reach the tolerance within max_iter iterations");
+                h.done == 2   ? "BiCGStab breakdown (rho, alpha or omega vanished or was not finite)"
+                : h.done == 1 ? "the true residual stayed above tol after the restarts"
+                              : "BiCGStab did not reach the tolerance within max_iter iterations");
 }
 
 }  // namespace labfm

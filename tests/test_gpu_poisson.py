@@ -60,7 +60,7 @@ def test_poisson_periodic_matches_oracle(weight_dtype):
     the operator by ~1e-7 relative, which the solution follows at 1e-4)."""
     ns, L, ex, f, dm = _periodic_problem(4, 40, weight_dtype=weight_dtype)
     phi, iters, resid = _gpu_solve(L, f, dm)
-    assert resid <= 1e-12 and 0 < iters < 20000
+    assert resid <= 1e-13 and 0 < iters < 20000  # LABFM_OK means the true residual met tol
     ref = _oracle_solve(ns, 4, f, dm)
     tol = 1e-8 if weight_dtype == "f64" else 1e-4
     assert np.abs(phi - ref).max() <= tol * np.abs(ref).max(), np.abs(phi - ref).max()
@@ -79,6 +79,7 @@ def test_poisson_dirichlet_walls_matches_oracle():
     f = np.where(ns.wall, ex, -8 * np.pi ** 2 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y))
     dm = ns.wall.astype(np.uint8)
     phi, iters, resid = _gpu_solve(L, f, dm)
+    assert resid <= 1e-13
     ref = _oracle_solve(ns, k, f, dm)
     assert np.abs(phi - ref).max() <= 1e-8 * np.abs(ref).max()
     assert np.array_equal(phi[ns.wall], ex[ns.wall])
