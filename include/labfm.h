@@ -74,7 +74,13 @@ enum {
     /* X and W in double; M, its partially pivoted LU, Psi and W . Psi in double-float
      * (pairs of FP32, ~48 bits, on the FP32 pipes); then iterative refinement on the
      * polynomial-reproduction residual C - sum_j X_j w_j computed in double (the moment
-     * conditions of Sec. 3.1).  Default: 1 refinement step. */
+     * conditions of Sec. 3.1).  Default: adaptive per node.  With eta_t the relative size of the
+     * t-th change of a node's weights (largest over its operators, eta_0 = 1), the node stops
+     * after step t >= 1 once eta_t^2 / eta_(t-1) < 2^-44 (converged; one step for most nodes),
+     * or once eta_t > eta_(t-1) / 2 (the corrections have reached the rounding level of the
+     * FP64 residual), or after 6 steps.  A node whose corrections grow instead (eta_t above
+     * both eta_(t-1) / 2 and 1e-3: M too ill-conditioned for the double-float inverse) is built
+     * again by the FP64 path (LABFM_PREC_FP64).  labfm_get_build_info reports both counts. */
     LABFM_PREC_MIXED = 1,
     /* As LABFM_PREC_MIXED, with M formed on the tensor cores: X and W are scaled per row (a power
      * of two per chunk of <= 64 neighbours) and cut into seven 8-bit BF16 slices; the slice
@@ -82,7 +88,7 @@ enum {
      * in tensor memory) and combined in double-float. */
     LABFM_PREC_MIXED_TC = 2
 };
-/* LABFM_PREC_MIXED with exactly n refinement steps, n = 0..4 */
+/* LABFM_PREC_MIXED with exactly n refinement steps, n = 0..4 (no adaptive rule, no FP64 rebuild) */
 #define LABFM_PREC_MIXED_REFINE(n) (LABFM_PREC_MIXED | (((n) + 1) << 8))
 /* LABFM_PREC_MIXED_TC with exactly n refinement steps, n = 0..4 */
 #define LABFM_PREC_MIXED_TC_REFINE(n) (LABFM_PREC_MIXED_TC | (((n) + 1) << 8))
@@ -172,6 +178,20 @@ labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int unifor
                                  int n_ops, const double *C, int precision, int weight_dtype,
                                  int32_t *node_status, int64_t *n_bad_out);
 
+/* Statistics of the last successful labfm_build_weights on this context. */
+typedef struct {
+    /* mixed builds: nodes by the number of refinement steps they took (index 0..7; with the
+     * default adaptive rule at most 6), the nodes then rebuilt in FP64 included; nodes flagged
+     * before the refinement (undersampled, a zero pivot, a non-finite M) are not counted; all
+     * zero after an FP64 build */
+    int64_t refine_steps[8];
+    /* mixed builds: nodes whose refinement diverged and that the FP64 build redid */
+    int64_t fp64_rebuilt;
+} labfm_build_info;
+
+/* Copy the statistics of the last weight build into *info.  LABFM_ERR_STATE before a build. */
+labfm_status labfm_get_build_info(labfm_ctx *ctx, labfm_build_info *info);
+
 /* Context-owned device view of the weights: *w points to [nnz][n_ops] of *dtype. */
 labfm_status labfm_get_weights(labfm_ctx *ctx, const void **w, int *dtype, int *n_ops);
 
@@ -252,7 +272,10 @@ labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, voi
  * state per chunk.  The product's launch shape (lanes per node x entries in flight, 3 x 3 shapes)
  * is timed once per problem class (floor(log2 n), mean stencil size) on a context, as for
  * labfm_apply (n >= 4096, stream not capturing).
- * Stops when ||F - A Phi|| <= tol ||F|| (the recurrence residual), or after max_iter iterations.
+ * Stops when the recurrence residual ||r|| <= tol ||F||, or after max_iter iterations.  The
+ * recurrence residual drifts from the true one ||F - A Phi|| in finite precision, so the true
+ * residual is then formed; if it is above tol, the iteration restarts from the current Phi
+ * (r = F - A Phi), at most 4 times and within max_iter iterations in total.
  * With a periodic node set A has the constants in its null space: fix at least one node with the
  * Dirichlet mask.
  *   op          operator index (0 <= op < n_ops), weights of either dtype
@@ -261,10 +284,11 @@ labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, voi
  *               entry, and then stay exact), the solution out (distinct from f)
  *   dirichlet   device uint8[n] or NULL
  *   tol         relative residual target, > 0;  max_iter >= 1
- *   iters_out   host, may be NULL: iterations taken
+ *   iters_out   host, may be NULL: iterations taken (over all restarts)
  *   resid_out   host, may be NULL: the true relative residual ||F - A Phi|| / ||F|| at exit
- * Returns LABFM_ERR_NOT_CONVERGED on breakdown or when max_iter ends the iteration (phi holds the
- * last iterate).  Synchronises the context stream.  LABFM_ERR_STATE before labfm_build_weights.
+ * Returns LABFM_OK only when that true residual is <= tol; LABFM_ERR_NOT_CONVERGED on breakdown,
+ * when max_iter ends the iteration, or when the true residual stays above tol after the restarts
+ * (phi holds the last iterate).  Synchronises the context stream.  LABFM_ERR_STATE before labfm_build_weights.
  */
 labfm_status labfm_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet,
                          double tol, int max_iter, int *iters_out, double *resid_out);
@@ -296,11 +320,13 @@ labfm_status labfm_solve(labfm_ctx *ctx, int op, const double *f, double *phi, c
  * n > LABFM_NOALLOC_MAX_NODES or nnz > col_capacity (row_ptr is then valid, col untouched),
  * LABFM_ERR_CUDA on a CUDA error.  The call synchronises `stream` before returning.
  *
- * The first call on a device looks up the device address of the fixed array (once per
- * device); make that first call before any stream capture begins.  All calls share the one
- * array per device: calls whose GPU work overlaps (on different streams or host threads) race
- * on it and must be serialised by the caller.  The array keeps the previous call's contents;
- * every call clears what it needs cleared.
+ * Every call looks up the device address of the fixed array with the device current (so a
+ * reset of the device's primary context between calls is harmless); the first call on a device
+ * also loads the library's device code there, so make it before any stream capture begins (the
+ * call synchronises `stream` and cannot itself be captured).  All calls share the one array per
+ * device: calls whose GPU work overlaps (on different streams or host threads) race on it and
+ * must be serialised by the caller.  The array keeps the previous call's contents; every call
+ * clears what it needs cleared.
  */
 #define LABFM_NOALLOC_MAX_NODES 262144
 labfm_status labfm_build_neighbours_noalloc(int device, void *stream, int64_t n, const double *xy, const double *h,

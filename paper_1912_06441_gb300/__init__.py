@@ -41,7 +41,7 @@ MAX_OPS = 8
 # every symbol include/labfm.h declares
 C_FUNCTIONS = ["labfm_create", "labfm_destroy", "labfm_last_error", "labfm_set_stream", "labfm_build_neighbours",
                "labfm_get_neighbours", "labfm_build_weights", "labfm_get_weights", "labfm_apply", "labfm_step",
-               "labfm_step_burgers", "labfm_solve", "labfm_build_neighbours_noalloc"]
+               "labfm_step_burgers", "labfm_solve", "labfm_build_neighbours_noalloc", "labfm_get_build_info"]
 NOALLOC_MAX_NODES = 262144  # LABFM_NOALLOC_MAX_NODES
 
 _lib = None
@@ -91,9 +91,16 @@ def load_library(path: str | None = None, build_if_missing: bool = False):
     lib.labfm_solve.restype = I
     lib.labfm_build_neighbours_noalloc.argtypes = [I, P, I64, P, P, I, P, P, P, P, I64, ct.POINTER(I64)]
     lib.labfm_build_neighbours_noalloc.restype = I
+    lib.labfm_get_build_info.argtypes = [P, ct.POINTER(_BuildInfo)]
+    lib.labfm_get_build_info.restype = I
     if path is None:
         _lib = lib
     return lib
+
+
+class _BuildInfo(ct.Structure):
+    """labfm_build_info"""
+    _fields_ = [("refine_steps", ct.c_int64 * 8), ("fp64_rebuilt", ct.c_int64)]
 
 
 class _DevView:
@@ -232,6 +239,13 @@ class Labfm:
         self._check(st)
         self.n_ops = n_ops
         return int(nbad.value)
+
+    def get_build_info(self):
+        """Statistics of the last weight build: {"refine_steps": [nodes taking 0..7 refinement
+        steps], "fp64_rebuilt": nodes the FP64 build redid} (mixed builds; zeros after FP64)."""
+        info = _BuildInfo()
+        self._check(self.lib.labfm_get_build_info(self._ctx, ct.byref(info)))
+        return {"refine_steps": list(info.refine_steps), "fp64_rebuilt": int(info.fp64_rebuilt)}
 
     def get_weights(self):
         """Context-owned weights as a torch view [nnz, n_ops]."""

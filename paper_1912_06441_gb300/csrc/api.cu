@@ -205,7 +205,7 @@ labfm_status labfm_create(labfm_ctx **out, int device, void *stream)
     ctx->device = device;
     ctx->stream = (cudaStream_t)stream;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMallocHost(&ctx->host_small, 256) != cudaSuccess) {
+    if (cudaMallocHost(&ctx->host_small, 1024) != cudaSuccess) {  // status words read back by the calls
         delete ctx;
         return LABFM_ERR_NOMEM;
     }
@@ -220,7 +220,7 @@ void labfm_destroy(labfm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->node_xy, &ctx->node_h, &ctx->row_ptr, &ctx->col, &ctx->cell_of, &ctx->cell_count, &ctx->cell_start,
                       &ctx->cell_nodes, &ctx->counts, &ctx->scan_tmp, &ctx->misc, &ctx->w,
-                      &ctx->status_tmp, &ctx->wtilde, &ctx->mscratch, &ctx->mrecs, &ctx->mwstore, &ctx->wcomb, &ctx->rk_acc,
+                      &ctx->status_tmp, &ctx->wtilde, &ctx->mscratch, &ctx->mrecs, &ctx->mwstore, &ctx->mfallback, &ctx->wcomb, &ctx->rk_acc,
                       &ctx->rk_stage_a, &ctx->rk_stage_b, &ctx->wburg, &ctx->bu_acc, &ctx->bu_stage_a,
                       &ctx->bu_stage_b, &ctx->sol_w, &ctx->sol_vec, &ctx->sol_part};
     for (DevBuf *b : bufs) b->release();
@@ -314,6 +314,15 @@ labfm_status labfm_build_weights(labfm_ctx *ctx, const int8_t *order, int unifor
         ctx->grad01 = g;
     }
     return st;
+}
+
+labfm_status labfm_get_build_info(labfm_ctx *ctx, labfm_build_info *info)
+{
+    if (!ctx || !info) return LABFM_ERR_ARG;
+    if (!ctx->have_weights) return fail(ctx, LABFM_ERR_STATE, "no weights built");
+    for (int t = 0; t < 8; t++) info->refine_steps[t] = ctx->info_ref_hist[t];
+    info->fp64_rebuilt = ctx->info_fp64_rebuilt;
+    return LABFM_OK;
 }
 
 labfm_status labfm_get_weights(labfm_ctx *ctx, const void **w, int *dtype, int *n_ops)

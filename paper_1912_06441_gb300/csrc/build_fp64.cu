@@ -415,12 +415,14 @@ __global__ void k_order_scatter(int64_t n, const int8_t *__restrict__ order, con
 
 }  // namespace
 
-static int precision_nref(int precision, int k)
+// Refinement steps of a mixed build: LABFM_PREC_MIXED[_TC]_REFINE(n) fixes n; otherwise each
+// node refines until it converges (at most NREF_ADAPTIVE steps; one for most nodes).
+constexpr int NREF_ADAPTIVE = 6;
+static int precision_nref(int precision, bool &adaptive)
 {
     int forced = (precision >> 8) & 0xf;  // LABFM_PREC_MIXED_REFINE(n) stores n + 1 here
-    if (forced) return forced - 1;
-    (void)k;
-    return 1;  // one step reaches the FP64 floor at every order (measured up to k = 8)
+    adaptive = forced == 0;
+    return forced ? forced - 1 : NREF_ADAPTIVE;
 }
 
 labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops, const double *Cin,
@@ -435,8 +437,13 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
     if (mixed) LABFM_CUDA_TRY(ctx, ctx->wtilde.reserve((size_t)ctx->nnz * n_ops * 8 + 8));
     LABFM_CUDA_TRY(ctx, ctx->misc.reserve(4096));
     unsigned long long *dmisc = ctx->misc.as<unsigned long long>();
-    // misc layout: [0] bad nodes, [1] bad orders, [2..10] order counts, [11..19] bases, [20..28] cursors
-    LABFM_CUDA_TRY(ctx, cudaMemsetAsync(dmisc, 0, 32 * sizeof(unsigned long long), s));
+    // misc layout: [0] bad nodes, [1] bad orders, [2..10] order counts, [11..19] bases, [20..28] cursors,
+    // [30] tensor-core waits that gave up, [31] nodes handed to the FP64 build, [32..39] nodes by
+    // refinement steps
+    constexpr int NMISC = 40;
+    LABFM_CUDA_TRY(ctx, cudaMemsetAsync(dmisc, 0, NMISC * sizeof(unsigned long long), s));
+    for (int t = 0; t < 8; t++) ctx->info_ref_hist[t] = 0;
+    ctx->info_fp64_rebuilt = 0;
 
     BuildArgs a{};
     a.xy = ctx->node_xy.as<double>();
@@ -477,6 +484,10 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         m.num_sms = ctx->num_sms;
         m.tc = base_prec == LABFM_PREC_MIXED_TC;
         m.tc_timeout = dmisc + 30;
+        m.fb_count = dmisc + 31;
+        m.ref_hist = dmisc + 32;
+        LABFM_CUDA_TRY(ctx, ctx->mfallback.reserve(sizeof(int32_t) * (n > 0 ? n : 1)));
+        m.fb_list = ctx->mfallback.as<int32_t>();
         for (int t = 0; t < n_ops * PMAX; t++) m.C[t] = Cin[t];
         for (int d = 0; d < n_ops; d++) {
             int l = 0;
@@ -493,7 +504,9 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         }
         m.list = list;
         m.n_list = n_list;
-        m.nref = precision_nref(precision, k);
+        bool adaptive = false;
+        m.nref = precision_nref(precision, adaptive);
+        m.adaptive = adaptive ? 1 : 0;
         // per-node matrices of one batch: at most 2^18 nodes (4.2 GB at k = 8)
         m.batch_nodes = std::max<int64_t>(1, std::min<int64_t>(n_list, (int64_t)1 << 18));
         cudaError_t e = ctx->mscratch.reserve(mixed_scratch_bytes_per_node(k) * (size_t)m.batch_nodes + 256);
@@ -548,9 +561,23 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
             }
         }
     }
-    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, 32 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, NMISC * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hs[30]) return fail(ctx, LABFM_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+    if (mixed && hs[31]) {
+        // nodes whose refinement diverged (the double-float inverse too inaccurate for the
+        // iteration to contract): the FP64 build writes their weights and statuses
+        const int64_t nfb = (int64_t)hs[31];
+        ctx->info_fp64_rebuilt = nfb;
+        a.list = ctx->mfallback.as<int32_t>();
+        a.n_list = nfb;
+        if (!order) LABFM_CUDA_TRY(ctx, launch_order(uniform_order, a, ctx->num_sms, s));
+        else LABFM_CUDA_TRY(ctx, launch_all_orders(a, order, ctx->num_sms, s));
+        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
+    if (mixed)
+        for (int t = 0; t < 8; t++) ctx->info_ref_hist[t] = (int64_t)hs[32 + t];
     int64_t nbad = (int64_t)hs[0];
     if (n_bad_out) *n_bad_out = nbad;
     if (nbad) return fail(ctx, LABFM_ERR_SINGULAR, std::to_string(nbad) + " node(s) flagged");

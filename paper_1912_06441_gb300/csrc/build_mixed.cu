@@ -7,10 +7,12 @@
 //      M = sum_j X_j (outer) W_j in double-float register tiles  -> M (global).
 //   B  k_mixed_invert (two threads per row, the matrix in shared memory): Gauss-Jordan
 //      inversion of M with partial pivoting (interchanges undone on the columns) -> M^-1.
-//   C  k_mixed_weights (CTA per node): Psi~ = M^-1 C~, w~ = W . Psi~, then `nref` refinement
-//      steps on the residual of the moment conditions of Sec. 3.1
+//   C  k_mixed_weights (CTA per node): Psi~ = M^-1 C~, w~ = W . Psi~, then refinement steps on
+//      the residual of the moment conditions of Sec. 3.1
 //          r = C~ - sum_j X_j w~_j   (FP64)        w~ <- w~ + W . (M^-1 r)
-//      and the physical weights w = h^-l_d w~.
+//      and the physical weights w = h^-l_d w~.  A fixed number of steps when the caller forces
+//      one; by default each node refines until its weights stop changing (adaptive: see
+//      refine_decision), and a node whose corrections grow instead is handed to the FP64 build.
 // Targets are scaled per operator d by h^(l_d - |alpha|), l_d = highest degree with a non-zero
 // entry of C^d, so that Psi~ stays within float range; w = h^-l_d w~ is the same similarity
 // transform as the FP64 build (exact in exact arithmetic).
@@ -25,6 +27,7 @@ namespace labfm {
 namespace {
 
 constexpr int MIX_THREADS = 256;
+static_assert(MIX_THREADS / 32 >= MAX_OPS, "a warp per operator in the weights kernel's sums");
 constexpr int PARTS = 3;            // threads per neighbour in the X/W evaluation
 constexpr int NREC = 8;             // per-neighbour record: q, 1/q, u, v, W0', W0'', W0'''
 
@@ -40,10 +43,11 @@ template <int K> struct MCfg {
     static_assert(RG * CG <= MIX_THREADS, "assembly tile grid exceeds the CTA");
     // kernel A: Xf, Wf (df) + neighbour records
     static constexpr size_t smemA = 8 * ((size_t)2 * NB * LDX + (size_t)NB * NREC);
-    // kernel C: Xd (double), Wf (df), records, Psi/rhs (df) and residual (double); M^-1 is read
-    // from global memory (through L1), which keeps three CTAs per SM
-    static constexpr size_t smemC =
-        8 * ((size_t)2 * NB * LDX + (size_t)NB * NREC + (size_t)2 * P * MAX_OPS + (size_t)NB * MAX_OPS);
+    // kernel C: Xd (double), Wf (df), records, Psi/rhs (df), the chunk's w~ (double) and its
+    // last corrections (float); M^-1 is read from global memory (through L1), which keeps three
+    // CTAs per SM
+    static constexpr size_t smemC = 8 * ((size_t)2 * NB * LDX + (size_t)NB * NREC + (size_t)2 * P * MAX_OPS +
+                                         (size_t)NB * MAX_OPS) + 4 * (size_t)NB * MAX_OPS;
 };
 
 struct DfTables {
@@ -84,7 +88,11 @@ struct MixedArgs {
     double L[2], halfL[2];
     int rbf;
     int n_ops;
-    int nref;
+    int nref;           // refinement steps: exactly this many, or at most this many when adaptive
+    int adaptive;       // 1: per-node stopping rule (refine_decision)
+    int32_t *fb_list;   // nodes whose refinement diverged, for the FP64 build (adaptive only)
+    unsigned long long *fb_count;
+    unsigned long long *ref_hist;  // [NREF_MAX + 1] nodes by number of refinement steps taken
     void *w;            // [nnz][n_ops] output
     int wdtype;
     double *wt;         // [nnz][n_ops] scratch: unscaled weights w~ in double
@@ -893,7 +901,42 @@ __global__ void __launch_bounds__(InvCfg<p_of_k(K)>::NT) k_mixed_invert(MixedArg
 
 // ------------------------------------------------------------------------------------------
 // C: Psi~ = M^-1 C~, w~ = W . Psi~, FP64 residual refinement, physical weights
+//
+// Adaptive refinement.  Step t changes the weights by dw_t (t = 0: the first solve, dw_0 = w_0);
+// eta_t = max_d ||dw_t,d|| / ||w_t,d|| over the node's stencil (eta_0 = 1).  Refinement with an
+// approximate inverse contracts the error by a factor rho per step, and the correction dw_t is
+// close to the error before it, so rho ~ eta_t / eta_(t-1) and the error left after step t is
+// about eta_t^2 / eta_(t-1).  The node stops after step t >= 1 when
+//   - that estimate is below 2^-44 (~6e-14: within a few hundred ulps of double precision), or
+//   - eta_t > eta_(t-1) / 2: the corrections no longer shrink, because they are at the rounding
+//     level of the FP64 residual (the floor of the method on this stencil), or because the
+//     inverse is too inaccurate for the iteration to contract (cond(M) u_df >~ 1); in the latter
+//     case, recognised by eta_t > 1e-3, the node is rebuilt in FP64 (fb_list), or
+//   - t = NREF_MAX.
+// Most nodes stop after one step, with no residual evaluated after it.
 // ------------------------------------------------------------------------------------------
+constexpr int NREF_MAX = 6;
+constexpr float REF_EPS = 5.6843419e-14f;  // 2^-44
+constexpr float REF_DIVERGED = 1e-3f;
+
+// Thread 0: the decision after step `it` from the per-operator sums of dw^2 and w^2 in shared
+// memory.  Returns 1 to continue, 0 to stop, 2 to stop and rebuild the node in FP64.
+__device__ __forceinline__ int refine_decision(int it, int nmax, int n_ops, const float *dw2, const float *w2,
+                                               float eta_prev, float &eta)
+{
+    eta = 0.0f;
+    for (int d = 0; d < n_ops; d++)
+        if (w2[d] > 0.0f) eta = fmaxf(eta, sqrtf(dw2[d] / w2[d]));
+    if (it == 0) {
+        eta = 1.0f;
+        return nmax > 0 ? 1 : 0;
+    }
+    if (!(eta <= 1e30f)) return 2;  // not finite
+    if (eta > 0.5f * eta_prev) return eta > REF_DIVERGED ? 2 : 0;
+    if (eta * eta <= REF_EPS * eta_prev) return 0;
+    return it < nmax ? 1 : 0;
+}
+
 template <int K>
 __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
 {
@@ -906,9 +949,12 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
     df *Rhs = Nrec + NB * NREC;                              // [P][MAX_OPS] right-hand sides
     df *Psi = Rhs + P * MAX_OPS;                             // [P][MAX_OPS]
     double *Wt = reinterpret_cast<double *>(Psi + P * MAX_OPS);  // [NB][MAX_OPS] w~ of the chunk
+    float *Vt = reinterpret_cast<float *>(Wt + NB * MAX_OPS);    // [NB][MAX_OPS] the last correction of w~
     __shared__ double s_hneg[KMAX + 1], s_hpos[KMAX + 1];
     __shared__ double s_res[PMAX * MAX_OPS];
-    __shared__ int s_flag;
+    __shared__ float s_dw2[MAX_OPS], s_w2[MAX_OPS];  // per operator: sum of dw^2 and of w^2 over the stencil
+    __shared__ float s_eta;
+    __shared__ int s_flag, s_go;
     const int tid = threadIdx.x;
     const int n_ops = A.n_ops;
 
@@ -961,7 +1007,10 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
         if (nchunks == 1) stage_chunk<K>(A, rs, 0, ni, Xd, nullptr, Wf, Nrec);
         else __syncthreads();
 
-        for (int it = 0; it <= A.nref; it++) {
+        float eta_prev = 1.0f;
+        int go = 1;
+        int it = 0;
+        for (;; it++) {
             // Psi (or its correction) = M^-1 Rhs, thread per (m, d)
             for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
                 int m = t / n_ops, d = t % n_ops;
@@ -975,7 +1024,6 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
                 if (q < P) s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
                 Psi[m * MAX_OPS + d] = df_add(s0, s1);
             }
-            __syncthreads();
             // w~ (+)= W . Psi over the chunks; the residual r = C~ - sum_j X_j w~_j accumulates
             for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
                 int m = t / n_ops, d = t % n_ops;
@@ -983,6 +1031,11 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
                 double sc = l >= deg ? s_hpos[l - deg] : s_hneg[deg - l];
                 s_res[m * MAX_OPS + d] = A.C[d * PMAX + m] * sc;
             }
+            if (tid < MAX_OPS) {
+                s_dw2[tid] = 0.0f;
+                s_w2[tid] = 0.0f;
+            }
+            __syncthreads();
             for (int ch = 0; ch < nchunks; ch++) {
                 const int j0 = ch * NB, nj = min(NB, ni - j0);
                 if (nchunks > 1) stage_chunk<K>(A, rs, j0, nj, Xd, nullptr, Wf, Nrec);
@@ -1001,9 +1054,48 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
                     const double wv = it == 0 ? v : A.wt[idx] + v;
                     A.wt[idx] = wv;
                     Wt[j * MAX_OPS + d] = wv;
+                    Vt[j * MAX_OPS + d] = (float)v;
                 }
                 __syncthreads();
-                if (it < A.nref) {
+                if (A.adaptive) {
+                    // per operator (warp d): the chunk's sums of dw^2 and w^2, in float
+                    const int wp = tid >> 5, ln = tid & 31;
+                    if (wp < n_ops) {
+                        float a2 = 0.0f, b2 = 0.0f;
+                        for (int j = ln; j < nj; j += 32) {
+                            const float vf = Vt[j * MAX_OPS + wp], wf = (float)Wt[j * MAX_OPS + wp];
+                            a2 = fmaf(vf, vf, a2);
+                            b2 = fmaf(wf, wf, b2);
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                            b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+                        }
+                        if (ln == 0) {
+                            s_dw2[wp] += a2;
+                            s_w2[wp] += b2;
+                        }
+                    }
+                    __syncthreads();
+                }
+                // the residual of this pass is needed only if another step follows; with one
+                // chunk the adaptive decision is known here, before the residual is formed
+                bool res;
+                if (!A.adaptive) {
+                    res = it < A.nref;
+                } else if (nchunks == 1) {
+                    if (tid == 0) {
+                        float eta;
+                        s_go = refine_decision(it, A.nref, n_ops, s_dw2, s_w2, eta_prev, eta);
+                        s_eta = eta;
+                    }
+                    __syncthreads();
+                    res = s_go == 1;
+                } else {
+                    res = it < A.nref;
+                }
+                if (res) {
                     for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
                         int m = t / n_ops, d = t % n_ops;
                         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -1020,12 +1112,33 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
                 }
                 __syncthreads();
             }
-            if (it == A.nref) break;
+            if (A.adaptive) {
+                if (nchunks > 1) {
+                    if (tid == 0) {
+                        float eta;
+                        s_go = refine_decision(it, A.nref, n_ops, s_dw2, s_w2, eta_prev, eta);
+                        s_eta = eta;
+                    }
+                    __syncthreads();
+                }
+                go = s_go;
+                eta_prev = s_eta;
+                if (go != 1) break;
+            } else if (it == A.nref) {
+                break;
+            }
             for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
                 int m = t / n_ops, d = t % n_ops;
                 Rhs[m * MAX_OPS + d] = df_from_double(s_res[m * MAX_OPS + d]);
             }
             __syncthreads();
+        }
+        if (tid == 0 && A.ref_hist) atomicAdd(&A.ref_hist[min(it, NREF_MAX)], 1ull);
+        if (go == 2) {
+            // the corrections grew: the FP64 build redoes this node (weights and status)
+            if (tid == 0) A.fb_list[atomicAdd(A.fb_count, 1ull)] = (int32_t)i;
+            __syncthreads();
+            continue;
         }
 
         // physical weights w = h^-l_d w~
@@ -1130,6 +1243,10 @@ cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
     a.rbf = p.rbf;
     a.n_ops = p.n_ops;
     a.nref = p.nref;
+    a.adaptive = p.adaptive;
+    a.fb_list = p.fb_list;
+    a.fb_count = p.fb_count;
+    a.ref_hist = p.ref_hist;
     a.w = p.w;
     a.wdtype = p.wdtype;
     a.wt = p.wt;

@@ -70,6 +70,10 @@ struct labfm_ctx {
     labfm::DevBuf mscratch;  // scratch of the mixed-precision build: per-node matrices of one batch
     labfm::DevBuf mrecs;     // scratch of the mixed-precision build: per-entry preamble records
     labfm::DevBuf mwstore;   // scratch of the mixed-precision build: W of every entry (double-float)
+    labfm::DevBuf mfallback; // scratch of the mixed-precision build: nodes rebuilt in FP64
+    // statistics of the last labfm_build_weights (labfm_get_build_info)
+    int64_t info_ref_hist[8] = {0};
+    int64_t info_fp64_rebuilt = 0;
 
     // RK4
     labfm::DevBuf wcomb, rk_acc, rk_stage_a, rk_stage_b;
@@ -120,6 +124,10 @@ struct MixedArgsPublic {
     int periodic;
     double L[2], halfL[2];
     int rbf, n_ops, nref;
+    int adaptive;                   // 1: refine each node until it converges, at most nref steps
+    int32_t *fb_list;               // [n] nodes handed to the FP64 build (refinement diverged)
+    unsigned long long *fb_count;   // device counter of fb_list
+    unsigned long long *ref_hist;   // device [nref + 1]: nodes by refinement steps taken
     void *w;
     int wdtype;
     double *wt;

@@ -1,6 +1,6 @@
 """Shared helpers of the GPU parity tests: run the CUDA path through the C ABI, slice its CSR
 output, and compare against the CPU oracle with tolerances tied to the oracle's own FP64
-rounding floor (FP64 oracle vs long-double oracle on the same inputs)."""
+rounding floor (FP64 oracle vs binary128 oracle on the same inputs)."""
 import numpy as np
 
 import labfm_synth as S
@@ -11,6 +11,10 @@ HS = {1: 1.2, 2: 1.2, 3: 1.3, 4: 1.4, 5: 1.6, 6: 1.8, 7: 2.0, 8: 2.2}
 OPS = {1: ("dx", "dy"), 2: ("dx", "dy", "lap"), 3: ("dx", "dy", "lap"), 4: ("dx", "dy", "lap", "lap2"),
        5: ("dx", "dy", "lap", "lap2"), 6: ("dx", "dy", "lap", "lap3"), 7: ("dx", "dy", "lap", "lap3"),
        8: ("dx", "dy", "lap", "lap4")}
+
+# The reference the GPU and the FP64 oracle are measured against: the same oracle in IEEE
+# binary128 (113-bit significand), on every host.
+REF_PRECISION = "q"
 
 # Absolute floors of the weight/derivative tolerance (1e-11 relative, where FP64 allows it)
 TOL_FLOOR_MAX = 1e-11
@@ -74,12 +78,12 @@ def oracle_refs(ns, k, ops, q, rp_q, col_q, rbf="wendland_c2", order=None, abf_f
     else:
         kw["order"] = order
     r64 = oracle.build_weights(ns.xy, ns.h, ns.periodic, rp_q, col_q, C, **kw)
-    rld = oracle.build_weights(ns.xy, ns.h, ns.periodic, rp_q, col_q, C, precision="ld", **kw)
+    rld = oracle.build_weights(ns.xy, ns.h, ns.periodic, rp_q, col_q, C, precision=REF_PRECISION, **kw)
     return r64, rld
 
 
 def assert_weights_parity(w_gpu_q, r64, rld, rp_q, label=""):
-    """GPU weights vs the long-double oracle, bounded by the FP64 oracle's own error."""
+    """GPU weights vs the binary128 oracle, bounded by the FP64 oracle's own error."""
     ok = (r64["status"] == 0) & (rld["status"] == 0)
     e_gpu = node_rel_err(w_gpu_q, rld["w"], rp_q)[ok]
     e_64 = node_rel_err(r64["w"], rld["w"], rp_q)[ok]
