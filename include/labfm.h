@@ -167,8 +167,14 @@ labfm_status labfm_get_neighbours(labfm_ctx *ctx, const int64_t **row_ptr, const
  *                layout [nnz][n_ops] (entry e of the CSR, operator d at e*n_ops + d)
  *   node_status  device int32[n] receiving LABFM_NODE_* per node, or NULL
  *   n_bad_out    host, receives the number of flagged nodes (may be NULL)
- * With per-node orders the nodes are bucketed by order; the FP64 build then runs every order in
- * one persistent launch (highest order first), the mixed builds one launch per order.
+ * The FP64 kernel builds a node with a group of 64, 128 or 256 threads (several small-order nodes
+ * per CTA); the group size per order is chosen by timing the candidates once per (order, mean
+ * stencil size, n_ops) on up to 16,384 of the order's nodes (not while `stream` is being captured,
+ * nor below 4,096 nodes), and kept for the life of the context.  With per-node orders the nodes
+ * are bucketed by (order, stencil size) and the FP64-built orders run in one persistent launch,
+ * costliest nodes first.  The mixed builds build orders 1-4 with the FP64 kernel (small, well
+ * conditioned systems: faster there and exact to the FP64 floor) and each order from 5 up with
+ * the mixed kernels.
  * Flagged nodes get zero weights.  Returns LABFM_ERR_SINGULAR if any node was
  * flagged (the weights of all other nodes are valid), LABFM_ERR_STATE if no
  * stencils were built, LABFM_ERR_TIMEOUT if a bounded wait for the tensor cores
@@ -187,6 +193,9 @@ typedef struct {
     int64_t refine_steps[8];
     /* mixed builds: nodes whose refinement diverged and that the FP64 build redid */
     int64_t fp64_rebuilt;
+    /* per order k (index 1..8): threads that built one node in the FP64 kernel (64, 128: several
+     * nodes per CTA; 256: one), as the build autotuner chose them; 0 for orders not built there */
+    int32_t fp64_group_threads[LABFM_MAX_ORDER + 1];
 } labfm_build_info;
 
 /* Copy the statistics of the last weight build into *info.  LABFM_ERR_STATE before a build. */

@@ -2,13 +2,20 @@
 // M = sum_j X_j (outer) W_j (Eq. disc_form), Gaussian elimination with partial pivoting of
 // M Psi = C^d for all operators at once (Eq. lsys), and w_j^d = W_j . Psi^d (Eq. w_abf).
 //
-// One CTA per node (persistent over a node list).  Neighbour data are staged in shared
-// memory in chunks of NB neighbours: Xs[j][m], Ws[j][n] (row stride LDX, a multiple of 4 so
-// that a thread's 4 consecutive W values are one 32-byte load).  The p x p assembly is tiled
-// 2 x 4 per thread in registers across chunks.  The augmented matrix [M | Chat] (Chat_alpha =
-// C_alpha h^-|alpha|) is then eliminated in shared memory, one column per step, in the space of
-// the X staging (X is not read again), which keeps a CTA within a quarter of the SM's shared
-// memory: four CTAs per SM.
+// A group of G threads per node (persistent over a node list): the whole CTA (G = 256) from order 6
+// or 7 up, and two or four nodes per CTA below (G = 128 or 64, each group on its own named
+// barrier), where the p x p system is small and a whole CTA would spend its time in barrier
+// latency with most threads idle.  G per order is chosen by timing (build autotuner).
+// Neighbour data are staged in shared memory in chunks of NB neighbours: Xs[j][m], Ws[j][n]
+// (row stride LDX, a multiple of 4 so that a thread's 4 consecutive W values are one 32-byte
+// load).  The p x p assembly is tiled 2 x 4 per thread in registers across chunks.  The augmented
+// matrix [M | Chat] (Chat_alpha = C_alpha h^-|alpha|) is then eliminated in shared memory, one
+// column per step, in the space of the X staging (X is not read again), which keeps a CTA within
+// a quarter of the SM's shared memory: four CTAs per SM.
+//
+// Per-node orders (walls and variable resolution, Sec. 4.1) run in one persistent launch over
+// work items: nodes bucketed by (order, stencil size), taken largest first, an item being one
+// node of a CTA-wide order or 256 / G nodes of a grouped one.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -20,18 +27,46 @@ namespace {
 
 constexpr int BUILD_THREADS = 256;
 
-template <int K> struct Cfg {
+// Shared memory of one CTA beyond the X/W staging: the scalars and small arrays of the node being
+// built, carved from the dynamic allocation (so that a kernel holding several orders allocates
+// them once, not once per order).
+struct NodeShared {
+    double psi[PMAX * MAX_OPS];  // Psi^d, kept while X and W are staged again
+    double invpiv[PMAX];         // 1 / pivot of each column, reused by the back substitution
+    double hpow[KMAX + 1];       // h^-n
+    double inv;
+    int piv;
+    int flag;  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
+};
+
+// The CTA's dynamic shared memory: that of one order-8 node (72-neighbour chunks), so that four
+// CTAs fit an SM; a CTA of NG = 256 / G groups gives each group a 1/NG share.
+constexpr size_t SMEM_CTA = (sizeof(double) * ((size_t)2 * 72 * 44) + sizeof(NodeShared) + 15) / 16 * 16;
+
+template <int K, int G> struct Cfg {
     static constexpr int P = p_of_k(K);
     static constexpr int LDX = (P + 3) / 4 * 4;
-    static constexpr int NB = K >= 7 ? 72 : 64;
+    static constexpr int NG = BUILD_THREADS / G;  // nodes per CTA
+    static_assert(G % 32 == 0 && BUILD_THREADS % G == 0, "groups of whole warps");
+    // neighbours per staged chunk: what the group's share of the CTA's shared memory holds, <= 72
+    static constexpr size_t GROUP_SMEM = (SMEM_CTA / NG) / 16 * 16;
+    static constexpr int NB_FIT = (int)((GROUP_SMEM - sizeof(NodeShared)) / (sizeof(double) * 2 * LDX));
+    static constexpr int NB = NB_FIT < 72 ? NB_FIT : 72;
     static constexpr int TM = 2, TN = 4;
     static constexpr int RG = (P + TM - 1) / TM, CG = (P + TN - 1) / TN;
-    static_assert(RG * CG <= BUILD_THREADS, "assembly tile grid exceeds the CTA");
+    static_assert(RG * CG <= G, "assembly tile grid exceeds the group");
     static constexpr int LDA = P + MAX_OPS + 1;  // augmented row stride (odd: fewer bank conflicts)
     // the augmented matrix reuses the X staging (X is not read after the assembly)
     static_assert((size_t)P * LDA <= (size_t)NB * LDX, "augmented matrix fits the X staging");
     static constexpr size_t smem_bytes = sizeof(double) * ((size_t)2 * NB * LDX);
+    static_assert(smem_bytes + sizeof(NodeShared) <= GROUP_SMEM, "group staging fits its share");
 };
+
+// group sizes a given order may run with (the assembly tile grid must fit the group)
+__host__ __device__ constexpr bool group_ok(int K, int G)
+{
+    return G == 256 || (G == 128 && K <= 6) || (G == 64 && K <= 5);
+}
 
 struct BuildArgs {
     int64_t n_list;           // nodes in this launch
@@ -51,31 +86,28 @@ struct BuildArgs {
     double C[MAX_OPS * PMAX];  // target vectors, row d = C^d (physical units)
 };
 
-// Shared memory of one CTA beyond the X/W staging: the scalars and small arrays of the node being
-// built, carved from the dynamic allocation (so that a kernel holding several orders allocates
-// them once, not once per order).
-struct NodeShared {
-    double psi[PMAX * MAX_OPS];  // Psi^d, kept while X and W are staged again
-    double invpiv[PMAX];         // 1 / pivot of each column, reused by the back substitution
-    double hpow[KMAX + 1];       // h^-n
-    double inv;
-    int piv;
-    int flag;  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
-};
+// Named barrier of group g of G threads: 1..2 for G = 128, 3..6 for G = 64 (an id is never used
+// with two thread counts); the CTA-wide group uses the CTA barrier.
+template <int G> __device__ __forceinline__ int group_bar(int g) { return (G == 128 ? 1 : 3) + g; }
 
-template <int K> constexpr size_t node_smem_bytes() { return Cfg<K>::smem_bytes + sizeof(NodeShared); }
-constexpr size_t max_node_smem_bytes()
+// Barrier of one group: the CTA barrier for a CTA-wide group, named barrier `bar` of G threads
+// otherwise.
+template <int G> __device__ __forceinline__ void gsync(int bar)
 {
-    return std::max({node_smem_bytes<1>(), node_smem_bytes<2>(), node_smem_bytes<3>(), node_smem_bytes<4>(),
-                     node_smem_bytes<5>(), node_smem_bytes<6>(), node_smem_bytes<7>(), node_smem_bytes<8>()});
+    if constexpr (G == BUILD_THREADS) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G) : "memory");
+    }
 }
 
-// The whole build of node i at order K by the CTA: stage X and W, assemble M, eliminate
-// [M | Chat], weights.  Ends synchronised (the shared memory is reused by the next node).
-template <int K>
-__device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double *smem)
+// The whole build of node i at order K by a group of G threads (group-local thread index `tid`,
+// barrier `bar`): stage X and W, assemble M, eliminate [M | Chat], weights.  Ends synchronised
+// (the group's shared memory is reused by its next node).
+template <int K, int G>
+__device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double *smem, int tid, int bar)
 {
-    using C = Cfg<K>;
+    using C = Cfg<K, G>;
     constexpr int P = C::P, LDX = C::LDX, NB = C::NB, LDA = C::LDA, TM = C::TM, TN = C::TN;
     double *Xs = smem;                 // [NB][LDX]
     double *Ws = Xs + NB * LDX;        // [NB][LDX]
@@ -85,7 +117,6 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
     int &s_piv = sh.piv, &s_flag = sh.flag;
     double &s_inv = sh.inv;
 
-    const int tid = threadIdx.x;
     const int n_ops = A.n_ops;
     const int W_ = P + n_ops;  // used columns of the augmented matrix
     const int rg = tid / C::CG, cg = tid % C::CG;
@@ -95,7 +126,7 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
         const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
         const int ni = (int)(re - rs);
         if (ni < P) {
-            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += BUILD_THREADS) {
+            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += G) {
                 if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
                 else ((float *)A.w)[rs * n_ops + t] = 0.0f;
             }
@@ -125,7 +156,7 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
         for (int ch = 0; ch < nchunks; ch++) {
             const int j0 = ch * NB;
             const int nj = min(NB, ni - j0);
-            for (int t = tid; t < nj; t += BUILD_THREADS) {
+            for (int t = tid; t < nj; t += G) {
                 int j = A.col[rs + j0 + t];
                 double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
                 if (A.periodic) {
@@ -139,7 +170,7 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
 #pragma unroll
                 for (int e = P; e < LDX; e++) X[e] = W[e] = 0.0;
             }
-            __syncthreads();
+            gsync<G>(bar);
             if (tile_active) {
                 for (int j = 0; j < nj; j++) {
                     const double *X = Xs + j * LDX + rg * TM;
@@ -159,11 +190,11 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                         for (int b = 0; b < TN; b++) acc[a][b] = fma(xv[a], wv[b], acc[a][b]);
                 }
             }
-            if (ch + 1 < nchunks) __syncthreads();
+            if (ch + 1 < nchunks) gsync<G>(bar);
         }
         // M into the augmented matrix, scaled targets into its right-hand columns
         if (tid == 0) s_flag = 0;
-        __syncthreads();
+        gsync<G>(bar);
         if (tile_active) {
             bool finite = true;
 #pragma unroll
@@ -179,11 +210,11 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
             // a non-finite entry of M (a neighbour on top of node i: singular ABFs)
             if (!finite) atomicOr(&s_flag, 4);
         }
-        for (int t = tid; t < P * n_ops; t += BUILD_THREADS) {
+        for (int t = tid; t < P * n_ops; t += G) {
             int m = t / n_ops, d = t % n_ops;
             Am[m * LDA + P + d] = A.C[d * PMAX + m] * s_hpow[elem_degree(m)];
         }
-        __syncthreads();
+        gsync<G>(bar);
         const bool bad_m = (s_flag & 4) != 0;
 
         // Gaussian elimination with partial pivoting (first largest |pivot| wins)
@@ -219,50 +250,50 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                     s_invpiv[c] = s_inv;
                 }
             }
-            __syncthreads();
+            gsync<G>(bar);
             const int pr = s_piv;
             if (pr != c) {
-                for (int t = c + tid; t < W_; t += BUILD_THREADS) {
+                for (int t = c + tid; t < W_; t += G) {
                     double a = Am[c * LDA + t];
                     Am[c * LDA + t] = Am[pr * LDA + t];
                     Am[pr * LDA + t] = a;
                 }
-                __syncthreads();
+                gsync<G>(bar);
             }
             const double inv = s_inv;
-            for (int r = c + 1 + tid; r < P; r += BUILD_THREADS) Am[r * LDA + c] *= inv;
-            __syncthreads();
+            for (int r = c + 1 + tid; r < P; r += G) Am[r * LDA + c] *= inv;
+            gsync<G>(bar);
             const int nr = P - c - 1, nc = W_ - c - 1;
-            for (int t = tid; t < nr * nc; t += BUILD_THREADS) {
+            for (int t = tid; t < nr * nc; t += G) {
                 int r = c + 1 + t / nc, q = c + 1 + t % nc;
                 Am[r * LDA + q] = fma(-Am[r * LDA + c], Am[c * LDA + q], Am[r * LDA + q]);
             }
-            __syncthreads();
+            gsync<G>(bar);
         }
         // back substitution on the n_ops right-hand sides
         for (int c = P - 1; c >= 0 && !bad_m; c--) {
             if (tid < n_ops) Am[c * LDA + P + tid] *= s_invpiv[c];
-            __syncthreads();
-            for (int t = tid; t < c * n_ops; t += BUILD_THREADS) {
+            gsync<G>(bar);
+            for (int t = tid; t < c * n_ops; t += G) {
                 int r = t / n_ops, d = t % n_ops;
                 Am[r * LDA + P + d] = fma(-Am[r * LDA + c], Am[c * LDA + P + d], Am[r * LDA + P + d]);
             }
-            __syncthreads();
+            gsync<G>(bar);
         }
         const bool singular = (s_flag & 5) != 0;  // no weights from a failed elimination
-        for (int t = tid; t < P * n_ops; t += BUILD_THREADS) {
+        for (int t = tid; t < P * n_ops; t += G) {
             const int m = t / n_ops, d = t - m * n_ops;
             s_psi[m * MAX_OPS + d] = Am[m * LDA + P + d];
         }
-        __syncthreads();
+        gsync<G>(bar);
 
         // weights w_j^d = W_j . Psi^d
         for (int ch = 0; ch < nchunks; ch++) {
             const int j0 = ch * NB;
             const int nj = min(NB, ni - j0);
             if (nchunks > 1) {  // the staged W of earlier chunks were overwritten: recompute
-                __syncthreads();
-                for (int t = tid; t < nj; t += BUILD_THREADS) {
+                gsync<G>(bar);
+                for (int t = tid; t < nj; t += G) {
                     int j = A.col[rs + j0 + t];
                     double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
                     if (A.periodic) {
@@ -273,9 +304,9 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                     }
                     eval_xw<K>(dx * ihi, dy * ihi, A.rbf, Xs + t * LDX, Ws + t * LDX);
                 }
-                __syncthreads();
+                gsync<G>(bar);
             }
-            for (int t = tid; t < nj * n_ops; t += BUILD_THREADS) {
+            for (int t = tid; t < nj * n_ops; t += G) {
                 int j = t / n_ops, d = t % n_ops;
                 double s = 0.0;
                 if (!singular) {
@@ -292,10 +323,10 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                 else ((float *)A.w)[idx] = (float)s;
             }
         }
-        __syncthreads();
+        gsync<G>(bar);
         const int flag = s_flag;
         if (flag & 2) {  // a weight was not finite: the whole node is zeroed
-            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += BUILD_THREADS) {
+            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += G) {
                 if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
                 else ((float *)A.w)[rs * n_ops + t] = 0.0f;
             }
@@ -308,109 +339,170 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
             if (A.node_status) A.node_status[i] = st;
             if (st != LABFM_NODE_OK) atomicAdd(A.n_bad, 1ull);
         }
-        __syncthreads();  // shared state is reused by the next node
+        gsync<G>(bar);  // shared state is reused by the next node
     }
 }
 
-// One order for all listed nodes (persistent over the list).
-template <int K>
+// One order for all listed nodes (persistent over the list; 256 / G nodes per CTA at a time).
+template <int K, int G>
 __global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64(BuildArgs A)
 {
+    using C = Cfg<K, G>;
     extern __shared__ __align__(16) double smem[];
-    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x)
-        build_node<K>(A, A.list ? (int64_t)A.list[li] : li, smem);
+    const int g = threadIdx.x / G;
+    double *gs = smem + g * (C::GROUP_SMEM / sizeof(double));
+    for (int64_t li = (int64_t)blockIdx.x * C::NG + g; li < A.n_list; li += (int64_t)gridDim.x * C::NG)
+        build_node<K, G>(A, A.list ? (int64_t)A.list[li] : li, gs, threadIdx.x % G, group_bar<G>(g));
 }
 
-// Every order in one persistent launch (per-node order, Sec. 4.1 walls and variable resolution):
-// the list holds the nodes by ascending order, and CTAs take them from the end, so that the
-// costliest nodes go first and the cheap ones fill the tail.
-__global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64_orders(BuildArgs A, const int8_t *__restrict__ order)
+// Work items of the one-launch build over per-node orders: orders from KMAX down; order k has
+// n_items[k] items starting at item0[k], item t covering the list entries base[k] + (t -
+// item0[k]) NG_k ... of that order, NG_k = 256 / group[k] (the last item may be short).
+struct OrderItems {
+    int group[KMAX + 1];
+    int64_t base[KMAX + 1], cnt[KMAX + 1], item0[KMAX + 1], n_items[KMAX + 1];
+    int64_t total;
+};
+
+template <int K, int G>
+__device__ __forceinline__ void run_item(const BuildArgs &A, const OrderItems &I, int64_t t, double *smem)
+{
+    if constexpr (group_ok(K, G)) {
+        using C = Cfg<K, G>;
+        const int g = threadIdx.x / G;
+        const int64_t e = (t - I.item0[K]) * C::NG + g;  // entry within order K
+        if (e < I.cnt[K])
+            build_node<K, G>(A, (int64_t)A.list[I.base[K] + e], smem + g * (C::GROUP_SMEM / sizeof(double)),
+                             threadIdx.x % G, group_bar<G>(g));
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void run_item_k(const BuildArgs &A, const OrderItems &I, int64_t t, double *smem)
+{
+    switch (I.group[K]) {
+    case 64: run_item<K, 64>(A, I, t, smem); break;
+    case 128: run_item<K, 128>(A, I, t, smem); break;
+    default: run_item<K, 256>(A, I, t, smem); break;
+    }
+}
+
+// Every order in one persistent launch: CTAs take the items in order (the costliest first, the
+// list being bucketed by descending (order, stencil size)), so that the cheap ones fill the tail.
+// The groups of a CTA run their items independently; where the group size changes from one item
+// to the next, the whole CTA meets first, so that no group starts on shared memory (or a named
+// barrier) that a group of the previous size still uses.  The item sequence, hence that barrier,
+// is the same for every thread of the CTA.
+__global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64_items(BuildArgs A, OrderItems I)
 {
     extern __shared__ __align__(16) double smem[];
-    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
-        const int64_t i = A.list[A.n_list - 1 - li];
-        switch (order[i]) {
-        case 1: build_node<1>(A, i, smem); break;
-        case 2: build_node<2>(A, i, smem); break;
-        case 3: build_node<3>(A, i, smem); break;
-        case 4: build_node<4>(A, i, smem); break;
-        case 5: build_node<5>(A, i, smem); break;
-        case 6: build_node<6>(A, i, smem); break;
-        case 7: build_node<7>(A, i, smem); break;
-        default: build_node<8>(A, i, smem); break;
+    int prev_group = 0;
+    for (int64_t t = blockIdx.x; t < I.total; t += gridDim.x) {
+        int k = KMAX;
+        while (k > 1 && t >= I.item0[k] + I.n_items[k]) k--;
+        if (I.group[k] != prev_group) {
+            if (prev_group != 0) __syncthreads();
+            prev_group = I.group[k];
+        }
+        switch (k) {
+        case 1: run_item_k<1>(A, I, t, smem); break;
+        case 2: run_item_k<2>(A, I, t, smem); break;
+        case 3: run_item_k<3>(A, I, t, smem); break;
+        case 4: run_item_k<4>(A, I, t, smem); break;
+        case 5: run_item_k<5>(A, I, t, smem); break;
+        case 6: run_item_k<6>(A, I, t, smem); break;
+        case 7: run_item_k<7>(A, I, t, smem); break;
+        default: run_item_k<8>(A, I, t, smem); break;
         }
     }
 }
 
-template <int K>
-static cudaError_t launch_k(const BuildArgs &a, int num_sms, cudaStream_t s)
+// Listed nodes of any orders, one per CTA (the few nodes a mixed build hands back to FP64).
+__global__ void __launch_bounds__(BUILD_THREADS, 4) k_build_fp64_any(BuildArgs A, const int8_t *__restrict__ order,
+                                                                    int uniform_order)
 {
-    using C = Cfg<K>;
-    constexpr size_t smem = node_smem_bytes<K>();
-    cudaError_t e = cudaFuncSetAttribute(k_build_fp64<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_fp64<K>, BUILD_THREADS, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = std::min<int64_t>(a.n_list, (int64_t)num_sms * per_sm);
-    if (grid < 1) return cudaSuccess;
-    k_build_fp64<K><<<(unsigned)grid, BUILD_THREADS, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-static cudaError_t launch_all_orders(const BuildArgs &a, const int8_t *order, int num_sms, cudaStream_t s)
-{
-    constexpr size_t smem = max_node_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_build_fp64_orders, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_fp64_orders, BUILD_THREADS, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = std::min<int64_t>(a.n_list, (int64_t)num_sms * per_sm);
-    if (grid < 1) return cudaSuccess;
-    k_build_fp64_orders<<<(unsigned)grid, BUILD_THREADS, smem, s>>>(a, order);
-    return cudaGetLastError();
-}
-
-static cudaError_t launch_order(int k, const BuildArgs &a, int num_sms, cudaStream_t s)
-{
-    switch (k) {
-    case 1: return launch_k<1>(a, num_sms, s);
-    case 2: return launch_k<2>(a, num_sms, s);
-    case 3: return launch_k<3>(a, num_sms, s);
-    case 4: return launch_k<4>(a, num_sms, s);
-    case 5: return launch_k<5>(a, num_sms, s);
-    case 6: return launch_k<6>(a, num_sms, s);
-    case 7: return launch_k<7>(a, num_sms, s);
-    default: return launch_k<8>(a, num_sms, s);
+    extern __shared__ __align__(16) double smem[];
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
+        const int64_t i = A.list[li];
+        switch (order ? order[i] : uniform_order) {
+        case 1: build_node<1, 256>(A, i, smem, threadIdx.x, 0); break;
+        case 2: build_node<2, 256>(A, i, smem, threadIdx.x, 0); break;
+        case 3: build_node<3, 256>(A, i, smem, threadIdx.x, 0); break;
+        case 4: build_node<4, 256>(A, i, smem, threadIdx.x, 0); break;
+        case 5: build_node<5, 256>(A, i, smem, threadIdx.x, 0); break;
+        case 6: build_node<6, 256>(A, i, smem, threadIdx.x, 0); break;
+        case 7: build_node<7, 256>(A, i, smem, threadIdx.x, 0); break;
+        default: build_node<8, 256>(A, i, smem, threadIdx.x, 0); break;
+        }
     }
 }
 
-// Bucket nodes by order: counts per order, then a stable list of node ids per order.
-__global__ void k_order_count(int64_t n, const int8_t *__restrict__ order, unsigned long long *__restrict__ cnt,
-                              unsigned long long *__restrict__ bad)
+template <class KernelT, class... Args>
+static cudaError_t launch_persistent_build(KernelT kern, int64_t units, int num_sms, cudaStream_t s, Args... args)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CTA);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BUILD_THREADS, SMEM_CTA);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::min<int64_t>(units, (int64_t)num_sms * per_sm);
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, BUILD_THREADS, SMEM_CTA, s>>>(args...);
+    return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t launch_k(const BuildArgs &a, int G, int num_sms, cudaStream_t s)
+{
+    if (G == 64 && group_ok(K, 64))
+        return launch_persistent_build(k_build_fp64<K, group_ok(K, 64) ? 64 : 256>, (a.n_list + 3) / 4, num_sms, s, a);
+    if (G == 128 && group_ok(K, 128))
+        return launch_persistent_build(k_build_fp64<K, group_ok(K, 128) ? 128 : 256>, (a.n_list + 1) / 2, num_sms, s,
+                                       a);
+    return launch_persistent_build(k_build_fp64<K, 256>, a.n_list, num_sms, s, a);
+}
+
+static cudaError_t launch_order(int k, int G, const BuildArgs &a, int num_sms, cudaStream_t s)
+{
+    switch (k) {
+    case 1: return launch_k<1>(a, G, num_sms, s);
+    case 2: return launch_k<2>(a, G, num_sms, s);
+    case 3: return launch_k<3>(a, G, num_sms, s);
+    case 4: return launch_k<4>(a, G, num_sms, s);
+    case 5: return launch_k<5>(a, G, num_sms, s);
+    case 6: return launch_k<6>(a, G, num_sms, s);
+    case 7: return launch_k<7>(a, G, num_sms, s);
+    default: return launch_k<8>(a, G, num_sms, s);
+    }
+}
+
+// Bucketing by (order, stencil size), both descending: key = (KMAX - k) 256 + 255 - min(N_i, 255).
+constexpr int NBUCKET = (KMAX + 1) * 256;
+__device__ __forceinline__ int bucket_key(int k, int64_t deg) { return (KMAX - k) * 256 + 255 - (int)min(deg, (int64_t)255); }
+
+__global__ void k_bucket_count(int64_t n, const int8_t *__restrict__ order, const int64_t *__restrict__ row_ptr,
+                               unsigned int *__restrict__ hist, unsigned long long *__restrict__ bad)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int k = order[i];
+    const int k = order[i];
     if (k < 1 || k > KMAX) {
         atomicAdd(bad, 1ull);
         return;
     }
-    atomicAdd(&cnt[k], 1ull);
+    atomicAdd(&hist[bucket_key(k, row_ptr[i + 1] - row_ptr[i])], 1u);
 }
 
-__global__ void k_order_scatter(int64_t n, const int8_t *__restrict__ order, const unsigned long long *__restrict__ base,
-                                unsigned long long *__restrict__ cursor, int32_t *__restrict__ list)
+// cursor[b] starts at the first list position of bucket b
+__global__ void k_bucket_scatter(int64_t n, const int8_t *__restrict__ order, const int64_t *__restrict__ row_ptr,
+                                 unsigned int *__restrict__ cursor, int32_t *__restrict__ list)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int k = order[i];
+    const int k = order[i];
     if (k < 1 || k > KMAX) return;
-    unsigned long long pos = base[k] + atomicAdd(&cursor[k], 1ull);
-    list[pos] = (int32_t)i;
+    list[atomicAdd(&cursor[bucket_key(k, row_ptr[i + 1] - row_ptr[i])], 1u)] = (int32_t)i;
 }
 
 }  // namespace
@@ -435,14 +527,17 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
     size_t wbytes = (size_t)ctx->nnz * n_ops * (weight_dtype == LABFM_F64 ? 8 : 4);
     LABFM_CUDA_TRY(ctx, ctx->w.reserve(wbytes > 0 ? wbytes : 8));
     if (mixed) LABFM_CUDA_TRY(ctx, ctx->wtilde.reserve((size_t)ctx->nnz * n_ops * 8 + 8));
-    LABFM_CUDA_TRY(ctx, ctx->misc.reserve(4096));
-    unsigned long long *dmisc = ctx->misc.as<unsigned long long>();
-    // misc layout: [0] bad nodes, [1] bad orders, [2..10] order counts, [11..19] bases, [20..28] cursors,
-    // [30] tensor-core waits that gave up, [31] nodes handed to the FP64 build, [32..39] nodes by
-    // refinement steps
+    // misc layout: [0] bad nodes, [1] bad orders, [30] tensor-core waits that gave up, [31] nodes
+    // handed to the FP64 build, [32..39] nodes by refinement steps; from byte 1024 the bucket
+    // histogram, from byte 1024 + 4 NBUCKET the bucket cursors
     constexpr int NMISC = 40;
+    LABFM_CUDA_TRY(ctx, ctx->misc.reserve(1024 + 8 * (size_t)NBUCKET));
+    unsigned long long *dmisc = ctx->misc.as<unsigned long long>();
+    unsigned int *d_hist = reinterpret_cast<unsigned int *>(ctx->misc.as<char>() + 1024);
+    unsigned int *d_cursor = d_hist + NBUCKET;
     LABFM_CUDA_TRY(ctx, cudaMemsetAsync(dmisc, 0, NMISC * sizeof(unsigned long long), s));
     for (int t = 0; t < 8; t++) ctx->info_ref_hist[t] = 0;
+    for (int t = 0; t <= KMAX; t++) ctx->info_group[t] = 0;
     ctx->info_fp64_rebuilt = 0;
 
     BuildArgs a{};
@@ -496,12 +591,63 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
             m.lmax[d] = l;
         }
     }
-    auto launch = [&](int k, const int32_t *list, int64_t n_list) -> cudaError_t {
-        if (!mixed) {
-            a.list = list;
-            a.n_list = n_list;
-            return launch_order(k, a, ctx->num_sms, s);
+    // Orders that the FP64 kernel builds: all of them for LABFM_PREC_FP64; for the mixed builds the
+    // orders below MIXED_MIN_ORDER, whose p x p systems (p <= 14) are small and well conditioned:
+    // there the cost is latency, which the grouped FP64 kernel hides better than the four-kernel
+    // mixed pipeline, and FP64 arithmetic is accurate to the floor.
+    constexpr int MIXED_MIN_ORDER = 5;
+    auto fp64_route = [&](int k) { return !mixed || k < MIXED_MIN_ORDER; };
+
+    // Group size of the FP64 kernel per order: timed once per (order, mean stencil size, n_ops)
+    // on up to 16,384 of the order's real nodes (the autotuner of the build), kept in the
+    // context's table.  Not while the caller's stream is being captured, nor below 4,096 nodes.
+    auto group_for = [&](int k, const int32_t *list, int64_t cnt, double deg, int &G) -> cudaError_t {
+        G = k <= 5 ? 64 : 256;
+        const uint64_t dkey = (uint64_t)std::min(deg + 0.5, 65535.0);
+        const uint64_t key = (dkey << 40) | ((uint64_t)k << 32) | (5ull << 24) | ((uint64_t)n_ops << 16);
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) {
+            G = (int)it->second;
+            return cudaSuccess;
         }
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(s, &cap);
+        if (e != cudaSuccess) return e;
+        if (cap != cudaStreamCaptureStatusNone) return cudaSuccess;
+        if (cnt >= 4096) {
+            const int cand[3] = {64, 128, 256};
+            float best = 1e30f;
+            cudaEvent_t e0, e1;
+            if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+            if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                return e;
+            }
+            BuildArgs t = a;
+            t.list = list;
+            t.n_list = std::min<int64_t>(cnt, 16384);
+            for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+                if (!group_ok(k, cand[c])) continue;
+                e = launch_order(k, cand[c], t, ctx->num_sms, s);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = launch_order(k, cand[c], t, ctx->num_sms, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && ms < best) {
+                    best = ms;
+                    G = cand[c];
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (e != cudaSuccess) return e;
+        }
+        ctx->tuned[key] = (uint32_t)G;
+        return cudaSuccess;
+    };
+    auto launch_mixed = [&](int k, const int32_t *list, int64_t n_list) -> cudaError_t {
         m.list = list;
         m.n_list = n_list;
         bool adaptive = false;
@@ -528,38 +674,74 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
 
     unsigned long long *hs = (unsigned long long *)ctx->host_small;
     if (!order) {
-        LABFM_CUDA_TRY(ctx, launch(uniform_order, nullptr, n));
+        const int k = uniform_order;
+        if (fp64_route(k)) {
+            int G = 256;
+            LABFM_CUDA_TRY(ctx, group_for(k, nullptr, n, n > 0 ? (double)ctx->nnz / (double)n : 0.0, G));
+            ctx->info_group[k] = G;
+            LABFM_CUDA_TRY(ctx, cudaMemsetAsync(dmisc, 0, sizeof(unsigned long long), s));  // the timing runs' flags
+            a.list = nullptr;
+            a.n_list = n;
+            LABFM_CUDA_TRY(ctx, launch_order(k, G, a, ctx->num_sms, s));
+        } else {
+            LABFM_CUDA_TRY(ctx, launch_mixed(k, nullptr, n));
+        }
     } else {
-        int nb = (int)((n + 255) / 256);
-        k_order_count<<<nb, 256, 0, s>>>(n, order, dmisc + 2, dmisc + 1);
+        // bucket the nodes by (order, stencil size), both descending
+        LABFM_CUDA_TRY(ctx, cudaMemsetAsync(d_hist, 0, sizeof(unsigned int) * NBUCKET, s));
+        const int nb = (int)((n + 255) / 256);
+        k_bucket_count<<<nb, 256, 0, s>>>(n, order, a.row_ptr, d_hist, dmisc + 1);
         LABFM_CUDA_TRY(ctx, cudaGetLastError());
-        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        std::vector<unsigned int> hist(NBUCKET);
+        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hist.data(), d_hist, sizeof(unsigned int) * NBUCKET, cudaMemcpyDeviceToHost, s));
         LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         if (hs[1] != 0) return fail(ctx, LABFM_ERR_ARG, "order[] has entries outside 1..8");
-        unsigned long long cnt[KMAX + 1], base[KMAX + 1];
-        unsigned long long acc = 0;
-        for (int k = 0; k <= KMAX; k++) {
-            cnt[k] = hs[2 + k];
-            base[k] = acc;
-            acc += cnt[k];
+        std::vector<unsigned int> start(NBUCKET);
+        int64_t cnt[KMAX + 1] = {0}, base[KMAX + 1] = {0};
+        double degsum[KMAX + 1] = {0};
+        unsigned int acc = 0;
+        for (int b = 0; b < NBUCKET; b++) {
+            start[b] = acc;
+            acc += hist[b];
+            const int k = KMAX - b / 256;
+            if (k >= 1) {
+                if (cnt[k] == 0 && hist[b]) base[k] = start[b];
+                cnt[k] += hist[b];
+                degsum[k] += (double)hist[b] * (255 - b % 256);
+            }
         }
         LABFM_CUDA_TRY(ctx, ctx->status_tmp.reserve(sizeof(int32_t) * (n > 0 ? n : 1)));
         int32_t *list = ctx->status_tmp.as<int32_t>();
-        for (int k = 0; k <= KMAX; k++) hs[k] = base[k];
-        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(dmisc + 11, hs, sizeof(base), cudaMemcpyHostToDevice, s));
-        k_order_scatter<<<nb, 256, 0, s>>>(n, order, dmisc + 11, dmisc + 20, list);
+        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(d_cursor, start.data(), sizeof(unsigned int) * NBUCKET, cudaMemcpyHostToDevice, s));
+        k_bucket_scatter<<<nb, 256, 0, s>>>(n, order, a.row_ptr, d_cursor, list);
         LABFM_CUDA_TRY(ctx, cudaGetLastError());
-        if (!mixed) {
-            // every order in one persistent launch over the whole (ascending-order) list
-            a.list = list;
-            a.n_list = (int64_t)acc;
-            LABFM_CUDA_TRY(ctx, launch_all_orders(a, order, ctx->num_sms, s));
-        } else {
-            for (int k = KMAX; k >= 1; k--) {
-                if (!cnt[k]) continue;
-                LABFM_CUDA_TRY(ctx, launch(k, list + base[k], (int64_t)cnt[k]));
-            }
+        // the FP64-routed orders: one persistent launch over their work items, costliest first
+        OrderItems I{};
+        int64_t items = 0;
+        for (int k = KMAX; k >= 1; k--) {
+            I.group[k] = 256;
+            I.base[k] = base[k];
+            I.item0[k] = items;
+            if (!fp64_route(k) || !cnt[k]) continue;
+            int G = 256;
+            LABFM_CUDA_TRY(ctx, group_for(k, list + base[k], cnt[k], degsum[k] / (double)cnt[k], G));
+            const int ng = BUILD_THREADS / G;
+            I.group[k] = G;
+            ctx->info_group[k] = G;
+            I.cnt[k] = cnt[k];
+            I.n_items[k] = (cnt[k] + ng - 1) / ng;
+            items += I.n_items[k];
         }
+        I.total = items;
+        LABFM_CUDA_TRY(ctx, cudaMemsetAsync(dmisc, 0, sizeof(unsigned long long), s));  // the timing runs' flags
+        if (items) {
+            a.list = list;
+            a.n_list = n;
+            LABFM_CUDA_TRY(ctx, launch_persistent_build(k_build_fp64_items, items, ctx->num_sms, s, a, I));
+        }
+        for (int k = KMAX; k >= 1; k--)
+            if (!fp64_route(k) && cnt[k]) LABFM_CUDA_TRY(ctx, launch_mixed(k, list + base[k], cnt[k]));
     }
     LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, NMISC * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -571,8 +753,7 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         ctx->info_fp64_rebuilt = nfb;
         a.list = ctx->mfallback.as<int32_t>();
         a.n_list = nfb;
-        if (!order) LABFM_CUDA_TRY(ctx, launch_order(uniform_order, a, ctx->num_sms, s));
-        else LABFM_CUDA_TRY(ctx, launch_all_orders(a, order, ctx->num_sms, s));
+        LABFM_CUDA_TRY(ctx, launch_persistent_build(k_build_fp64_any, nfb, ctx->num_sms, s, a, order, uniform_order));
         LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     }

@@ -74,6 +74,7 @@ struct labfm_ctx {
     // statistics of the last labfm_build_weights (labfm_get_build_info)
     int64_t info_ref_hist[8] = {0};
     int64_t info_fp64_rebuilt = 0;
+    int info_group[LABFM_MAX_ORDER + 1] = {0};  // threads per node of the FP64 kernel, per order built by it
 
     // RK4
     labfm::DevBuf wcomb, rk_acc, rk_stage_a, rk_stage_b;

