@@ -152,6 +152,30 @@ def measured_fp64_peak(torch, dev):
     return 2.0 * n ** 3 / best / 1e12
 
 
+def measured_fp32_peak(torch, dev):
+    """FP32 FFMA peak measured here with cuBLAS SGEMM (8192^3, TF32 off: the FP32 pipes), TFLOP/s."""
+    n = 8192
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        a = torch.randn(n, n, dtype=torch.float32, device=dev)
+        b = torch.randn(n, n, dtype=torch.float32, device=dev)
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return 2.0 * n ** 3 / best / 1e12
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -342,10 +366,19 @@ def mixed_vs_fp64(torch, P, dev, local_rank, nsx, k, ops, field):
         ms = _time(torch, lambda: L.build_weights(C, uniform_order=k, precision=prec))
         ders[prec] = L.apply(f).cpu().numpy()
         res[prec] = {"ms": ms, "mnodes_per_s": n / (ms * 1e-3) / 1e6}
-        if prec != "fp64":
-            res[prec].update(L.get_build_info())
+        info = L.get_build_info()
+        if prec == "fp64":
+            res[prec]["fp64_group_threads"] = info["fp64_group_threads"]
+        else:
+            res[prec].update(info)
     res["speedup_mixed_over_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
     res["speedup_mixed_tc_over_fp64"] = res["fp64"]["ms"] / res["mixed_tc"]["ms"]
+    # the FP64 build's algorithmic flops per node (the same work for every variant) over each
+    # variant's time: FP64-equivalent TFLOP/s, set against the FP64 pipe's measured peak
+    ni = L.nnz / n
+    flops = build_flops_per_node(k, ni, len(ops)) * n
+    for prec in ("fp64", "mixed", "mixed_tc"):
+        res[prec]["fp64_equivalent_tflops"] = flops / (res[prec]["ms"] * 1e-3) / 1e12
     res["ops"] = list(ops)
     res["deriv_diff_mixed_vs_fp64"] = deriv_errors(ders["mixed"], ders["fp64"])
     res["deriv_diff_mixed_tc_vs_fp64"] = deriv_errors(ders["mixed_tc"], ders["fp64"])
@@ -626,7 +659,9 @@ def rk4_large(torch, P, dev, local_rank, n_side=2048, nsteps=1000):
 
 def walls_variable_order(torch, P, dev, local_rank, n_side=1000):
     """Non-periodic unit square with walls, spacing varying 4x, per-node order 2..8 (capped at 4
-    near walls): the bucketed build (one launch per order) in FP64 and mixed precision."""
+    near walls): the build with nodes bucketed by (order, stencil size), in FP64 (one persistent
+    launch over all orders) and in mixed precision (orders 2-4 in that launch, orders 5-8 through
+    the mixed kernels), with the group sizes the build autotuner chose."""
     ns = S.variable_wall_nodes(n_side, seed=4)
     n = ns.n
     L = P.Labfm(local_rank)
@@ -642,6 +677,7 @@ def walls_variable_order(torch, P, dev, local_rank, n_side=1000):
         st = status.cpu().numpy()
         res[prec] = {"ms": ms, "mnodes_per_s": n / (ms * 1e-3) / 1e6,
                      "flagged_nodes": int((st != 0).sum())}
+        res[prec].update(L.get_build_info())
     L.close()
     return res
 
@@ -814,7 +850,16 @@ def run_labfm(args, rank, world, local_rank):
         "gpu_launches": args.steps * (nbr_launches(n, ncells_of(HS / N_SIDE)) + 1 + 1 + 1 + 4),
         "clocks": clk,
     }
+    line["build_tuning"] = L.get_build_info()["fp64_group_threads"]
     line["extra"] = extra_measurements(torch, P, dev, local_rank, ns, field, hbm)
+    fp32_peak = measured_fp32_peak(torch, dev)
+    line["extra"]["peaks"] = {"fp64_tflops": fp64_peak, "fp64_source": "cuBLAS DGEMM 4096^3 (FP64 pipe)",
+                              "fp32_tflops": fp32_peak, "fp32_source": "cuBLAS SGEMM 8192^3, TF32 off (FFMA pipes)",
+                              "hbm_gbs": hbm, "hbm_source": hbm_src}
+    for key in ("order8_mixed_vs_fp64", "order6_mixed_vs_fp64"):
+        for prec in ("fp64", "mixed", "mixed_tc"):
+            r = line["extra"][key][prec]
+            r["fp64_equivalent_frac_of_fp64_peak"] = r["fp64_equivalent_tflops"] / fp64_peak
     a32 = line["extra"].get("apply_f32")
     if a32:  # the HBM-bound variant of the apply, beside the FP64-pipe-bound one above
         line["apply_roofline"]["f32_variant"] = {

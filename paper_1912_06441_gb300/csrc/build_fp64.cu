@@ -614,7 +614,9 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         cudaError_t e = cudaStreamIsCapturing(s, &cap);
         if (e != cudaSuccess) return e;
         if (cap != cudaStreamCaptureStatusNone) return cudaSuccess;
-        if (cnt >= 4096) {
+        const int n_ok = (int)group_ok(k, 64) + (int)group_ok(k, 128) + (int)group_ok(k, 256);
+        if (n_ok == 1) G = 256;  // one candidate: nothing to time
+        if (cnt >= 4096 && n_ok > 1) {
             const int cand[3] = {64, 128, 256};
             float best = 1e30f;
             cudaEvent_t e0, e1;

@@ -492,9 +492,10 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, 
                  "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+// Bounded wait for the completion of phase `parity` of the mbarrier (polls; false: gave up).
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, int polls = 1 << 20)
 {
-    for (int it = 0; it < (1 << 20); it++) {
+    for (int it = 0; it < polls; it++) {
         uint32_t done;
         asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
                      : "=r"(done)
@@ -533,6 +534,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
     __shared__ uint32_t s_max[2 * P];  // per-row max |hi| of X (0..P-1) and W (P..2P-1) over the chunk
     __shared__ int s_e[2 * P];          // the rows' scaling exponents
     __shared__ int s_bad, s_abort;
+    __shared__ uint32_t s_pending;  // the mbarrier phase whose MMAs a timed-out wait left behind
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -680,6 +682,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
                 if (!ok) {
                     if (tid == 0) {
                         s_abort = 1;
+                        s_pending = phase ^ 1u;
                         atomicAdd(A.tc_timeout, 1ull);
                     }
                 } else if (epi) {
@@ -748,6 +751,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
         if (tid == 0) A.flag[li] = s_bad;
         __syncthreads();
     }
+    // After a wait that gave up, the MMAs of that commit may still be writing tensor memory: wait
+    // for them once more (bounded, 4x longer) before the memory is released.  The call reports
+    // LABFM_ERR_TIMEOUT either way and its weights are undefined.  (Not exercised on the GPU:
+    // making a wait run out would leave tensor-core work in flight on a shared GPU.)
+    if (s_abort) tc_wait(mbar, s_pending, 1 << 22);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
