@@ -141,10 +141,27 @@ __constant__ RPolyTable c_rpoly = make_rpoly_table();
 __constant__ double c_invfact[KMAX + 1] = {1.0,       1.0,        0.5,         1.0 / 6.0,   1.0 / 24.0,
                                            1.0 / 120, 1.0 / 720., 1.0 / 5040., 1.0 / 40320.};
 
+// 1 / (a! b!) as the product of the two reciprocals above, rounded once (the value a product of
+// the two entries of c_invfact gives at run time)
+struct InvFact2 {
+    double v[KMAX + 1][KMAX + 1];
+};
+constexpr InvFact2 make_invfact2()
+{
+    const double f[KMAX + 1] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120, 1.0 / 720., 1.0 / 5040., 1.0 / 40320.};
+    InvFact2 T{};
+    for (int a = 0; a <= KMAX; a++)
+        for (int b = 0; b <= KMAX; b++) T.v[a][b] = f[a] * f[b];
+    return T;
+}
+__constant__ InvFact2 c_invfact2 = make_invfact2();
+
 // Monomials and ABFs of one scaled offset (x, y), written to X[0..P), W[0..P).
 // In polar form q = |(x, y)|, (u, v) = (x, y)/q, degree n = a + b:
 //   X_(a,b) = q^n u^a v^b / (a! b!)          d^(a,b)|r| = q^(1-n) P_(a,b)(u, v)
-// and both use the same n+1 products u^t v^(n-t), formed once per degree.  Results go
+// and both use the same n+1 products u^t v^(n-t), formed once per degree.  d^(a,b)|r| has the
+// parity of a in x (|r| is even in x and y), so P_(a,b) has only the terms u^t v^(n-t) with t of
+// the parity of a: the others are skipped (their coefficients are exactly zero).  Results go
 // straight to shared memory to keep the register footprint small.
 template <int K>
 __device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__restrict__ X, double *__restrict__ W)
@@ -174,10 +191,10 @@ __device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__r
 #pragma unroll
         for (int a = n; a >= 0; a--) {
             const int e = p_of_k(n - 1) + (n - a);
-            X[e] = qn * mono[a] * (c_invfact[a] * c_invfact[n - a]);
+            X[e] = qn * mono[a] * c_invfact2.v[a][n - a];
             double s = 0.0;
 #pragma unroll
-            for (int t = 0; t <= n; t++) s = fma(c_rpoly.c[e][t], mono[t], s);
+            for (int t = a & 1; t <= n; t += 2) s = fma(c_rpoly.c[e][t], mono[t], s);
             const double dr = s * iqn;
             double wv = d1 * dr;
             // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)

@@ -181,7 +181,7 @@ __device__ __forceinline__ void eval_xw_part(const df *__restrict__ rec, int par
             // parts and sum errors collected in one float, renormalised once at the end
             float sh = 0.0f, sl = 0.0f;
 #pragma unroll
-            for (int t = 0; t <= n; t++) {
+            for (int t = a & 1; t <= n; t += 2) {  // P_alpha has only the terms of a's parity
                 const float c = c_dft.rpoly[e][t];
                 if (c != 0.0f) {
                     const float ph = __fmul_rn(c, mono[t].hi);
@@ -295,7 +295,7 @@ __device__ __forceinline__ void stage_chunk(const MixedArgs &A, int64_t rs, int 
 #pragma unroll
             for (int e = 0; e < P; e++) {
                 const int a = elem_a(e), b = elem_degree(e) - a;
-                X[e] = xp[a] * yp[b] * (c_invfact[a] * c_invfact[b]);
+                X[e] = xp[a] * yp[b] * c_invfact2.v[a][b];
             }
 #pragma unroll
             for (int e = P; e < LDX; e++) X[e] = 0.0;
@@ -315,10 +315,12 @@ __device__ __forceinline__ void stage_chunk(const MixedArgs &A, int64_t rs, int 
         }
     }
     // the padding columns the tiles read
-    for (int t = threadIdx.x; t < nj * (LDX - P); t += MIX_THREADS) {
-        const int jj = t / (LDX - P), e = P + t % (LDX - P);
-        if (Xf) Xf[jj * LDX + e] = df{0.0f, 0.0f};
-        Wf[jj * LDX + e] = df{0.0f, 0.0f};
+    if constexpr (LDX > P) {
+        for (int t = threadIdx.x; t < nj * (LDX - P); t += MIX_THREADS) {
+            const int jj = t / (LDX - P), e = P + t % (LDX - P);
+            if (Xf) Xf[jj * LDX + e] = df{0.0f, 0.0f};
+            Wf[jj * LDX + e] = df{0.0f, 0.0f};
+        }
     }
     __syncthreads();
 }
