@@ -606,7 +606,6 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
     // orders below MIXED_MIN_ORDER, whose p x p systems (p <= 14) are small and well conditioned:
     // there the cost is latency, which the grouped FP64 kernel hides better than the four-kernel
     // mixed pipeline, and FP64 arithmetic is accurate to the floor.
-    constexpr int MIXED_MIN_ORDER = 5;
     auto fp64_route = [&](int k) { return !mixed || k < MIXED_MIN_ORDER; };
 
     // Group size of the FP64 kernel per order: timed once per (order, mean stencil size, n_ops)
@@ -660,14 +659,15 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         ctx->tuned[key] = (uint32_t)G;
         return cudaSuccess;
     };
+    // the mixed kernels over the listed nodes, all at order k
     auto launch_mixed = [&](int k, const int32_t *list, int64_t n_list) -> cudaError_t {
         m.list = list;
         m.n_list = n_list;
         bool adaptive = false;
         m.nref = precision_nref(precision, adaptive);
         m.adaptive = adaptive ? 1 : 0;
-        // per-node matrices of one batch: at most 2^18 nodes (4.2 GB at k = 8)
-        m.batch_nodes = std::max<int64_t>(1, std::min<int64_t>(n_list, (int64_t)1 << 18));
+        // per-node matrices of one batch: at most 2^20 nodes (16 GB at k = 8)
+        m.batch_nodes = std::max<int64_t>(1, std::min<int64_t>(n_list, (int64_t)1 << 20));
         cudaError_t e = ctx->mscratch.reserve(mixed_scratch_bytes_per_node(k) * (size_t)m.batch_nodes + 256);
         if (e != cudaSuccess) return e;
         m.scratch = ctx->mscratch.ptr;
@@ -753,6 +753,10 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
             a.n_list = n;
             LABFM_CUDA_TRY(ctx, launch_persistent_build(k_build_fp64_items, items, ctx->num_sms, s, a, I));
         }
+        // the mixed-built orders (MIXED_MIN_ORDER .. 8), highest first, each over its segment of the
+        // bucketed list (one launch per order and phase: kernels shaped for each order were faster
+        // than one launch per phase over all orders, which carries order 8's shared memory and
+        // thread count for every node)
         for (int k = KMAX; k >= 1; k--)
             if (!fp64_route(k) && cnt[k]) LABFM_CUDA_TRY(ctx, launch_mixed(k, list + base[k], cnt[k]));
     }

@@ -96,11 +96,13 @@ struct MixedArgs {
     void *w;            // [nnz][n_ops] output
     int wdtype;
     double *wt;         // [nnz][n_ops] scratch: unscaled weights w~ in double
-    df *Mg;             // [n_list][P][P] scratch: M, then M^-1
+    df *Mg;             // [n_list][mstride] scratch: M, then M^-1 (p x p, row-major)
+    int64_t mstride;    // elements per node in Mg (p^2)
     int *flag;          // [n_list] scratch: per-node failure bits
     Rec *recs;          // [nnz] per-entry preamble (k_mixed_records)
-    df *wstore;         // [nnz][P] W of every entry in double-float, written by the assembly and
-                        // read by the weights kernel; null: the weights kernel evaluates W again
+    df *wstore;         // [nnz][wstride] W of every entry in double-float, written by the assembly
+                        // and read by the weights kernel; null: the weights kernel evaluates W again
+    int64_t wstride;    // elements per entry in wstore (p)
     unsigned long long *tc_timeout;  // tensor-core assembly: waits that gave up
     int32_t *node_status;
     unsigned long long *n_bad;
@@ -303,10 +305,10 @@ __device__ __forceinline__ void stage_chunk(const MixedArgs &A, int64_t rs, int 
     }
     if (A.wstore && !Xf) {
         // W as the assembly stored it (coalesced: consecutive threads, consecutive elements)
-        const df *ws = A.wstore + (rs + j0) * (int64_t)P;
+        const df *ws = A.wstore + (rs + j0) * A.wstride;
         for (int t = threadIdx.x; t < nj * P; t += MIX_THREADS) {
             const int jj = t / P, e = t - jj * P;
-            Wf[jj * LDX + e] = ws[t];
+            Wf[jj * LDX + e] = ws[jj * A.wstride + e];
         }
     } else {
         for (int t = threadIdx.x; t < nj * PARTS; t += MIX_THREADS) {
@@ -339,11 +341,10 @@ __device__ __forceinline__ void mark_undersampled(const MixedArgs &A, int64_t li
 // A: X, W and M in double-float
 // ------------------------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_assemble(MixedArgs A)
+__device__ __forceinline__ void assemble_node(const MixedArgs &A, int64_t li, double *smem_d, int &s_bad)
 {
     using C = MCfg<K>;
     constexpr int P = C::P, LDX = C::LDX, NB = C::NB, TM = C::TM, TN = C::TN;
-    extern __shared__ __align__(16) double smem_d[];
     df *Xf = reinterpret_cast<df *>(smem_d);  // [NB][LDX]
     df *Wf = Xf + NB * LDX;                   // [NB][LDX]
     df *Nrec = Wf + NB * LDX;                 // [NB][NREC]
@@ -351,71 +352,76 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_assemble(MixedArgs A)
     const int rg = tid / C::CG, cg = tid % C::CG;
     const bool tile_active = tid < C::RG * C::CG;
 
-    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
-        const int64_t i = node_of(A, li);
-        const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
-        const int ni = (int)(re - rs);
-        if (ni < P) {
-            mark_undersampled(A, li, i, rs, ni);
-            continue;
+    const int64_t i = node_of(A, li);
+    const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
+    const int ni = (int)(re - rs);
+    if (ni < P) {
+        mark_undersampled(A, li, i, rs, ni);
+        return;
+    }
+    df acc[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; a++)
+#pragma unroll
+        for (int b = 0; b < TN; b++) acc[a][b] = df{0.0f, 0.0f};
+    for (int j0 = 0; j0 < ni; j0 += NB) {
+        const int nj = min(NB, ni - j0);
+        stage_chunk<K>(A, rs, j0, nj, nullptr, Xf, Wf, Nrec);
+        if (A.wstore) {
+            df *ws = A.wstore + (rs + j0) * A.wstride;
+            for (int t = tid; t < nj * P; t += MIX_THREADS) {
+                const int jj = t / P, e = t - jj * P;
+                ws[jj * A.wstride + e] = Wf[jj * LDX + e];
+            }
         }
-        df acc[TM][TN];
+        if (tile_active) {
+            for (int j = 0; j < nj; j++) {
+                const df *X = Xf + j * LDX + rg * TM;
+                const df *W = Wf + j * LDX + cg * TN;
+                df xv[TM], wv[TN];
+#pragma unroll
+                for (int a = 0; a < TM; a++) xv[a] = X[a];
+                float4 w01 = *reinterpret_cast<const float4 *>(W);
+                float4 w23 = *reinterpret_cast<const float4 *>(W + 2);
+                wv[0] = df{w01.x, w01.y};
+                wv[1] = df{w01.z, w01.w};
+                wv[2] = df{w23.x, w23.y};
+                wv[3] = df{w23.z, w23.w};
+#pragma unroll
+                for (int a = 0; a < TM; a++)
+#pragma unroll
+                    for (int b = 0; b < TN; b++) acc[a][b] = df_fma(xv[a], wv[b], acc[a][b]);
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    if (tile_active) {
+        df *Mg = A.Mg + li * A.mstride;
+        bool finite = true;
 #pragma unroll
         for (int a = 0; a < TM; a++)
 #pragma unroll
-            for (int b = 0; b < TN; b++) acc[a][b] = df{0.0f, 0.0f};
-        for (int j0 = 0; j0 < ni; j0 += NB) {
-            const int nj = min(NB, ni - j0);
-            stage_chunk<K>(A, rs, j0, nj, nullptr, Xf, Wf, Nrec);
-            if (A.wstore) {
-                df *ws = A.wstore + (rs + j0) * (int64_t)P;
-                for (int t = tid; t < nj * P; t += MIX_THREADS) {
-                    const int jj = t / P, e = t - jj * P;
-                    ws[t] = Wf[jj * LDX + e];
+            for (int b = 0; b < TN; b++) {
+                int m = rg * TM + a, c = cg * TN + b;
+                if (m < P && c < P) {
+                    Mg[m * P + c] = acc[a][b];
+                    finite &= df_isfinite(acc[a][b]);
                 }
             }
-            if (tile_active) {
-                for (int j = 0; j < nj; j++) {
-                    const df *X = Xf + j * LDX + rg * TM;
-                    const df *W = Wf + j * LDX + cg * TN;
-                    df xv[TM], wv[TN];
-#pragma unroll
-                    for (int a = 0; a < TM; a++) xv[a] = X[a];
-                    float4 w01 = *reinterpret_cast<const float4 *>(W);
-                    float4 w23 = *reinterpret_cast<const float4 *>(W + 2);
-                    wv[0] = df{w01.x, w01.y};
-                    wv[1] = df{w01.z, w01.w};
-                    wv[2] = df{w23.x, w23.y};
-                    wv[3] = df{w23.z, w23.w};
-#pragma unroll
-                    for (int a = 0; a < TM; a++)
-#pragma unroll
-                        for (int b = 0; b < TN; b++) acc[a][b] = df_fma(xv[a], wv[b], acc[a][b]);
-                }
-            }
-            __syncthreads();
-        }
-        __shared__ int s_bad;
-        if (tid == 0) s_bad = 0;
-        __syncthreads();
-        if (tile_active) {
-            df *Mg = A.Mg + li * (int64_t)P * P;
-            bool finite = true;
-#pragma unroll
-            for (int a = 0; a < TM; a++)
-#pragma unroll
-                for (int b = 0; b < TN; b++) {
-                    int m = rg * TM + a, c = cg * TN + b;
-                    if (m < P && c < P) {
-                        Mg[m * P + c] = acc[a][b];
-                        finite &= df_isfinite(acc[a][b]);
-                    }
-                }
-            if (!finite) s_bad = 4;  // a neighbour on top of node i: singular ABFs
-        }
-        __syncthreads();
-        if (tid == 0) A.flag[li] = s_bad;
+        if (!finite) s_bad = 4;  // a neighbour on top of node i: singular ABFs
     }
+    __syncthreads();
+    if (tid == 0) A.flag[li] = s_bad;
+}
+
+template <int K>
+__global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_assemble(MixedArgs A)
+{
+    extern __shared__ __align__(16) double smem_d[];
+    __shared__ int s_bad;
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) assemble_node<K>(A, li, smem_d, s_bad);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -520,29 +526,232 @@ __device__ __forceinline__ int tc_row_exp(float m) { return m > 0.0f ? ilogbf(m)
 // byte offset of element (row r, k) in a K-major core-matrix slice
 __device__ __forceinline__ int tc_off(int r, int k) { return (r >> 3) * TC_ROWB + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
 
+// Shared state of the tensor-core assembly, kept by the kernel across the nodes of a CTA.
+struct TcShared {
+    uint32_t max[2 * PMAX];  // per-row max |hi| of X (0..P-1) and W (P..2P-1) over the chunk
+    int e[2 * PMAX];         // the rows' scaling exponents
+    int bad, abort;
+    uint32_t pending;        // the mbarrier phase whose MMAs a timed-out wait left behind
+};
+
+// M of list entry li on the tensor cores (the CTA's tensor memory `tmem`, mbarrier `mbar` with
+// its current `phase`).  Returns with ts.abort set if a completion wait gave up.
 template <int K>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A)
+__device__ __forceinline__ void tc_node(const MixedArgs &A, int64_t li, unsigned char *smem_tc, TcShared &ts,
+                                        uint32_t tmem, uint32_t mbar, uint32_t &phase)
 {
     using C = TcCfg<K>;
     constexpr int P = C::P, PN = C::PN, LDS = C::LDS;
-    extern __shared__ __align__(1024) unsigned char smem_tc[];
     unsigned char *sA = smem_tc;                      // X slices (and the X staging)
     unsigned char *sB = smem_tc + C::A_BYTES;         // W slices (and the W staging)
     df *sM = reinterpret_cast<df *>(sB + C::B_BYTES);  // M of the node, accumulated over chunks
     df *Xst = reinterpret_cast<df *>(sA);
     df *Wst = reinterpret_cast<df *>(sB);
-    __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ uint32_t s_tmem;
-    __shared__ uint32_t s_max[2 * P];  // per-row max |hi| of X (0..P-1) and W (P..2P-1) over the chunk
-    __shared__ int s_e[2 * P];          // the rows' scaling exponents
-    __shared__ int s_bad, s_abort;
-    __shared__ uint32_t s_pending;  // the mbarrier phase whose MMAs a timed-out wait left behind
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // epilogue role: warps 0, 1, 4, 5 read lane quadrants 0 and 1 (alpha = lane + 32 q);
+    // warps w and w + 4 take the two halves of the beta columns
+    const int q = warp & 3, half = warp >> 2;
+    const int alpha = 32 * q + lane;
+    const bool epi = q < 2;
+    const int64_t i = node_of(A, li);
+    const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
+    const int ni = (int)(re - rs);
+    if (ni < P) {
+        mark_undersampled(A, li, i, rs, ni);
+        return;
+    }
+    if (tid == 0) ts.bad = 0;
+    for (int j0 = 0; j0 < ni; j0 += TC_KC) {
+        const int nj = min(TC_KC, ni - j0);
+        const int ksteps = (nj + 15) / 16;
+        // 1. X and W of the chunk in double-float (TC_PARTS threads per neighbour)
+        if (tid < 2 * P) ts.max[tid] = 0u;
+        for (int t = tid; t < TC_KC * TC_PARTS; t += TC_THREADS) {
+            const int part = t / TC_KC, jj = t - part * TC_KC;
+            if (jj < nj)
+                eval_xw_part<K, TC_PARTS>(A.recs[rs + j0 + jj].v, part, Xst + jj * LDS, Wst + jj * LDS);
+        }
+        __syncthreads();
+        if (A.wstore) {  // W for the weights kernel (the staging is read-only until the next barrier)
+            df *ws = A.wstore + (rs + j0) * A.wstride;
+            for (int t = tid; t < nj * P; t += TC_THREADS) {
+                const int jj = t / P, e = t - jj * P;
+                ws[jj * A.wstride + e] = Wst[jj * LDS + e];
+            }
+        }
+        // 2. octets (row r of one operand, 8 consecutive neighbours) to registers, and the
+        //    row maxima of |hi| (as ordered bit patterns: non-negative floats compare as integers)
+        constexpr int NOCT = 2 * P * (TC_KC / 8);
+        constexpr int PER = (NOCT + TC_THREADS - 1) / TC_THREADS;
+        df val[PER][8];
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int o = tid + u * TC_THREADS;
+            const int opnd = o / (P * (TC_KC / 8)), rem = o - opnd * (P * (TC_KC / 8));
+            const int r = rem % P, oct = rem / P;
+            uint32_t m = 0u;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const int jj = 8 * oct + c;
+                val[u][c] = (o < NOCT && jj < nj) ? (opnd == 0 ? Xst : Wst)[jj * LDS + r] : df{0.0f, 0.0f};
+                m = max(m, __float_as_uint(fabsf(val[u][c].hi)));  // NaN and inf sort above finite
+            }
+            if (o < NOCT && m) atomicMax(&ts.max[opnd * P + r], m);
+        }
+        __syncthreads();
+        // 3. slices -> BF16 operands, one 16-byte core-matrix row (8 neighbours) per store;
+        //    K positions nj .. 16 ksteps - 1 are zero
+        if (tid < 2 * P) {
+            const uint32_t mb = ts.max[tid];
+            ts.e[tid] = tc_row_exp(mb >= 0x7f800000u ? 0.0f : __uint_as_float(mb));
+        }
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int o = tid + u * TC_THREADS;
+            const int opnd = o / (P * (TC_KC / 8)), rem = o - opnd * (P * (TC_KC / 8));
+            const int r = rem % P, oct = rem / P;
+            if (o >= NOCT || 8 * oct >= 16 * ksteps) continue;
+            const uint32_t mb = ts.max[opnd * P + r];
+            if (mb >= 0x7f800000u) ts.bad = 4;  // a neighbour on top of node i: singular ABFs
+            const float sc = tc_pow2(-tc_row_exp(mb >= 0x7f800000u ? 0.0f : __uint_as_float(mb)));
+            float rh[8], rl[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                rh[c] = val[u][c].hi * sc;
+                rl[c] = val[u][c].lo * sc;
+            }
+            unsigned char *base = (opnd == 0 ? sA : sB) + tc_off(r, 8 * oct);
+            const int sstride = opnd == 0 ? C::SA : C::SB;
+#pragma unroll
+            for (int sl = 1; sl <= NSL; sl++) {
+                const float up = tc_pow2(8 * sl), dn = tc_pow2(-8 * sl);
+                uint32_t packed[4];
+#pragma unroll
+                for (int c = 0; c < 8; c += 2) {
+                    const float c0 = rintf(rh[c] * up), c1 = rintf(rh[c + 1] * up);  // integers, |c| <= 256
+                    two_sum(__fsub_rn(rh[c], c0 * dn), rl[c], rh[c], rl[c]);          // exact remainders
+                    two_sum(__fsub_rn(rh[c + 1], c1 * dn), rl[c + 1], rh[c + 1], rl[c + 1]);
+                    __nv_bfloat162 pr = __floats2bfloat162_rn(c0, c1);
+                    packed[c / 2] = *reinterpret_cast<uint32_t *>(&pr);
+                }
+                *reinterpret_cast<uint4 *>(base + (sl - 1) * sstride) =
+                    make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // 4. per round of levels: issue, wait, read out
+        for (int t0 = 2; t0 <= NSL + 1 && !ts.abort; t0 += C::LPR) {
+            const int t1 = min(NSL + 1, t0 + C::LPR - 1);
+            asm volatile("tcgen05.fence::after_thread_sync;");  // the last read-out is complete
+            if (tid == 0) {
+                uint64_t ad[NSL], bd[NSL];
+                const uint32_t a0 = tc_smem_u32(sA), b0 = tc_smem_u32(sB);
+#pragma unroll
+                for (int sl = 0; sl < NSL; sl++) {
+                    ad[sl] = tc_desc(a0 + sl * C::SA);
+                    bd[sl] = tc_desc(b0 + sl * C::SB);
+                }
+                // one MMA per (X slice a, K step): B = the W slices b_lo .. b_hi that pair with a
+                // inside the round (adjacent rows), D shifted so that column block b lands in
+                // level a + b's accumulator.  a = 1 covers every level of the round, so its
+                // first K step initialises all of them.
+                for (int a = 1; a <= NSL && a < t1; a++) {
+                    const int b_lo = max(1, t0 - a), b_hi = min(NSL, t1 - a);
+                    if (b_lo > b_hi) continue;
+                    const uint32_t idesc = tc_idesc((b_hi - b_lo + 1) * PN);
+                    const uint32_t dcol = (uint32_t)((a + b_lo - t0) * PN);
+                    for (int ks = 0; ks < ksteps; ks++)  // +256 B per K step = +16 in the address field
+                        tc_mma(tmem + dcol, ad[a - 1] + (uint64_t)(16 * ks), bd[b_lo - 1] + (uint64_t)(16 * ks),
+                               idesc, (a == 1 && ks == 0) ? 0 : 1);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    mbar));
+            }
+            const bool ok = tc_wait(mbar, phase);
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!ok) {
+                if (tid == 0) {
+                    ts.abort = 1;
+                    ts.pending = phase ^ 1u;
+                    atomicAdd(A.tc_timeout, 1ull);
+                }
+            } else if (epi) {
+                // thread (alpha, half): M[alpha][beta] for its half of the beta columns,
+                // accumulated over the rounds and chunks in shared memory.  The levels of a
+                // round are exact integers < 2^24: S = sum_t D_t 2^(8 (t1 - t)) is exact in
+                // int64 (< 2^57), and M += 2^(eX + eW - 8 t1) S.
+                const bool own = alpha < P;
+                constexpr int HB = PN / 2;  // columns per half
+                df *Mrow = sM + (own ? alpha : 0) * C::LDSM;
+                const int ex = ts.e[own ? alpha : 0] - 8 * t1;
+                for (int g = 0; g < HB; g += 8) {
+                    // all levels of this round for 8 columns: issue the loads, then one wait
+                    uint32_t v[C::LPR][8];
+#pragma unroll
+                    for (int l = 0; l < C::LPR; l++) {
+                        if (t0 + l <= t1) {
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
+                                  "=r"(v[l][5]), "=r"(v[l][6]), "=r"(v[l][7])
+                                : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(l * PN + half * HB + g)));
+                        }
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (own) {
+#pragma unroll
+                        for (int c = 0; c < 8; c++) {
+                            const int beta = half * HB + g + c;
+                            if (beta >= P) continue;
+                            long long S = 0;
+#pragma unroll
+                            for (int l = 0; l < C::LPR; l++)
+                                if (t0 + l <= t1) S = S * 256 + (long long)__float2int_rn(__uint_as_float(v[l][c]));
+                            // S = H 2^32 + L1 2^16 + L0, |H| < 2^25, L1, L0 < 2^16: three exact floats
+                            const int H = (int)(S >> 32);
+                            const uint32_t L = (uint32_t)S;
+                            float sh, sl;
+                            two_sum((float)H * 4294967296.0f, (float)(L >> 16) * 65536.0f, sh, sl);
+                            sl = __fadd_rn(sl, (float)(L & 0xffffu));
+                            fast_two_sum(sh, sl, sh, sl);
+                            const float sc = tc_pow2(ex + ts.e[P + beta]);
+                            const df add = df{sh * sc, sl * sc};
+                            Mrow[beta] = (j0 == 0 && t0 == 2) ? add : df_add(Mrow[beta], add);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+        }
+        if (ts.abort) break;
+    }
+    if (ts.abort) return;
+    // M of the node -> global
+    df *Mg = A.Mg + li * A.mstride;
+    bool finite = true;
+    for (int u = tid; u < P * P; u += TC_THREADS) {
+        const int r = u / P;
+        const df v = sM[r * C::LDSM + (u - r * P)];
+        finite &= df_isfinite(v);
+        Mg[u] = v;
+    }
+    if (!finite) ts.bad = 4;
+    __syncthreads();
+    if (tid == 0) A.flag[li] = ts.bad;
+    __syncthreads();
+}
 
+// CTA set-up of the tensor-core assembly: the mbarrier and 256 tensor-memory columns.
+__device__ __forceinline__ void tc_setup(uint64_t &s_mbar, uint32_t &s_tmem, TcShared &ts)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&s_mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
-        s_abort = 0;
+        ts.abort = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(&s_tmem)),
@@ -552,215 +761,36 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = s_tmem;
-    const uint32_t mbar = tc_smem_u32(&s_mbar);
-    uint32_t phase = 0;
+}
 
-    // epilogue role: warps 0, 1, 4, 5 read lane quadrants 0 and 1 (alpha = lane + 32 q);
-    // warps w and w + 4 take the two halves of the beta columns
-    const int q = warp & 3, half = warp >> 2;
-    const int alpha = 32 * q + lane;
-    const bool epi = q < 2;
-
-    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
-        const int64_t i = node_of(A, li);
-        const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
-        const int ni = (int)(re - rs);
-        if (ni < P) {
-            mark_undersampled(A, li, i, rs, ni);
-            continue;
-        }
-        if (tid == 0) s_bad = 0;
-        for (int j0 = 0; j0 < ni; j0 += TC_KC) {
-            const int nj = min(TC_KC, ni - j0);
-            const int ksteps = (nj + 15) / 16;
-            // 1. X and W of the chunk in double-float (TC_PARTS threads per neighbour)
-            if (tid < 2 * P) s_max[tid] = 0u;
-            for (int t = tid; t < TC_KC * TC_PARTS; t += TC_THREADS) {
-                const int part = t / TC_KC, jj = t - part * TC_KC;
-                if (jj < nj)
-                    eval_xw_part<K, TC_PARTS>(A.recs[rs + j0 + jj].v, part, Xst + jj * LDS, Wst + jj * LDS);
-            }
-            __syncthreads();
-            if (A.wstore) {  // W for the weights kernel (the staging is read-only until the next barrier)
-                df *ws = A.wstore + (rs + j0) * (int64_t)P;
-                for (int t = tid; t < nj * P; t += TC_THREADS) {
-                    const int jj = t / P, e = t - jj * P;
-                    ws[t] = Wst[jj * LDS + e];
-                }
-            }
-            // 2. octets (row r of one operand, 8 consecutive neighbours) to registers, and the
-            //    row maxima of |hi| (as ordered bit patterns: non-negative floats compare as integers)
-            constexpr int NOCT = 2 * P * (TC_KC / 8);
-            constexpr int PER = (NOCT + TC_THREADS - 1) / TC_THREADS;
-            df val[PER][8];
-#pragma unroll
-            for (int u = 0; u < PER; u++) {
-                const int o = tid + u * TC_THREADS;
-                const int opnd = o / (P * (TC_KC / 8)), rem = o - opnd * (P * (TC_KC / 8));
-                const int r = rem % P, oct = rem / P;
-                uint32_t m = 0u;
-#pragma unroll
-                for (int c = 0; c < 8; c++) {
-                    const int jj = 8 * oct + c;
-                    val[u][c] = (o < NOCT && jj < nj) ? (opnd == 0 ? Xst : Wst)[jj * LDS + r] : df{0.0f, 0.0f};
-                    m = max(m, __float_as_uint(fabsf(val[u][c].hi)));  // NaN and inf sort above finite
-                }
-                if (o < NOCT && m) atomicMax(&s_max[opnd * P + r], m);
-            }
-            __syncthreads();
-            // 3. slices -> BF16 operands, one 16-byte core-matrix row (8 neighbours) per store;
-            //    K positions nj .. 16 ksteps - 1 are zero
-            if (tid < 2 * P) {
-                const uint32_t mb = s_max[tid];
-                s_e[tid] = tc_row_exp(mb >= 0x7f800000u ? 0.0f : __uint_as_float(mb));
-            }
-#pragma unroll
-            for (int u = 0; u < PER; u++) {
-                const int o = tid + u * TC_THREADS;
-                const int opnd = o / (P * (TC_KC / 8)), rem = o - opnd * (P * (TC_KC / 8));
-                const int r = rem % P, oct = rem / P;
-                if (o >= NOCT || 8 * oct >= 16 * ksteps) continue;
-                const uint32_t mb = s_max[opnd * P + r];
-                if (mb >= 0x7f800000u) s_bad = 4;  // a neighbour on top of node i: singular ABFs
-                const float sc = tc_pow2(-tc_row_exp(mb >= 0x7f800000u ? 0.0f : __uint_as_float(mb)));
-                float rh[8], rl[8];
-#pragma unroll
-                for (int c = 0; c < 8; c++) {
-                    rh[c] = val[u][c].hi * sc;
-                    rl[c] = val[u][c].lo * sc;
-                }
-                unsigned char *base = (opnd == 0 ? sA : sB) + tc_off(r, 8 * oct);
-                const int sstride = opnd == 0 ? C::SA : C::SB;
-#pragma unroll
-                for (int sl = 1; sl <= NSL; sl++) {
-                    const float up = tc_pow2(8 * sl), dn = tc_pow2(-8 * sl);
-                    uint32_t packed[4];
-#pragma unroll
-                    for (int c = 0; c < 8; c += 2) {
-                        const float c0 = rintf(rh[c] * up), c1 = rintf(rh[c + 1] * up);  // integers, |c| <= 256
-                        two_sum(__fsub_rn(rh[c], c0 * dn), rl[c], rh[c], rl[c]);          // exact remainders
-                        two_sum(__fsub_rn(rh[c + 1], c1 * dn), rl[c + 1], rh[c + 1], rl[c + 1]);
-                        __nv_bfloat162 pr = __floats2bfloat162_rn(c0, c1);
-                        packed[c / 2] = *reinterpret_cast<uint32_t *>(&pr);
-                    }
-                    *reinterpret_cast<uint4 *>(base + (sl - 1) * sstride) =
-                        make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            // 4. per round of levels: issue, wait, read out
-            for (int t0 = 2; t0 <= NSL + 1 && !s_abort; t0 += C::LPR) {
-                const int t1 = min(NSL + 1, t0 + C::LPR - 1);
-                asm volatile("tcgen05.fence::after_thread_sync;");  // the last read-out is complete
-                if (tid == 0) {
-                    uint64_t ad[NSL], bd[NSL];
-                    const uint32_t a0 = tc_smem_u32(sA), b0 = tc_smem_u32(sB);
-#pragma unroll
-                    for (int sl = 0; sl < NSL; sl++) {
-                        ad[sl] = tc_desc(a0 + sl * C::SA);
-                        bd[sl] = tc_desc(b0 + sl * C::SB);
-                    }
-                    // one MMA per (X slice a, K step): B = the W slices b_lo .. b_hi that pair with a
-                    // inside the round (adjacent rows), D shifted so that column block b lands in
-                    // level a + b's accumulator.  a = 1 covers every level of the round, so its
-                    // first K step initialises all of them.
-                    for (int a = 1; a <= NSL && a < t1; a++) {
-                        const int b_lo = max(1, t0 - a), b_hi = min(NSL, t1 - a);
-                        if (b_lo > b_hi) continue;
-                        const uint32_t idesc = tc_idesc((b_hi - b_lo + 1) * PN);
-                        const uint32_t dcol = (uint32_t)((a + b_lo - t0) * PN);
-                        for (int ks = 0; ks < ksteps; ks++)  // +256 B per K step = +16 in the address field
-                            tc_mma(tmem + dcol, ad[a - 1] + (uint64_t)(16 * ks), bd[b_lo - 1] + (uint64_t)(16 * ks),
-                                   idesc, (a == 1 && ks == 0) ? 0 : 1);
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        mbar));
-                }
-                const bool ok = tc_wait(mbar, phase);
-                phase ^= 1u;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                if (!ok) {
-                    if (tid == 0) {
-                        s_abort = 1;
-                        s_pending = phase ^ 1u;
-                        atomicAdd(A.tc_timeout, 1ull);
-                    }
-                } else if (epi) {
-                    // thread (alpha, half): M[alpha][beta] for its half of the beta columns,
-                    // accumulated over the rounds and chunks in shared memory.  The levels of a
-                    // round are exact integers < 2^24: S = sum_t D_t 2^(8 (t1 - t)) is exact in
-                    // int64 (< 2^57), and M += 2^(eX + eW - 8 t1) S.
-                    const bool own = alpha < P;
-                    constexpr int HB = PN / 2;  // columns per half
-                    df *Mrow = sM + (own ? alpha : 0) * C::LDSM;
-                    const int ex = s_e[own ? alpha : 0] - 8 * t1;
-                    for (int g = 0; g < HB; g += 8) {
-                        // all levels of this round for 8 columns: issue the loads, then one wait
-                        uint32_t v[C::LPR][8];
-#pragma unroll
-                        for (int l = 0; l < C::LPR; l++) {
-                            if (t0 + l <= t1) {
-                                asm volatile(
-                                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                    : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
-                                      "=r"(v[l][5]), "=r"(v[l][6]), "=r"(v[l][7])
-                                    : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(l * PN + half * HB + g)));
-                            }
-                        }
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (own) {
-#pragma unroll
-                            for (int c = 0; c < 8; c++) {
-                                const int beta = half * HB + g + c;
-                                if (beta >= P) continue;
-                                long long S = 0;
-#pragma unroll
-                                for (int l = 0; l < C::LPR; l++)
-                                    if (t0 + l <= t1) S = S * 256 + (long long)__float2int_rn(__uint_as_float(v[l][c]));
-                                // S = H 2^32 + L1 2^16 + L0, |H| < 2^25, L1, L0 < 2^16: three exact floats
-                                const int H = (int)(S >> 32);
-                                const uint32_t L = (uint32_t)S;
-                                float sh, sl;
-                                two_sum((float)H * 4294967296.0f, (float)(L >> 16) * 65536.0f, sh, sl);
-                                sl = __fadd_rn(sl, (float)(L & 0xffffu));
-                                fast_two_sum(sh, sl, sh, sl);
-                                const float sc = tc_pow2(ex + s_e[P + beta]);
-                                const df add = df{sh * sc, sl * sc};
-                                Mrow[beta] = (j0 == 0 && t0 == 2) ? add : df_add(Mrow[beta], add);
-                            }
-                        }
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncthreads();
-            }
-            if (s_abort) break;
-        }
-        if (s_abort) break;
-        // M of the node -> global
-        df *Mg = A.Mg + li * (int64_t)P * P;
-        bool finite = true;
-        for (int u = tid; u < P * P; u += TC_THREADS) {
-            const int r = u / P;
-            const df v = sM[r * C::LDSM + (u - r * P)];
-            finite &= df_isfinite(v);
-            Mg[u] = v;
-        }
-        if (!finite) s_bad = 4;
-        __syncthreads();
-        if (tid == 0) A.flag[li] = s_bad;
-        __syncthreads();
-    }
-    // After a wait that gave up, the MMAs of that commit may still be writing tensor memory: wait
-    // for them once more (bounded, 4x longer) before the memory is released.  The call reports
-    // LABFM_ERR_TIMEOUT either way and its weights are undefined.  (Not exercised on the GPU:
-    // making a wait run out would leave tensor-core work in flight on a shared GPU.)
-    if (s_abort) tc_wait(mbar, s_pending, 1 << 22);
+// CTA tear-down.  After a wait that gave up, the MMAs of that commit may still be writing tensor
+// memory: wait for them once more (bounded, 4x longer) before the memory is released.  The call
+// reports LABFM_ERR_TIMEOUT either way and its weights are undefined.  (Not exercised on the GPU:
+// making a wait run out would leave tensor-core work in flight on a shared GPU.)
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t mbar, const TcShared &ts)
+{
+    if (ts.abort) tc_wait(mbar, ts.pending, 1 << 22);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+template <int K>
+__global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ TcShared ts;
+    tc_setup(s_mbar, s_tmem, ts);
+    const uint32_t tmem = s_tmem, mbar = tc_smem_u32(&s_mbar);
+    uint32_t phase = 0;
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
+        tc_node<K>(A, li, smem_tc, ts, tmem, mbar, phase);
+        if (ts.abort) break;
+    }
+    tc_teardown(tmem, mbar, ts);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -789,124 +819,139 @@ template <int P> struct InvCfg {
     static_assert(LDM % 4 == 2 && LDM >= WC, "row stride");
 };
 
-template <int K>
-__global__ void __launch_bounds__(InvCfg<p_of_k(K)>::NT) k_mixed_invert(MixedArgs A)
+// Shared memory of the inversion for matrices of up to PM rows and NWB warps per CTA.
+template <int PM, int NWB> struct InvShared {
+    df m[PM * InvCfg<PM>::LDM];
+    df prow[InvCfg<PM>::WC];
+    df pcol[PM];
+    float best[NWB];
+    int br[NWB];
+    int src[PM];
+    signed char piv[PM];
+};
+
+// M^-1 of list entry li at order K by a CTA of NTB threads (at least InvCfg<p>::NT).
+template <int K, int NTB, class SH>
+__device__ __forceinline__ void invert_node(const MixedArgs &A, int64_t li, SH &sh)
 {
-    using C = MCfg<K>;
-    constexpr int P = C::P;
+    constexpr int P = p_of_k(K);
     using I = InvCfg<P>;
-    constexpr int HALF = I::HALF, WC = I::WC, LDM = I::LDM, NT = I::NT, NW = I::NW;
-    __shared__ df s_m[P * LDM];
-    __shared__ df s_prow[WC];
-    __shared__ df s_pcol[P];
-    __shared__ float s_best[NW];
-    __shared__ int s_br[NW];
-    __shared__ int s_src[P];
-    __shared__ signed char s_piv[P];
+    constexpr int HALF = I::HALF, WC = I::WC, LDM = I::LDM, NW = NTB / 32;
+    static_assert(NTB >= I::NT && NTB % 32 == 0, "two threads per row, whole warps");
+    df *s_m = sh.m, *s_prow = sh.prow, *s_pcol = sh.pcol;
+    float *s_best = sh.best;
+    int *s_br = sh.br, *s_src = sh.src;
+    signed char *s_piv = sh.piv;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int r = t >> 1, hf = t & 1;
     const bool own = r < P;
 
-    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
-        if (A.flag[li] != 0) continue;  // uniform per CTA
-        const df *Mg = A.Mg + li * (int64_t)P * P;
-        for (int u = t; u < P * P; u += NT) {
-            const int rr = u / P;
-            s_m[rr * LDM + (u - rr * P)] = Mg[u];
+    if (A.flag[li] != 0) return;  // uniform per CTA
+    const df *Mg = A.Mg + li * A.mstride;
+    for (int u = t; u < P * P; u += NTB) {
+        const int rr = u / P;
+        s_m[rr * LDM + (u - rr * P)] = Mg[u];
+    }
+    if (WC > P)
+        for (int rr = t; rr < P; rr += NTB) s_m[rr * LDM + P] = df{0.0f, 0.0f};
+    __syncthreads();
+    bool zero = false;
+    for (int c = 0; c < P; c++) {
+        float best = (own && hf == 0 && r >= c) ? fabsf(s_m[r * LDM + c].hi) : -1.0f;
+        int br = own ? r : P;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+            if (ob > best || (ob == best && orr < br)) {
+                best = ob;
+                br = orr;
+            }
         }
-        if (WC > P)
-            for (int rr = t; rr < P; rr += NT) s_m[rr * LDM + P] = df{0.0f, 0.0f};
+        if (lane == 0) {
+            s_best[warp] = best;
+            s_br[warp] = br;
+        }
         __syncthreads();
-        bool zero = false;
-        for (int c = 0; c < P; c++) {
-            float best = (own && hf == 0 && r >= c) ? fabsf(s_m[r * LDM + c].hi) : -1.0f;
-            int br = own ? r : P;
+        best = s_best[0];
+        br = s_br[0];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ob > best || (ob == best && orr < br)) {
-                    best = ob;
-                    br = orr;
-                }
+        for (int w = 1; w < NW; w++)
+            if (s_best[w] > best) {  // later warps hold higher rows: strict keeps the lowest
+                best = s_best[w];
+                br = s_br[w];
             }
-            if (lane == 0) {
-                s_best[warp] = best;
-                s_br[warp] = br;
-            }
-            __syncthreads();
-            best = s_best[0];
-            br = s_br[0];
-#pragma unroll
-            for (int w = 1; w < NW; w++)
-                if (s_best[w] > best) {  // later warps hold higher rows: strict keeps the lowest
-                    best = s_best[w];
-                    br = s_br[w];
-                }
-            if (!(best > 0.0f) || !isfinite(best)) {
-                zero = true;
-                break;
-            }
-            // best > 0 comes from an even lane of a row r >= c, so c <= br < P
-            if (t == 0) s_piv[c] = (signed char)br;
-            if (t < WC) {  // column t: exchange rows c and br, publish the pivot row
-                const df a = s_m[c * LDM + t], b = s_m[br * LDM + t];
-                s_prow[t] = b;
-                if (br != c) {
-                    s_m[c * LDM + t] = b;
-                    s_m[br * LDM + t] = a;
-                }
-                // row t's entry of the pivot column after the exchange (rows c and br from the
-                // values this thread just read when t == c; other rows are not being written)
-                if (t == c) {
-                    s_pcol[c] = b;
-                    if (br != c) s_pcol[br] = a;
-                } else if (t < P && t != br) {
-                    s_pcol[t] = s_m[t * LDM + c];
-                }
-            }
-            __syncthreads();
-            const df inv = df_recip(s_prow[c]);
-            if (own) {
-                df *row = s_m + r * LDM + hf;  // this thread's columns: row[2 q]
-                const bool mine = (c & 1) == hf;
-                if (r == c) {
-#pragma unroll
-                    for (int q = 0; q < HALF; q++) row[2 * q] = df_mul(row[2 * q], inv);
-                    if (mine) row[c - hf] = inv;
-                } else {
-                    const df f = df_mul(s_pcol[r], inv);
-                    const df *pr = s_prow + hf;
-#pragma unroll
-                    for (int q = 0; q < HALF; q++) row[2 * q] = df_fms(f, pr[2 * q], row[2 * q]);
-                    if (mine) row[c - hf] = df_neg(f);
-                }
-            }
-            __syncthreads();
+        if (!(best > 0.0f) || !isfinite(best)) {
+            zero = true;
+            break;
         }
-        if (zero) {
-            if (t == 0) A.flag[li] = 1;
-            __syncthreads();
-            continue;
-        }
-        // column order of the result: undo the interchanges, last first
-        if (t == 0) {
-            for (int q = 0; q < P; q++) s_src[q] = q;
-            for (int c = P - 1; c >= 0; c--) {
-                const int pr = s_piv[c];
-                const int a = s_src[c];
-                s_src[c] = s_src[pr];
-                s_src[pr] = a;
+        // best > 0 comes from an even lane of a row r >= c, so c <= br < P
+        if (t == 0) s_piv[c] = (signed char)br;
+        if (t < WC) {  // column t: exchange rows c and br, publish the pivot row
+            const df a = s_m[c * LDM + t], b = s_m[br * LDM + t];
+            s_prow[t] = b;
+            if (br != c) {
+                s_m[c * LDM + t] = b;
+                s_m[br * LDM + t] = a;
+            }
+            // row t's entry of the pivot column after the exchange (rows c and br from the
+            // values this thread just read when t == c; other rows are not being written)
+            if (t == c) {
+                s_pcol[c] = b;
+                if (br != c) s_pcol[br] = a;
+            } else if (t < P && t != br) {
+                s_pcol[t] = s_m[t * LDM + c];
             }
         }
         __syncthreads();
-        df *Mo = A.Mg + li * (int64_t)P * P;
-        for (int u = t; u < P * P; u += NT) {
-            const int rr = u / P, q = u - rr * P;
-            Mo[u] = s_m[rr * LDM + s_src[q]];
+        const df inv = df_recip(s_prow[c]);
+        if (own) {
+            df *row = s_m + r * LDM + hf;  // this thread's columns: row[2 q]
+            const bool mine = (c & 1) == hf;
+            if (r == c) {
+#pragma unroll
+                for (int q = 0; q < HALF; q++) row[2 * q] = df_mul(row[2 * q], inv);
+                if (mine) row[c - hf] = inv;
+            } else {
+                const df f = df_mul(s_pcol[r], inv);
+                const df *pr = s_prow + hf;
+#pragma unroll
+                for (int q = 0; q < HALF; q++) row[2 * q] = df_fms(f, pr[2 * q], row[2 * q]);
+                if (mine) row[c - hf] = df_neg(f);
+            }
         }
         __syncthreads();
     }
+    if (zero) {
+        if (t == 0) A.flag[li] = 1;
+        __syncthreads();
+        return;
+    }
+    // column order of the result: undo the interchanges, last first
+    if (t == 0) {
+        for (int q = 0; q < P; q++) s_src[q] = q;
+        for (int c = P - 1; c >= 0; c--) {
+            const int pr = s_piv[c];
+            const int a = s_src[c];
+            s_src[c] = s_src[pr];
+            s_src[pr] = a;
+        }
+    }
+    __syncthreads();
+    df *Mo = A.Mg + li * A.mstride;
+    for (int u = t; u < P * P; u += NTB) {
+        const int rr = u / P, q = u - rr * P;
+        Mo[u] = s_m[rr * LDM + s_src[q]];
+    }
+    __syncthreads();
+}
+
+template <int K>
+__global__ void __launch_bounds__(InvCfg<p_of_k(K)>::NT) k_mixed_invert(MixedArgs A)
+{
+    using I = InvCfg<p_of_k(K)>;
+    __shared__ InvShared<p_of_k(K), I::NW> sh;
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) invert_node<K, I::NT>(A, li, sh);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -947,12 +992,21 @@ __device__ __forceinline__ int refine_decision(int it, int nmax, int n_ops, cons
     return it < nmax ? 1 : 0;
 }
 
+// Per-node shared state of the weights kernel.
+struct WShared {
+    double hneg[KMAX + 1], hpos[KMAX + 1];
+    double res[PMAX * MAX_OPS];
+    float dw2[MAX_OPS], w2[MAX_OPS];  // per operator: sum of dw^2 and of w^2 over the stencil
+    float eta;
+    int flag, go;
+};
+
+// Weights of list entry li at order K (dynamic shared memory of MCfg<K>::smemC bytes).
 template <int K>
-__global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
+__device__ __forceinline__ void weights_node(const MixedArgs &A, int64_t li, double *smem_d, WShared &ws)
 {
     using C = MCfg<K>;
     constexpr int P = C::P, LDX = C::LDX, NB = C::NB;
-    extern __shared__ __align__(16) double smem_d[];
     double *Xd = smem_d;                                     // [NB][LDX]
     df *Wf = reinterpret_cast<df *>(Xd + NB * LDX);          // [NB][LDX]
     df *Nrec = Wf + NB * LDX;                                // [NB][NREC]
@@ -960,222 +1014,227 @@ __global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
     df *Psi = Rhs + P * MAX_OPS;                             // [P][MAX_OPS]
     double *Wt = reinterpret_cast<double *>(Psi + P * MAX_OPS);  // [NB][MAX_OPS] w~ of the chunk
     float *Vt = reinterpret_cast<float *>(Wt + NB * MAX_OPS);    // [NB][MAX_OPS] the last correction of w~
-    __shared__ double s_hneg[KMAX + 1], s_hpos[KMAX + 1];
-    __shared__ double s_res[PMAX * MAX_OPS];
-    __shared__ float s_dw2[MAX_OPS], s_w2[MAX_OPS];  // per operator: sum of dw^2 and of w^2 over the stencil
-    __shared__ float s_eta;
-    __shared__ int s_flag, s_go;
+    double *s_hneg = ws.hneg, *s_hpos = ws.hpos, *s_res = ws.res;
+    float *s_dw2 = ws.dw2, *s_w2 = ws.w2;
+    float &s_eta = ws.eta;
+    int &s_flag = ws.flag, &s_go = ws.go;
     const int tid = threadIdx.x;
     const int n_ops = A.n_ops;
 
-    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) {
-        const int64_t i = node_of(A, li);
-        const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
-        const int ni = (int)(re - rs);
-        const int fl = A.flag[li];
-        if (fl & 8) {  // undersampled: weights already zeroed by kernel A
-            if (tid == 0) {
-                if (A.node_status) A.node_status[i] = LABFM_NODE_UNDERSAMPLED;
-                atomicAdd(A.n_bad, 1ull);
-            }
-            continue;
-        }
-        if (fl != 0) {
-            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
-                if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
-                else ((float *)A.w)[rs * n_ops + t] = 0.0f;
-            }
-            if (tid == 0) {
-                if (A.node_status) A.node_status[i] = (fl & 4) ? LABFM_NODE_NONFINITE : LABFM_NODE_SINGULAR;
-                atomicAdd(A.n_bad, 1ull);
-            }
-            continue;
-        }
-        const double hi = A.h[i];
-        const double ihi = 1.0 / hi;
+    const int64_t i = node_of(A, li);
+    const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
+    const int ni = (int)(re - rs);
+    const int fl = A.flag[li];
+    if (fl & 8) {  // undersampled: weights already zeroed by kernel A
         if (tid == 0) {
-            double s = 1.0, t = 1.0;
-            for (int q = 0; q <= KMAX; q++) {
-                s_hneg[q] = s;
-                s_hpos[q] = t;
-                s *= ihi;
-                t *= hi;
-            }
-            s_flag = 0;
+            if (A.node_status) A.node_status[i] = LABFM_NODE_UNDERSAMPLED;
+            atomicAdd(A.n_bad, 1ull);
         }
-        const df *__restrict__ Mi = A.Mg + li * (int64_t)P * P;  // M^-1 of the node (global)
-        __syncthreads();
-        // scaled targets C~_alpha = C_alpha h^(l_d - |alpha|)
+        return;
+    }
+    if (fl != 0) {
+        for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
+            if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
+            else ((float *)A.w)[rs * n_ops + t] = 0.0f;
+        }
+        if (tid == 0) {
+            if (A.node_status) A.node_status[i] = (fl & 4) ? LABFM_NODE_NONFINITE : LABFM_NODE_SINGULAR;
+            atomicAdd(A.n_bad, 1ull);
+        }
+        return;
+    }
+    const double hi = A.h[i];
+    const double ihi = 1.0 / hi;
+    if (tid == 0) {
+        double s = 1.0, t = 1.0;
+        for (int q = 0; q <= KMAX; q++) {
+            s_hneg[q] = s;
+            s_hpos[q] = t;
+            s *= ihi;
+            t *= hi;
+        }
+        s_flag = 0;
+    }
+    const df *__restrict__ Mi = A.Mg + li * A.mstride;  // M^-1 of the node (global)
+    __syncthreads();
+    // scaled targets C~_alpha = C_alpha h^(l_d - |alpha|)
+    for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
+        int m = t / n_ops, d = t % n_ops;
+        int deg = elem_degree(m), l = A.lmax[d];
+        double sc = l >= deg ? s_hpos[l - deg] : s_hneg[deg - l];
+        s_res[m * MAX_OPS + d] = A.C[d * PMAX + m] * sc;
+        Rhs[m * MAX_OPS + d] = df_from_double(s_res[m * MAX_OPS + d]);
+    }
+    const int nchunks = (ni + NB - 1) / NB;
+    if (nchunks == 1) stage_chunk<K>(A, rs, 0, ni, Xd, nullptr, Wf, Nrec);
+    else __syncthreads();
+
+    float eta_prev = 1.0f;
+    int go = 1;
+    int it = 0;
+    for (;; it++) {
+        // Psi (or its correction) = M^-1 Rhs, thread per (m, d)
+        for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
+            int m = t / n_ops, d = t % n_ops;
+            df s0 = df{0.0f, 0.0f}, s1 = s0;
+            const df *row = Mi + m * P;
+            int q = 0;
+            for (; q + 1 < P; q += 2) {
+                s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
+                s1 = df_fma(row[q + 1], Rhs[(q + 1) * MAX_OPS + d], s1);
+            }
+            if (q < P) s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
+            Psi[m * MAX_OPS + d] = df_add(s0, s1);
+        }
+        // w~ (+)= W . Psi over the chunks; the residual r = C~ - sum_j X_j w~_j accumulates
         for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
             int m = t / n_ops, d = t % n_ops;
             int deg = elem_degree(m), l = A.lmax[d];
             double sc = l >= deg ? s_hpos[l - deg] : s_hneg[deg - l];
             s_res[m * MAX_OPS + d] = A.C[d * PMAX + m] * sc;
-            Rhs[m * MAX_OPS + d] = df_from_double(s_res[m * MAX_OPS + d]);
         }
-        const int nchunks = (ni + NB - 1) / NB;
-        if (nchunks == 1) stage_chunk<K>(A, rs, 0, ni, Xd, nullptr, Wf, Nrec);
-        else __syncthreads();
-
-        float eta_prev = 1.0f;
-        int go = 1;
-        int it = 0;
-        for (;; it++) {
-            // Psi (or its correction) = M^-1 Rhs, thread per (m, d)
-            for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
-                int m = t / n_ops, d = t % n_ops;
-                df s0 = df{0.0f, 0.0f}, s1 = s0;
-                const df *row = Mi + m * P;
-                int q = 0;
-                for (; q + 1 < P; q += 2) {
-                    s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
-                    s1 = df_fma(row[q + 1], Rhs[(q + 1) * MAX_OPS + d], s1);
-                }
-                if (q < P) s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
-                Psi[m * MAX_OPS + d] = df_add(s0, s1);
-            }
-            // w~ (+)= W . Psi over the chunks; the residual r = C~ - sum_j X_j w~_j accumulates
-            for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
-                int m = t / n_ops, d = t % n_ops;
-                int deg = elem_degree(m), l = A.lmax[d];
-                double sc = l >= deg ? s_hpos[l - deg] : s_hneg[deg - l];
-                s_res[m * MAX_OPS + d] = A.C[d * PMAX + m] * sc;
-            }
-            if (tid < MAX_OPS) {
-                s_dw2[tid] = 0.0f;
-                s_w2[tid] = 0.0f;
-            }
-            __syncthreads();
-            for (int ch = 0; ch < nchunks; ch++) {
-                const int j0 = ch * NB, nj = min(NB, ni - j0);
-                if (nchunks > 1) stage_chunk<K>(A, rs, j0, nj, Xd, nullptr, Wf, Nrec);
-                for (int t = tid; t < nj * n_ops; t += MIX_THREADS) {
-                    int j = t / n_ops, d = t % n_ops;
-                    df s0 = df{0.0f, 0.0f}, s1 = s0;
-                    const df *W = Wf + j * LDX;
-                    int m = 0;
-                    for (; m + 1 < P; m += 2) {
-                        s0 = df_fma(W[m], Psi[m * MAX_OPS + d], s0);
-                        s1 = df_fma(W[m + 1], Psi[(m + 1) * MAX_OPS + d], s1);
-                    }
-                    if (m < P) s0 = df_fma(W[m], Psi[m * MAX_OPS + d], s0);
-                    const double v = df_to_double(df_add(s0, s1));
-                    const int64_t idx = (rs + j0 + j) * n_ops + d;
-                    const double wv = it == 0 ? v : A.wt[idx] + v;
-                    A.wt[idx] = wv;
-                    Wt[j * MAX_OPS + d] = wv;
-                    Vt[j * MAX_OPS + d] = (float)v;
-                }
-                __syncthreads();
-                if (A.adaptive) {
-                    // per operator (warp d): the chunk's sums of dw^2 and w^2, in float
-                    const int wp = tid >> 5, ln = tid & 31;
-                    if (wp < n_ops) {
-                        float a2 = 0.0f, b2 = 0.0f;
-                        for (int j = ln; j < nj; j += 32) {
-                            const float vf = Vt[j * MAX_OPS + wp], wf = (float)Wt[j * MAX_OPS + wp];
-                            a2 = fmaf(vf, vf, a2);
-                            b2 = fmaf(wf, wf, b2);
-                        }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-                            b2 += __shfl_xor_sync(0xffffffffu, b2, o);
-                        }
-                        if (ln == 0) {
-                            s_dw2[wp] += a2;
-                            s_w2[wp] += b2;
-                        }
-                    }
-                    __syncthreads();
-                }
-                // the residual of this pass is needed only if another step follows; with one
-                // chunk the adaptive decision is known here, before the residual is formed
-                bool res;
-                if (!A.adaptive) {
-                    res = it < A.nref;
-                } else if (nchunks == 1) {
-                    if (tid == 0) {
-                        float eta;
-                        s_go = refine_decision(it, A.nref, n_ops, s_dw2, s_w2, eta_prev, eta);
-                        s_eta = eta;
-                    }
-                    __syncthreads();
-                    res = s_go == 1;
-                } else {
-                    res = it < A.nref;
-                }
-                if (res) {
-                    for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
-                        int m = t / n_ops, d = t % n_ops;
-                        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                        int j = 0;
-                        for (; j + 3 < nj; j += 4) {
-                            s0 = fma(Xd[j * LDX + m], Wt[j * MAX_OPS + d], s0);
-                            s1 = fma(Xd[(j + 1) * LDX + m], Wt[(j + 1) * MAX_OPS + d], s1);
-                            s2 = fma(Xd[(j + 2) * LDX + m], Wt[(j + 2) * MAX_OPS + d], s2);
-                            s3 = fma(Xd[(j + 3) * LDX + m], Wt[(j + 3) * MAX_OPS + d], s3);
-                        }
-                        for (; j < nj; j++) s0 = fma(Xd[j * LDX + m], Wt[j * MAX_OPS + d], s0);
-                        s_res[m * MAX_OPS + d] -= (s0 + s1) + (s2 + s3);
-                    }
-                }
-                __syncthreads();
-            }
-            if (A.adaptive) {
-                if (nchunks > 1) {
-                    if (tid == 0) {
-                        float eta;
-                        s_go = refine_decision(it, A.nref, n_ops, s_dw2, s_w2, eta_prev, eta);
-                        s_eta = eta;
-                    }
-                    __syncthreads();
-                }
-                go = s_go;
-                eta_prev = s_eta;
-                if (go != 1) break;
-            } else if (it == A.nref) {
-                break;
-            }
-            for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
-                int m = t / n_ops, d = t % n_ops;
-                Rhs[m * MAX_OPS + d] = df_from_double(s_res[m * MAX_OPS + d]);
-            }
-            __syncthreads();
-        }
-        if (tid == 0 && A.ref_hist) atomicAdd(&A.ref_hist[min(it, NREF_MAX)], 1ull);
-        if (go == 2) {
-            // the corrections grew: the FP64 build redoes this node (weights and status)
-            if (tid == 0) A.fb_list[atomicAdd(A.fb_count, 1ull)] = (int32_t)i;
-            __syncthreads();
-            continue;
-        }
-
-        // physical weights w = h^-l_d w~
-        for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
-            int d = (int)(t % n_ops);
-            double v = A.wt[rs * n_ops + t] * s_hneg[A.lmax[d]];
-            if (!isfinite(v)) {
-                atomicOr(&s_flag, 2);
-                v = 0.0;
-            }
-            if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = v;
-            else ((float *)A.w)[rs * n_ops + t] = (float)v;
+        if (tid < MAX_OPS) {
+            s_dw2[tid] = 0.0f;
+            s_w2[tid] = 0.0f;
         }
         __syncthreads();
-        if (s_flag & 2) {
-            for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
-                if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
-                else ((float *)A.w)[rs * n_ops + t] = 0.0f;
+        for (int ch = 0; ch < nchunks; ch++) {
+            const int j0 = ch * NB, nj = min(NB, ni - j0);
+            if (nchunks > 1) stage_chunk<K>(A, rs, j0, nj, Xd, nullptr, Wf, Nrec);
+            for (int t = tid; t < nj * n_ops; t += MIX_THREADS) {
+                int j = t / n_ops, d = t % n_ops;
+                df s0 = df{0.0f, 0.0f}, s1 = s0;
+                const df *W = Wf + j * LDX;
+                int m = 0;
+                for (; m + 1 < P; m += 2) {
+                    s0 = df_fma(W[m], Psi[m * MAX_OPS + d], s0);
+                    s1 = df_fma(W[m + 1], Psi[(m + 1) * MAX_OPS + d], s1);
+                }
+                if (m < P) s0 = df_fma(W[m], Psi[m * MAX_OPS + d], s0);
+                const double v = df_to_double(df_add(s0, s1));
+                const int64_t idx = (rs + j0 + j) * n_ops + d;
+                const double wv = it == 0 ? v : A.wt[idx] + v;
+                A.wt[idx] = wv;
+                Wt[j * MAX_OPS + d] = wv;
+                Vt[j * MAX_OPS + d] = (float)v;
             }
+            __syncthreads();
+            if (A.adaptive) {
+                // per operator (warp d): the chunk's sums of dw^2 and w^2, in float
+                const int wp = tid >> 5, ln = tid & 31;
+                if (wp < n_ops) {
+                    float a2 = 0.0f, b2 = 0.0f;
+                    for (int j = ln; j < nj; j += 32) {
+                        const float vf = Vt[j * MAX_OPS + wp], wf = (float)Wt[j * MAX_OPS + wp];
+                        a2 = fmaf(vf, vf, a2);
+                        b2 = fmaf(wf, wf, b2);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+                    }
+                    if (ln == 0) {
+                        s_dw2[wp] += a2;
+                        s_w2[wp] += b2;
+                    }
+                }
+                __syncthreads();
+            }
+            // the residual of this pass is needed only if another step follows; with one
+            // chunk the adaptive decision is known here, before the residual is formed
+            bool res;
+            if (!A.adaptive) {
+                res = it < A.nref;
+            } else if (nchunks == 1) {
+                if (tid == 0) {
+                    float eta;
+                    s_go = refine_decision(it, A.nref, n_ops, s_dw2, s_w2, eta_prev, eta);
+                    s_eta = eta;
+                }
+                __syncthreads();
+                res = s_go == 1;
+            } else {
+                res = it < A.nref;
+            }
+            if (res) {
+                for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
+                    int m = t / n_ops, d = t % n_ops;
+                    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                    int j = 0;
+                    for (; j + 3 < nj; j += 4) {
+                        s0 = fma(Xd[j * LDX + m], Wt[j * MAX_OPS + d], s0);
+                        s1 = fma(Xd[(j + 1) * LDX + m], Wt[(j + 1) * MAX_OPS + d], s1);
+                        s2 = fma(Xd[(j + 2) * LDX + m], Wt[(j + 2) * MAX_OPS + d], s2);
+                        s3 = fma(Xd[(j + 3) * LDX + m], Wt[(j + 3) * MAX_OPS + d], s3);
+                    }
+                    for (; j < nj; j++) s0 = fma(Xd[j * LDX + m], Wt[j * MAX_OPS + d], s0);
+                    s_res[m * MAX_OPS + d] -= (s0 + s1) + (s2 + s3);
+                }
+            }
+            __syncthreads();
         }
-        if (tid == 0) {
-            const int st = (s_flag & 2) ? LABFM_NODE_NONFINITE : LABFM_NODE_OK;
-            if (A.node_status) A.node_status[i] = st;
-            if (st != LABFM_NODE_OK) atomicAdd(A.n_bad, 1ull);
+        if (A.adaptive) {
+            if (nchunks > 1) {
+                if (tid == 0) {
+                    float eta;
+                    s_go = refine_decision(it, A.nref, n_ops, s_dw2, s_w2, eta_prev, eta);
+                    s_eta = eta;
+                }
+                __syncthreads();
+            }
+            go = s_go;
+            eta_prev = s_eta;
+            if (go != 1) break;
+        } else if (it == A.nref) {
+            break;
+        }
+        for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
+            int m = t / n_ops, d = t % n_ops;
+            Rhs[m * MAX_OPS + d] = df_from_double(s_res[m * MAX_OPS + d]);
         }
         __syncthreads();
     }
+    if (tid == 0 && A.ref_hist) atomicAdd(&A.ref_hist[min(it, NREF_MAX)], 1ull);
+    if (go == 2) {
+        // the corrections grew: the FP64 build redoes this node (weights and status)
+        if (tid == 0) A.fb_list[atomicAdd(A.fb_count, 1ull)] = (int32_t)i;
+        __syncthreads();
+        return;
+    }
+
+    // physical weights w = h^-l_d w~
+    for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
+        int d = (int)(t % n_ops);
+        double v = A.wt[rs * n_ops + t] * s_hneg[A.lmax[d]];
+        if (!isfinite(v)) {
+            atomicOr(&s_flag, 2);
+            v = 0.0;
+        }
+        if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = v;
+        else ((float *)A.w)[rs * n_ops + t] = (float)v;
+    }
+    __syncthreads();
+    if (s_flag & 2) {
+        for (int64_t t = tid; t < (int64_t)ni * n_ops; t += MIX_THREADS) {
+            if (A.wdtype == LABFM_F64) ((double *)A.w)[rs * n_ops + t] = 0.0;
+            else ((float *)A.w)[rs * n_ops + t] = 0.0f;
+        }
+    }
+    if (tid == 0) {
+        const int st = (s_flag & 2) ? LABFM_NODE_NONFINITE : LABFM_NODE_OK;
+        if (A.node_status) A.node_status[i] = st;
+        if (st != LABFM_NODE_OK) atomicAdd(A.n_bad, 1ull);
+    }
+    __syncthreads();
+}
+
+template <int K>
+__global__ void __launch_bounds__(MIX_THREADS, 3) k_mixed_weights(MixedArgs A)
+{
+    extern __shared__ __align__(16) double smem_d[];
+    __shared__ WShared ws;
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) weights_node<K>(A, li, smem_d, ws);
 }
 
 template <class KernelT>
@@ -1195,50 +1254,44 @@ cudaError_t launch_persistent(KernelT kern, const MixedArgs &a, int threads, siz
     return cudaGetLastError();
 }
 
+cudaError_t launch_records(const MixedArgs &a, int num_sms, cudaStream_t s)
+{
+    const int64_t blocks = std::min<int64_t>((a.n_list + 7) / 8, (int64_t)num_sms * 16);
+    if (blocks > 0) k_mixed_records<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// two CTAs per SM, each holding TC_TMEM_COLS of the 512 tensor-memory columns for its whole run:
+// the shared-memory request (>= 80 KB, <= 113 KB) keeps a third CTA off the SM
+template <class KernelT>
+cudaError_t launch_tc(KernelT kern, const MixedArgs &a, size_t smem_needed, int num_sms, cudaStream_t s)
+{
+    const size_t smem = std::max<size_t>(smem_needed, 80 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(a.n_list, 2 * (int64_t)num_sms);
+    if (grid > 0) kern<<<(unsigned)grid, TC_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, bool tc, cudaStream_t s)
 {
     using C = MCfg<K>;
-    {
-        int64_t blocks = std::min<int64_t>((a.n_list + 7) / 8, (int64_t)num_sms * 16);
-        if (blocks > 0) k_mixed_records<<<(unsigned)blocks, 256, 0, s>>>(a);
-        cudaError_t e0 = cudaGetLastError();
-        if (e0 != cudaSuccess) return e0;
-    }
-    cudaError_t e;
-    if (tc) {
-        // two CTAs per SM, each holding TC_TMEM_COLS of the 512 tensor-memory columns for its
-        // whole run: the shared-memory request (>= 80 KB) keeps a third CTA off the SM
-        const size_t smem = std::max<size_t>(TcCfg<K>::smem, 80 * 1024);
-        e = cudaFuncSetAttribute(k_mixed_assemble_tc<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_mixed_assemble_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        // two CTAs per SM by construction (<= 113 KB of shared memory and 32 K registers each)
-        const int64_t grid = std::min<int64_t>(a.n_list, 2 * (int64_t)num_sms);
-        if (grid > 0) k_mixed_assemble_tc<K><<<(unsigned)grid, TC_THREADS, smem, s>>>(a);
-        e = cudaGetLastError();
-    } else {
-        e = launch_persistent(k_mixed_assemble<K>, a, MIX_THREADS, C::smemA, a.n_list, num_sms, s);
-    }
+    cudaError_t e = launch_records(a, num_sms, s);
+    if (e != cudaSuccess) return e;
+    if (tc) e = launch_tc(k_mixed_assemble_tc<K>, a, TcCfg<K>::smem, num_sms, s);
+    else e = launch_persistent(k_mixed_assemble<K>, a, MIX_THREADS, C::smemA, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
     e = launch_persistent(k_mixed_invert<K>, a, InvCfg<C::P>::NT, 0, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
     return launch_persistent(k_mixed_weights<K>, a, MIX_THREADS, C::smemC, a.n_list, num_sms, s);
 }
 
-}  // namespace
-
-size_t mixed_record_bytes() { return sizeof(Rec); }
-
-size_t mixed_scratch_bytes_per_node(int k)
-{
-    const int p = p_of_k(k);
-    return sizeof(df) * (size_t)p * p + sizeof(int);
-}
-
-cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
+MixedArgs make_args(const MixedArgsPublic &p)
 {
     MixedArgs a{};
     a.xy = p.xy;
@@ -1267,7 +1320,26 @@ cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
     a.wstore = reinterpret_cast<df *>(p.wstore);
     for (int d = 0; d < MAX_OPS; d++) a.lmax[d] = p.lmax[d];
     for (int t = 0; t < MAX_OPS * PMAX; t++) a.C[t] = p.C[t];
+    return a;
+}
+
+}  // namespace
+
+size_t mixed_record_bytes() { return sizeof(Rec); }
+
+size_t mixed_scratch_bytes_per_node(int k)
+{
+    const int p = p_of_k(k);
+    return sizeof(df) * (size_t)p * p + sizeof(int);
+}
+
+cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
+{
+    if (k < MIXED_MIN_ORDER || k > KMAX) return cudaErrorInvalidValue;
+    MixedArgs a = make_args(p);
     const int pk = p_of_k(k);
+    a.mstride = (int64_t)pk * pk;
+    a.wstride = pk;
     // scratch holds batch_nodes matrices; the node list is processed batch by batch
     const int64_t batch = p.batch_nodes;
     for (int64_t b0 = 0; b0 < p.n_list; b0 += batch) {
@@ -1275,13 +1347,9 @@ cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
         a.list = p.list ? p.list + b0 : nullptr;
         a.list_base = p.list ? 0 : b0;
         a.Mg = reinterpret_cast<df *>(p.scratch);
-        a.flag = reinterpret_cast<int *>(reinterpret_cast<char *>(p.scratch) + sizeof(df) * (size_t)pk * pk * batch);
+        a.flag = reinterpret_cast<int *>(reinterpret_cast<char *>(p.scratch) + sizeof(df) * (size_t)a.mstride * batch);
         cudaError_t e;
         switch (k) {
-        case 1: e = launch_mixed_k<1>(a, p.num_sms, p.tc != 0, s); break;
-        case 2: e = launch_mixed_k<2>(a, p.num_sms, p.tc != 0, s); break;
-        case 3: e = launch_mixed_k<3>(a, p.num_sms, p.tc != 0, s); break;
-        case 4: e = launch_mixed_k<4>(a, p.num_sms, p.tc != 0, s); break;
         case 5: e = launch_mixed_k<5>(a, p.num_sms, p.tc != 0, s); break;
         case 6: e = launch_mixed_k<6>(a, p.num_sms, p.tc != 0, s); break;
         case 7: e = launch_mixed_k<7>(a, p.num_sms, p.tc != 0, s); break;

@@ -14,6 +14,9 @@ namespace labfm {
 constexpr int KMAX = LABFM_MAX_ORDER;
 constexpr int PMAX = LABFM_PMAX;
 constexpr int MAX_OPS = LABFM_MAX_OPS;
+// Lowest order a mixed-precision build runs through the mixed kernels; lower orders go to the
+// FP64 kernel (small, well conditioned systems: faster there, and exact to the FP64 floor).
+constexpr int MIXED_MIN_ORDER = 5;
 
 __host__ __device__ constexpr int p_of_k(int k) { return (k * k + 3 * k) / 2; }
 
@@ -144,6 +147,7 @@ struct MixedArgsPublic {
     unsigned long long *tc_timeout;  // device counter of tensor-core waits that gave up
     void *wstore;  // [nnz][p(k)] double-float W kept between the assembly and the weights, or null
 };
+// The mixed build of the listed nodes, all at order k (MIXED_MIN_ORDER <= k <= KMAX).
 cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s);
 size_t mixed_scratch_bytes_per_node(int k);
 size_t mixed_record_bytes();
