@@ -41,11 +41,11 @@ struct NodeShared {
 
 // The CTA's dynamic shared memory: that of one order-8 node (72-neighbour chunks), so that four
 // CTAs fit an SM; a CTA of NG = 256 / G groups gives each group a 1/NG share.
-constexpr size_t SMEM_CTA = (sizeof(double) * ((size_t)2 * 72 * 44) + sizeof(NodeShared) + 15) / 16 * 16;
+constexpr size_t SMEM_CTA = (sizeof(double) * ((size_t)2 * 72 * 45) + sizeof(NodeShared) + 15) / 16 * 16;
 
 template <int K, int G> struct Cfg {
     static constexpr int P = p_of_k(K);
-    static constexpr int LDX = (P + 3) / 4 * 4;
+    static constexpr int LDX = (P + 3) / 4 * 4 + 1;  // odd: rows of consecutive neighbours on distinct banks
     static constexpr int NG = BUILD_THREADS / G;  // nodes per CTA
     static_assert(G % 32 == 0 && BUILD_THREADS % G == 0, "groups of whole warps");
     // neighbours per staged chunk: what the group's share of the CTA's shared memory holds, <= 72
@@ -185,12 +185,8 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                     double xv[TM], wv[TN];
 #pragma unroll
                     for (int a = 0; a < TM; a++) xv[a] = X[a];
-                    double2 w01 = *reinterpret_cast<const double2 *>(W);
-                    double2 w23 = *reinterpret_cast<const double2 *>(W + 2);
-                    wv[0] = w01.x;
-                    wv[1] = w01.y;
-                    wv[2] = w23.x;
-                    wv[3] = w23.y;
+#pragma unroll
+                    for (int b = 0; b < TN; b++) wv[b] = W[b];
 #pragma unroll
                     for (int a = 0; a < TM; a++)
 #pragma unroll
