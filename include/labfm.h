@@ -196,6 +196,10 @@ typedef struct {
     /* per order k (index 1..8): threads that built one node in the FP64 kernel (64, 128: several
      * nodes per CTA; 256: one), as the build autotuner chose them; 0 for orders not built there */
     int32_t fp64_group_threads[LABFM_MAX_ORDER + 1];
+    /* per order k (index 1..8): threads per matrix row (2 or 4) of the mixed builds' double-float
+     * inversion, as the build autotuner chose them (timed once per (order, mean stencil size,
+     * n_ops, precision) like the FP64 group size); 0 for orders not built by the mixed kernels */
+    int32_t mixed_inv_threads_per_row[LABFM_MAX_ORDER + 1];
 } labfm_build_info;
 
 /* Copy the statistics of the last weight build into *info.  LABFM_ERR_STATE before a build. */

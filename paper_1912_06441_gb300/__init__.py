@@ -100,7 +100,8 @@ def load_library(path: str | None = None, build_if_missing: bool = False):
 
 class _BuildInfo(ct.Structure):
     """labfm_build_info"""
-    _fields_ = [("refine_steps", ct.c_int64 * 8), ("fp64_rebuilt", ct.c_int64), ("fp64_group_threads", ct.c_int32 * 9)]
+    _fields_ = [("refine_steps", ct.c_int64 * 8), ("fp64_rebuilt", ct.c_int64), ("fp64_group_threads", ct.c_int32 * 9),
+                ("mixed_inv_threads_per_row", ct.c_int32 * 9)]
 
 
 class _DevView:
@@ -243,12 +244,15 @@ class Labfm:
     def get_build_info(self):
         """Statistics of the last weight build: {"refine_steps": [nodes taking 0..7 refinement
         steps], "fp64_rebuilt": nodes the FP64 build redid (mixed builds; zeros after FP64),
-        "fp64_group_threads": {order: threads per node of the FP64 kernel}}."""
+        "fp64_group_threads": {order: threads per node of the FP64 kernel},
+        "mixed_inv_threads_per_row": {order: threads per row of the mixed inversion}}."""
         info = _BuildInfo()
         self._check(self.lib.labfm_get_build_info(self._ctx, ct.byref(info)))
         return {"refine_steps": list(info.refine_steps), "fp64_rebuilt": int(info.fp64_rebuilt),
                 "fp64_group_threads": {k: int(info.fp64_group_threads[k]) for k in range(1, 9)
-                                       if info.fp64_group_threads[k]}}
+                                       if info.fp64_group_threads[k]},
+                "mixed_inv_threads_per_row": {k: int(info.mixed_inv_threads_per_row[k]) for k in range(1, 9)
+                                              if info.mixed_inv_threads_per_row[k]}}
 
     def get_weights(self):
         """Context-owned weights as a torch view [nnz, n_ops]."""

@@ -322,7 +322,10 @@ labfm_status labfm_get_build_info(labfm_ctx *ctx, labfm_build_info *info)
     if (!ctx->have_weights) return fail(ctx, LABFM_ERR_STATE, "no weights built");
     for (int t = 0; t < 8; t++) info->refine_steps[t] = ctx->info_ref_hist[t];
     info->fp64_rebuilt = ctx->info_fp64_rebuilt;
-    for (int k = 0; k <= LABFM_MAX_ORDER; k++) info->fp64_group_threads[k] = ctx->info_group[k];
+    for (int k = 0; k <= LABFM_MAX_ORDER; k++) {
+        info->fp64_group_threads[k] = ctx->info_group[k];
+        info->mixed_inv_threads_per_row[k] = ctx->info_inv_tpr[k];
+    }
     return LABFM_OK;
 }
 

@@ -544,7 +544,7 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
     unsigned int *d_cursor = d_hist + NBUCKET;
     LABFM_CUDA_TRY(ctx, cudaMemsetAsync(dmisc, 0, NMISC * sizeof(unsigned long long), s));
     for (int t = 0; t < 8; t++) ctx->info_ref_hist[t] = 0;
-    for (int t = 0; t <= KMAX; t++) ctx->info_group[t] = 0;
+    for (int t = 0; t <= KMAX; t++) ctx->info_group[t] = ctx->info_inv_tpr[t] = 0;
     ctx->info_fp64_rebuilt = 0;
 
     BuildArgs a{};
@@ -656,9 +656,10 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         return cudaSuccess;
     };
     // the mixed kernels over the listed nodes, all at order k
-    auto launch_mixed = [&](int k, const int32_t *list, int64_t n_list) -> cudaError_t {
+    auto launch_mixed_raw = [&](int k, const int32_t *list, int64_t n_list, int tpr) -> cudaError_t {
         m.list = list;
         m.n_list = n_list;
+        m.inv_tpr = tpr;
         bool adaptive = false;
         m.nref = precision_nref(precision, adaptive);
         m.adaptive = adaptive ? 1 : 0;
@@ -680,6 +681,57 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
             cudaGetLastError();  // a failed reservation only disables the store
         return launch_build_mixed(k, m, s);
     };
+    // Threads per row of the mixed inversion (2 or 4), timed once per (order, mean stencil size,
+    // n_ops, precision) on the whole mixed pipeline over up to 16,384 of the order's nodes (the
+    // timing runs' counters are cleared afterwards; their weights are overwritten by the build).
+    auto launch_mixed = [&](int k, const int32_t *list, int64_t cnt, double deg) -> cudaError_t {
+        int tpr = 2;
+        const uint64_t dkey = (uint64_t)std::min(deg + 0.5, 65535.0);
+        const uint64_t key = (dkey << 40) | ((uint64_t)k << 32) | (6ull << 24) | ((uint64_t)n_ops << 16) |
+                             ((uint64_t)base_prec << 8);
+        auto it = ctx->tuned.find(key);
+        cudaError_t e = cudaSuccess;
+        if (it != ctx->tuned.end()) {
+            tpr = (int)it->second;
+        } else {
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            e = cudaStreamIsCapturing(s, &cap);
+            if (e != cudaSuccess) return e;
+            if (cap == cudaStreamCaptureStatusNone && cnt >= 4096) {
+                cudaEvent_t e0, e1;
+                if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+                if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    return e;
+                }
+                const int64_t nt = std::min<int64_t>(cnt, 16384);
+                float best = 1e30f;
+                for (int cand = 2; cand <= 4 && e == cudaSuccess; cand += 2) {
+                    e = launch_mixed_raw(k, list, nt, cand);  // warm-up
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                    if (e == cudaSuccess) e = launch_mixed_raw(k, list, nt, cand);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                    float ms = 0.0f;
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e == cudaSuccess && ms < best) {
+                        best = ms;
+                        tpr = cand;
+                    }
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (e != cudaSuccess) return e;
+                // the timing runs' flags, rebuild lists and step counts
+                e = cudaMemsetAsync(dmisc, 0, sizeof(unsigned long long), s);
+                if (e == cudaSuccess) e = cudaMemsetAsync(dmisc + 30, 0, 10 * sizeof(unsigned long long), s);
+                if (e != cudaSuccess) return e;
+            }
+            ctx->tuned[key] = (uint32_t)tpr;
+        }
+        ctx->info_inv_tpr[k] = tpr;
+        return launch_mixed_raw(k, list, cnt, tpr);
+    };
 
     unsigned long long *hs = (unsigned long long *)ctx->host_small;
     if (!order) {
@@ -693,7 +745,7 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
             a.n_list = n;
             LABFM_CUDA_TRY(ctx, launch_order(k, G, a, ctx->num_sms, s));
         } else {
-            LABFM_CUDA_TRY(ctx, launch_mixed(k, nullptr, n));
+            LABFM_CUDA_TRY(ctx, launch_mixed(k, nullptr, n, n > 0 ? (double)ctx->nnz / (double)n : 0.0));
         }
     } else {
         // bucket the nodes by (order, stencil size), both descending
@@ -754,7 +806,8 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
         // than one launch per phase over all orders, which carries order 8's shared memory and
         // thread count for every node)
         for (int k = KMAX; k >= 1; k--)
-            if (!fp64_route(k) && cnt[k]) LABFM_CUDA_TRY(ctx, launch_mixed(k, list + base[k], cnt[k]));
+            if (!fp64_route(k) && cnt[k])
+                LABFM_CUDA_TRY(ctx, launch_mixed(k, list + base[k], cnt[k], degsum[k] / (double)cnt[k]));
     }
     LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(hs, dmisc, NMISC * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));

@@ -794,14 +794,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
 }
 
 // ------------------------------------------------------------------------------------------
-// B: Gauss-Jordan inversion with partial pivoting, in double-float; one CTA per node with two
-// threads per row of the working matrix in shared memory: thread t updates the columns
-// q = h, h + 2, h + 4, ... of row t / 2 (h = t % 2), so that 2P lanes do work and each thread's
-// update is half a row (a thread per row would keep 20 of 64 lanes idle at p = 44 and double
-// the length of each update).  A zero column pads odd P to an even width WC.  The row stride is
-// twice an odd number of 8-byte words, so the 16 lanes of a half-warp (8 rows, both column
-// parities) touch 16 distinct bank pairs.  Per pivot column c:
-//   1. argmax of |M[r][c]| over r >= c (even lanes; warp shuffles, then the warps through
+// B: Gauss-Jordan inversion with partial pivoting, in double-float; one CTA per node with TPR
+// (2 or 4, chosen by the build autotuner) threads per row of the working matrix in shared memory:
+// thread t updates the columns q = h, h + TPR, h + 2 TPR, ... of row t / TPR (h = t % TPR), so
+// that TPR P lanes do work and each thread's update is 1/TPR of a row.  Zero columns pad P to a
+// multiple WC of TPR.  The row stride LDM (in 8-byte words) is TPR times an odd number, so the
+// 16 lanes of a half-warp (16 / TPR rows, TPR column classes) touch 16 distinct bank pairs.  Per
+// pivot column c:
+//   1. argmax of |M[r][c]| over r >= c (lanes h = 0; warp shuffles, then the warps through
 //      shared memory; the lowest row wins a tie);
 //   2. rows c and argmax exchanged (threads over columns), the pivot row and the pivot column
 //      (after the exchange) published in shared memory;
@@ -809,51 +809,51 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
 //      row c: M[c][q] /= p, M[c][c] = 1 / p.
 // The row interchanges are undone on the columns when the result is written out.
 // ------------------------------------------------------------------------------------------
-template <int P> struct InvCfg {
-    static constexpr int HALF = (P + 1) / 2;             // columns per thread
-    static constexpr int WC = 2 * HALF;                  // working columns (one zero pad for odd P)
-    static constexpr int LDM = WC % 4 == 2 ? WC : WC + 2;  // row stride: 2 x odd, in 8-byte words
-    static constexpr int NT = (2 * P + 31) / 32 * 32;    // threads: two per row, whole warps
+template <int P, int TPR> struct InvCfg {
+    static_assert(TPR == 2 || TPR == 4, "two or four threads per row");
+    static constexpr int PART = (P + TPR - 1) / TPR;                         // columns per thread
+    static constexpr int WC = TPR * PART;                                     // working columns
+    static constexpr int LDM = (WC / TPR) % 2 ? WC : WC + TPR;                // TPR x odd
+    static constexpr int NT = (TPR * P + 31) / 32 * 32;                       // threads, whole warps
     static constexpr int NW = NT / 32;
-    static_assert(NT >= WC && NT >= 2 * P, "a thread per column and two per row");
-    static_assert(LDM % 4 == 2 && LDM >= WC, "row stride");
+    static_assert(NT >= WC && NT >= TPR * P, "a thread per column and TPR per row");
+    static_assert((LDM / TPR) % 2 == 1 && LDM % TPR == 0 && LDM >= WC, "row stride");
 };
 
-// Shared memory of the inversion for matrices of up to PM rows and NWB warps per CTA.
-template <int PM, int NWB> struct InvShared {
-    df m[PM * InvCfg<PM>::LDM];
-    df prow[InvCfg<PM>::WC];
-    df pcol[PM];
-    float best[NWB];
-    int br[NWB];
-    int src[PM];
-    signed char piv[PM];
+// Shared memory of the inversion of one p x p matrix with TPR threads per row.
+template <int P, int TPR> struct InvShared {
+    df m[P * InvCfg<P, TPR>::LDM];
+    df prow[InvCfg<P, TPR>::WC];
+    df pcol[P];
+    float best[InvCfg<P, TPR>::NW];
+    int br[InvCfg<P, TPR>::NW];
+    int src[P];
+    signed char piv[P];
 };
 
-// M^-1 of list entry li at order K by a CTA of NTB threads (at least InvCfg<p>::NT).
-template <int K, int NTB, class SH>
-__device__ __forceinline__ void invert_node(const MixedArgs &A, int64_t li, SH &sh)
+// M^-1 of list entry li at order K by a CTA of InvCfg<p, TPR>::NT threads.
+template <int K, int TPR>
+__device__ __forceinline__ void invert_node(const MixedArgs &A, int64_t li, InvShared<p_of_k(K), TPR> &sh)
 {
     constexpr int P = p_of_k(K);
-    using I = InvCfg<P>;
-    constexpr int HALF = I::HALF, WC = I::WC, LDM = I::LDM, NW = NTB / 32;
-    static_assert(NTB >= I::NT && NTB % 32 == 0, "two threads per row, whole warps");
+    using I = InvCfg<P, TPR>;
+    constexpr int PART = I::PART, WC = I::WC, LDM = I::LDM, NT = I::NT, NW = I::NW;
     df *s_m = sh.m, *s_prow = sh.prow, *s_pcol = sh.pcol;
     float *s_best = sh.best;
     int *s_br = sh.br, *s_src = sh.src;
     signed char *s_piv = sh.piv;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int r = t >> 1, hf = t & 1;
+    const int r = t / TPR, hf = t % TPR;
     const bool own = r < P;
 
     if (A.flag[li] != 0) return;  // uniform per CTA
     const df *Mg = A.Mg + li * A.mstride;
-    for (int u = t; u < P * P; u += NTB) {
+    for (int u = t; u < P * P; u += NT) {
         const int rr = u / P;
         s_m[rr * LDM + (u - rr * P)] = Mg[u];
     }
     if (WC > P)
-        for (int rr = t; rr < P; rr += NTB) s_m[rr * LDM + P] = df{0.0f, 0.0f};
+        for (int u = t; u < P * (WC - P); u += NT) s_m[(u / (WC - P)) * LDM + P + u % (WC - P)] = df{0.0f, 0.0f};
     __syncthreads();
     bool zero = false;
     for (int c = 0; c < P; c++) {
@@ -885,7 +885,7 @@ __device__ __forceinline__ void invert_node(const MixedArgs &A, int64_t li, SH &
             zero = true;
             break;
         }
-        // best > 0 comes from an even lane of a row r >= c, so c <= br < P
+        // best > 0 comes from a lane h = 0 of a row r >= c, so c <= br < P
         if (t == 0) s_piv[c] = (signed char)br;
         if (t < WC) {  // column t: exchange rows c and br, publish the pivot row
             const df a = s_m[c * LDM + t], b = s_m[br * LDM + t];
@@ -906,17 +906,17 @@ __device__ __forceinline__ void invert_node(const MixedArgs &A, int64_t li, SH &
         __syncthreads();
         const df inv = df_recip(s_prow[c]);
         if (own) {
-            df *row = s_m + r * LDM + hf;  // this thread's columns: row[2 q]
-            const bool mine = (c & 1) == hf;
+            df *row = s_m + r * LDM + hf;  // this thread's columns: row[TPR q]
+            const bool mine = (c % TPR) == hf;
             if (r == c) {
 #pragma unroll
-                for (int q = 0; q < HALF; q++) row[2 * q] = df_mul(row[2 * q], inv);
+                for (int q = 0; q < PART; q++) row[TPR * q] = df_mul(row[TPR * q], inv);
                 if (mine) row[c - hf] = inv;
             } else {
                 const df f = df_mul(s_pcol[r], inv);
                 const df *pr = s_prow + hf;
 #pragma unroll
-                for (int q = 0; q < HALF; q++) row[2 * q] = df_fms(f, pr[2 * q], row[2 * q]);
+                for (int q = 0; q < PART; q++) row[TPR * q] = df_fms(f, pr[TPR * q], row[TPR * q]);
                 if (mine) row[c - hf] = df_neg(f);
             }
         }
@@ -939,19 +939,18 @@ __device__ __forceinline__ void invert_node(const MixedArgs &A, int64_t li, SH &
     }
     __syncthreads();
     df *Mo = A.Mg + li * A.mstride;
-    for (int u = t; u < P * P; u += NTB) {
+    for (int u = t; u < P * P; u += NT) {
         const int rr = u / P, q = u - rr * P;
         Mo[u] = s_m[rr * LDM + s_src[q]];
     }
     __syncthreads();
 }
 
-template <int K>
-__global__ void __launch_bounds__(InvCfg<p_of_k(K)>::NT) k_mixed_invert(MixedArgs A)
+template <int K, int TPR>
+__global__ void __launch_bounds__(InvCfg<p_of_k(K), TPR>::NT) k_mixed_invert(MixedArgs A)
 {
-    using I = InvCfg<p_of_k(K)>;
-    __shared__ InvShared<p_of_k(K), I::NW> sh;
-    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) invert_node<K, I::NT>(A, li, sh);
+    __shared__ InvShared<p_of_k(K), TPR> sh;
+    for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) invert_node<K, TPR>(A, li, sh);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1278,7 +1277,7 @@ cudaError_t launch_tc(KernelT kern, const MixedArgs &a, size_t smem_needed, int 
 }
 
 template <int K>
-cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, bool tc, cudaStream_t s)
+cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, bool tc, int inv_tpr, cudaStream_t s)
 {
     using C = MCfg<K>;
     cudaError_t e = launch_records(a, num_sms, s);
@@ -1286,7 +1285,8 @@ cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, bool tc, cudaStream_
     if (tc) e = launch_tc(k_mixed_assemble_tc<K>, a, TcCfg<K>::smem, num_sms, s);
     else e = launch_persistent(k_mixed_assemble<K>, a, MIX_THREADS, C::smemA, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
-    e = launch_persistent(k_mixed_invert<K>, a, InvCfg<C::P>::NT, 0, a.n_list, num_sms, s);
+    if (inv_tpr == 4) e = launch_persistent(k_mixed_invert<K, 4>, a, InvCfg<C::P, 4>::NT, 0, a.n_list, num_sms, s);
+    else e = launch_persistent(k_mixed_invert<K, 2>, a, InvCfg<C::P, 2>::NT, 0, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
     return launch_persistent(k_mixed_weights<K>, a, MIX_THREADS, C::smemC, a.n_list, num_sms, s);
 }
@@ -1350,10 +1350,10 @@ cudaError_t launch_build_mixed(int k, const MixedArgsPublic &p, cudaStream_t s)
         a.flag = reinterpret_cast<int *>(reinterpret_cast<char *>(p.scratch) + sizeof(df) * (size_t)a.mstride * batch);
         cudaError_t e;
         switch (k) {
-        case 5: e = launch_mixed_k<5>(a, p.num_sms, p.tc != 0, s); break;
-        case 6: e = launch_mixed_k<6>(a, p.num_sms, p.tc != 0, s); break;
-        case 7: e = launch_mixed_k<7>(a, p.num_sms, p.tc != 0, s); break;
-        default: e = launch_mixed_k<8>(a, p.num_sms, p.tc != 0, s); break;
+        case 5: e = launch_mixed_k<5>(a, p.num_sms, p.tc != 0, p.inv_tpr, s); break;
+        case 6: e = launch_mixed_k<6>(a, p.num_sms, p.tc != 0, p.inv_tpr, s); break;
+        case 7: e = launch_mixed_k<7>(a, p.num_sms, p.tc != 0, p.inv_tpr, s); break;
+        default: e = launch_mixed_k<8>(a, p.num_sms, p.tc != 0, p.inv_tpr, s); break;
         }
         if (e != cudaSuccess) return e;
     }

@@ -78,6 +78,7 @@ struct labfm_ctx {
     int64_t info_ref_hist[8] = {0};
     int64_t info_fp64_rebuilt = 0;
     int info_group[LABFM_MAX_ORDER + 1] = {0};  // threads per node of the FP64 kernel, per order built by it
+    int info_inv_tpr[LABFM_MAX_ORDER + 1] = {0};  // threads per row of the mixed inversion, per order
 
     // RK4
     labfm::DevBuf wcomb, rk_acc, rk_stage_a, rk_stage_b;
@@ -144,6 +145,7 @@ struct MixedArgsPublic {
     void *scratch;
     void *recs;  // [nnz] per-entry records, mixed_record_bytes() each
     int tc;      // 1: moment matrices on the tensor cores (exact BF16 slices), 0: double-float
+    int inv_tpr; // threads per matrix row in the inversion: 2 or 4
     unsigned long long *tc_timeout;  // device counter of tensor-core waits that gave up
     void *wstore;  // [nnz][p(k)] double-float W kept between the assembly and the weights, or null
 };
