@@ -27,6 +27,8 @@ __all__ = [
     "jittered_lattice",
     "variable_wall_nodes",
     "dirichlet_square",
+    "NeumannSquare",
+    "neumann_square",
     "HeatSteadyField",
     "ColeBurgersSolution",
     "ColeHopf2DSolution",
@@ -239,6 +241,57 @@ def dirichlet_square(n_side: int, h_over_s: float = 2.0, k: int = 4, eps: float 
     return NodeSet(xy=xy, h=np.full(n, h_over_s * s), s=np.full(n, s),
                    order=np.full(n, k, dtype=np.int8), periodic=False,
                    lo=(0.0, 0.0), hi=(1.0, 1.0), wall=(d == 0))
+
+
+@dataclass
+class NeumannSquare:
+    """The unit square of ``dirichlet_square`` with a Neumann boundary (Sec. 5.2) on its bottom
+    and top walls: ``ns`` holds the lattice nodes followed by one ghost node per Neumann wall
+    node.  ``dirichlet`` (bool [n]) marks the left and right walls (corners included);
+    ``ghost`` / ``parent`` (int64 [n_ghost]) pair each ghost node with its wall node b;
+    ``normal`` (float64 [n_ghost, 2]) is the unit normal at b pointing into the domain, so that
+    the ghost sits at r_b - n_b s."""
+
+    ns: NodeSet
+    dirichlet: np.ndarray
+    ghost: np.ndarray
+    parent: np.ndarray
+    normal: np.ndarray
+    spacing: float
+
+
+def neumann_square(n_side: int, h_over_s: float = 2.0, k: int = 4, eps: float = 0.5,
+                   seed: int = 1, wall_band: int = 2) -> NeumannSquare:
+    """Node set for Poisson's equation with Dirichlet walls at x = 0, 1 and Neumann walls at
+    y = 0, 1 (Sec. 5.2): the lattice of ``dirichlet_square`` (spacing s = 1/(n_side - 1),
+    jitter beyond ``wall_band`` rows of a wall), and for every node b of the bottom and top
+    walls other than the corners a ghost node at r_b - n_b s, n_b = (0, 1) at the bottom and
+    (0, -1) at the top.  Ghosts share h = h_over_s s and order k; the (non-periodic) box is
+    [0, 1] x [-s, 1 + s], so that it holds the ghosts."""
+    base = dirichlet_square(n_side, h_over_s, k, eps, seed, wall_band)
+    m = n_side
+    s = 1.0 / (m - 1)
+    idx = np.arange(m * m)
+    i, j = idx % m, idx // m
+    inner = (i > 0) & (i < m - 1)
+    bottom = np.nonzero(inner & (j == 0))[0]
+    top = np.nonzero(inner & (j == m - 1))[0]
+    parent = np.concatenate([bottom, top]).astype(np.int64)
+    normal = np.concatenate([np.tile([0.0, 1.0], (len(bottom), 1)), np.tile([0.0, -1.0], (len(top), 1))])
+    gxy = base.xy[parent] - normal * s
+    n0 = base.n
+    ghost = np.arange(n0, n0 + len(parent), dtype=np.int64)
+    xy = np.ascontiguousarray(np.concatenate([base.xy, gxy]))
+    ng = len(parent)
+    ns = NodeSet(xy=xy, h=np.concatenate([base.h, np.full(ng, h_over_s * s)]),
+                 s=np.concatenate([base.s, np.full(ng, s)]),
+                 order=np.full(n0 + ng, k, dtype=np.int8), periodic=False,
+                 lo=(0.0, -s), hi=(1.0, 1.0 + s),
+                 wall=np.concatenate([base.wall, np.zeros(ng, dtype=bool)]))
+    dirichlet = np.zeros(n0 + ng, dtype=bool)
+    dirichlet[:n0] = (i == 0) | (i == m - 1)
+    return NeumannSquare(ns=ns, dirichlet=dirichlet, ghost=ghost, parent=parent,
+                         normal=np.ascontiguousarray(normal), spacing=s)
 
 
 # ----------------------------------------------------------------------------------

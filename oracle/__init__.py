@@ -265,14 +265,21 @@ def steady_state(row_ptr, col, w, beta, u_fixed, frozen):
     return u
 
 
-def solve_operator(row_ptr, col, w, op, f, dirichlet=None):
+def solve_operator(row_ptr, col, w, op, f, dirichlet=None, neumann=None):
     """The global system of Sec. 5.2 (eq. poisson_system): A Phi = F with A_ij = w^op_ji (j != i),
     A_ii = -sum_j w^op_ji, and identity rows (Phi_i = f_i) where ``dirichlet`` is set; by a sparse
-    direct solve."""
+    direct solve.
+
+    ``neumann`` = (ghost, parent, normal, op_x, op_y): the ghost-node rows of Sec. 5.2 for a
+    Neumann boundary.  Row ghost[g] is replaced by the boundary normal derivative operator of its
+    parent node b = parent[g], n_x w^(op_x) + n_y w^(op_y) with (n_x, n_y) = normal[g]:
+    A_gj = n_x w^x_jb + n_y w^y_jb for every j in the stencil of b, and A_gb = minus the sum of
+    those entries; F_g (= f[ghost[g]]) is the prescribed normal derivative there."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spl
 
     w = np.asarray(w, dtype=np.float64)
+    rp = np.asarray(row_ptr, dtype=np.int64)
     beta = np.zeros(w.shape[1])
     beta[op] = 1.0
     A = operator_matrix(row_ptr, col, w, beta).tolil()
@@ -281,6 +288,23 @@ def solve_operator(row_ptr, col, w, op, f, dirichlet=None):
         for i in np.nonzero(np.asarray(dirichlet))[0]:
             A.rows[i] = [int(i)]
             A.data[i] = [1.0]
+    if neumann is not None:
+        ghost, parent, normal, op_x, op_y = neumann
+        normal = np.asarray(normal, dtype=np.float64).reshape(-1, 2)
+        for g in range(len(ghost)):
+            gi, pb = int(ghost[g]), int(parent[g])
+            nx, ny = normal[g]
+            row = {}
+            total = 0.0
+            for e in range(rp[pb], rp[pb + 1]):
+                c = nx * w[e, op_x] + ny * w[e, op_y]
+                j = int(col[e])
+                row[j] = row.get(j, 0.0) + c
+                total += c
+            row[pb] = row.get(pb, 0.0) - total
+            js = sorted(row)
+            A.rows[gi] = js
+            A.data[gi] = [row[j] for j in js]
     return spl.spsolve(sp.csc_matrix(A), b)
 
 

@@ -94,9 +94,17 @@ PY_MUTATIONS = {
     "Dirichlet rows ignored": ("solve_operator", "for i in np.nonzero(np.asarray(dirichlet))[0]:",
                                "for i in np.nonzero(np.asarray(dirichlet))[0][:0]:"),
     "operator index ignored": ("solve_operator", "beta[op] = 1.0", "beta[0] = 1.0"),
+    "Neumann row diagonal on the ghost instead of its parent": (
+        "solve_operator", "row[pb] = row.get(pb, 0.0) - total", "row[gi] = row.get(gi, 0.0) - total"),
+    "Neumann row without the normal's y component": (
+        "solve_operator", "c = nx * w[e, op_x] + ny * w[e, op_y]", "c = nx * w[e, op_x]"),
+    "Neumann row with the x and y operators swapped": (
+        "solve_operator", "c = nx * w[e, op_x] + ny * w[e, op_y]", "c = nx * w[e, op_y] + ny * w[e, op_x]"),
+    "Neumann ghost rows left out": ("solve_operator", "for g in range(len(ghost)):", "for g in range(0):"),
 }
 
 PY_PINS = [  # cheapest first; the first pin that fails ends the search
+    P.test_poisson_neumann_ghost_rows_reproduce_polynomials,
     P.test_global_matrix_and_direct_solve_vs_apply,
     P.test_heat_frozen_rk4_reaches_the_steady_state,
     lambda: P.test_heat_steady_state_table(2),

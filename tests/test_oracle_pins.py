@@ -839,3 +839,85 @@ def test_poisson_periodic_even_order_pattern():
         e20, e80 = poisson_periodic_error(k, 20, hdr), poisson_periodic_error(k, 80, hdr)
         rate = math.log2(e20 / e80) / 2.0
         assert lo <= rate <= hi, (k, e20, e80, rate)
+
+
+# a polynomial of degree 4 as {(a, b): coefficient of x^a y^b}
+NEUMANN_POLY = {(0, 0): 0.3, (1, 0): 1.0, (0, 1): -0.7, (2, 0): 0.5, (1, 1): -1.1, (0, 2): 0.8, (3, 0): 0.2,
+                (2, 1): -0.4, (0, 3): 0.6, (4, 0): 0.9, (2, 2): -0.3, (1, 3): 0.5, (0, 4): -0.7}
+
+
+def _poly_eval(c, x, y, dx=0, dy=0):
+    """sum c_ab d^dx/dx d^dy/dy (x^a y^b), by the power rule"""
+    out = np.zeros_like(x)
+    for (a, b), v in c.items():
+        if a < dx or b < dy:
+            continue
+        fa = math.factorial(a) // math.factorial(a - dx)
+        fb = math.factorial(b) // math.factorial(b - dy)
+        out = out + v * fa * fb * x ** (a - dx) * y ** (b - dy)
+    return out
+
+
+def neumann_problem(nside, k, field, rbf="quadratic", seed=21):
+    """Poisson's equation on the Neumann square (Dirichlet walls at x = 0, 1; Neumann walls with
+    ghost nodes at y = 0, 1): the oracle's stencils and weights of (d/dx, d/dy, nabla^2), and the
+    right-hand side F for the exact solution `field` = (phi, phi_x, phi_y, lap phi) as functions
+    of (x, y): nabla^2 phi in the Poisson rows, phi in the Dirichlet rows, n . grad phi at the
+    parent in the ghost rows."""
+    q = S.neumann_square(nside, 2.0, k, 0.5, seed=seed)
+    ns = q.ns
+    rp, col = oracle.neighbours(ns.xy, ns.h, False, ns.lo, ns.hi)
+    C = np.stack([S.op_c_vector(o, k) for o in ("dx", "dy", "lap")])
+    r = oracle.build_weights(ns.xy, ns.h, False, rp, col, C, k=k, rbf=rbf, abf_form="dw0", lo=ns.lo, hi=ns.hi)
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    phi, phx, phy, lap = field
+    ex = phi(x, y)
+    f = np.where(q.dirichlet, ex, lap(x, y))
+    xb, yb = x[q.parent], y[q.parent]
+    f[q.ghost] = q.normal[:, 0] * phx(xb, yb) + q.normal[:, 1] * phy(xb, yb)
+    return q, rp, col, r, ex, f
+
+
+def _neumann_poly_field():
+    c = NEUMANN_POLY
+    return (lambda x, y: _poly_eval(c, x, y), lambda x, y: _poly_eval(c, x, y, 1, 0),
+            lambda x, y: _poly_eval(c, x, y, 0, 1),
+            lambda x, y: _poly_eval(c, x, y, 2, 0) + _poly_eval(c, x, y, 0, 2))
+
+
+def test_poisson_neumann_ghost_rows_reproduce_polynomials():
+    """The Neumann ghost-node rows of Sec. 5.2 with k = 4 on a 21^2 square (Dirichlet walls at
+    x = 0, 1, Neumann walls at y = 0, 1 with one ghost per wall node): for a polynomial phi of
+    degree 4 every local operator is exact (polynomial reproduction, Sec. 3.1), so the exact
+    nodal values, ghosts included, satisfy every row of the enlarged system; its solution must
+    be phi itself.  A ghost row with its diagonal on the ghost instead of the parent, a normal
+    with the wrong sign or a dropped component, or rows left out all break it."""
+    q, rp, col, r, ex, f = neumann_problem(21, 4, _neumann_poly_field())
+    interior = np.ones(q.ns.n, bool)
+    interior[q.ghost] = False
+    assert (r["status"][interior] == 0).all()
+    phi = oracle.solve_operator(rp, col, r["w"], 2, f, q.dirichlet.astype(np.uint8),
+                                neumann=(q.ghost, q.parent, q.normal, 0, 1))
+    err = np.abs(phi - ex).max() / np.abs(ex).max()
+    assert err < 1e-9, err
+
+
+def test_poisson_neumann_convergence():
+    """Sec. 5.2's Neumann treatment is consistent with the order of the discretisation: for
+    phi = sin(2x + 0.3) cos(3y - 0.2) (nonzero normal derivative on both Neumann walls) the
+    solution error falls at least as h^(k - 1) from 21^2 to 41^2 nodes at k = 4 (one-sided
+    stencils at the walls)."""
+    field = (lambda x, y: np.sin(2 * x + 0.3) * np.cos(3 * y - 0.2),
+             lambda x, y: 2 * np.cos(2 * x + 0.3) * np.cos(3 * y - 0.2),
+             lambda x, y: -3 * np.sin(2 * x + 0.3) * np.sin(3 * y - 0.2),
+             lambda x, y: -13 * np.sin(2 * x + 0.3) * np.cos(3 * y - 0.2))
+    errs = []
+    for nside in (21, 41):
+        q, rp, col, r, ex, f = neumann_problem(nside, 4, field)
+        phi = oracle.solve_operator(rp, col, r["w"], 2, f, q.dirichlet.astype(np.uint8),
+                                    neumann=(q.ghost, q.parent, q.normal, 0, 1))
+        keep = np.ones(q.ns.n, bool)
+        keep[q.ghost] = False
+        errs.append(np.linalg.norm(phi[keep] - ex[keep]) / np.linalg.norm(ex[keep]))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate >= 3.0, (errs, rate)
