@@ -428,6 +428,7 @@ def extra_measurements(torch, P, dev, local_rank, ns, field, hbm):
         out["heat_dirichlet_k4"] = heat_dirichlet(torch, P, dev, local_rank)
         out["burgers_cole_k4"] = burgers_cole(torch, P, dev, local_rank)
         out["poisson_periodic_k4"] = poisson_periodic(torch, P, dev, local_rank)
+        out["poisson_neumann_k4"] = poisson_neumann(torch, P, dev, local_rank)
         out["rk4_2048"] = rk4_large(torch, P, dev, local_rank)
         out["walls_1m_variable_order"] = walls_variable_order(torch, P, dev, local_rank)
     return out
@@ -554,6 +555,50 @@ def poisson_periodic(torch, P, dev, local_rank, k=4, nside=512, tol=1e-10):
     return res
 
 
+def poisson_neumann(torch, P, dev, local_rank, k=4, nside=257, tol=1e-10):
+    """Poisson's equation with the Neumann ghost-node rows of Sec. 5.2: the unit square of
+    labfm_synth.neumann_square at 257 x 257 lattice nodes plus one ghost per Neumann wall node
+    (Dirichlet walls at x = 0, 1; Neumann walls at y = 0, 1; h/dr = 2, interior noise eps/dr = 0.5,
+    quadratic ABFs in the dW0/dr form, order 4), phi = sin(2 pi x + 0.3) cos(3 pi y - 0.2) (nonzero
+    normal derivative on both Neumann walls), solved by labfm_solve_neumann from zero to a
+    relative residual of 1e-10; error against phi at the lattice nodes."""
+    q = S.neumann_square(nside, 2.0, k, 0.5, seed=21)
+    ns = q.ns
+    L = P.Labfm(local_rank)
+    L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), False, ns.lo, ns.hi)
+    C = np.stack([S.op_c_vector(o, k) for o in ("dx", "dy", "lap")])
+    st = torch.zeros(ns.n, dtype=torch.int32, device=dev)
+    L.build_weights(C, uniform_order=k, rbf="quadratic", abf_form="dw0", node_status=st)
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    a, b = 2 * np.pi, 3 * np.pi
+    ex = np.sin(a * x + 0.3) * np.cos(b * y - 0.2)
+    f = np.where(q.dirichlet, ex, -(a * a + b * b) * ex)
+    xb, yb = x[q.parent], y[q.parent]
+    f[q.ghost] = q.normal[:, 1] * (-b * np.sin(a * xb + 0.3) * np.sin(b * yb - 0.2))  # n = (0, +-1)
+    fd = torch.from_numpy(f).to(dev)
+    dmd = torch.from_numpy(q.dirichlet.astype(np.uint8)).to(dev)
+    nm = (torch.from_numpy(q.ghost).to(dev), torch.from_numpy(q.parent).to(dev), torch.from_numpy(q.normal).to(dev),
+          0, 1)
+    phi = torch.zeros(ns.n, dtype=torch.float64, device=dev)
+    L.solve(2, fd, phi, dmd, tol=tol, max_iter=100000, neumann=nm)  # warm (allocations, first launches)
+    phi.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters, resid = L.solve(2, fd, phi, dmd, tol=tol, max_iter=100000, neumann=nm)  # synchronises at the end
+    ms = (time.perf_counter() - t0) * 1e3
+    got = phi.cpu().numpy()
+    keep = np.ones(ns.n, bool)
+    keep[q.ghost] = False
+    status = st.cpu().numpy()
+    res = {"nodes": ns.n, "ghost_rows": int(len(q.ghost)), "nnz": int(L.nnz), "order": k, "tol": tol,
+           "flagged_lattice_nodes": int((status[keep] != 0).sum()), "flagged_ghost_nodes": int((status[~keep] != 0).sum()),
+           "iterations": iters, "true_rel_residual": resid, "ms": ms, "us_per_iteration": ms * 1e3 / max(iters, 1),
+           "l2_err_vs_exact": float(np.linalg.norm(got[keep] - ex[keep]) / np.linalg.norm(ex[keep])),
+           "timing": "host wall clock around the call (it synchronises)"}
+    L.close()
+    return res
+
+
 RK4_JITTER = 0.1       # noise of the time-stepping node set: every order-8 stencil well conditioned
 RK4_RBF = "quadratic"  # the kernel of the PDE tests of Sec. 5
 RK4_ABF = "dw0"        # dW0/dr-only ABFs: the form the stability results of Sec. 4.2 belong to
@@ -655,6 +700,103 @@ def rk4_large(torch, P, dev, local_rank, n_side=2048, nsteps=1000):
         torch.cuda.empty_cache()
     res["nnz"] = int(L.nnz)
     return res
+
+
+def _host_spectral_radius(A, iters=80):
+    """Largest |lambda| of the sparse matrix A by power iteration on the host (seeded start)."""
+    v = np.random.default_rng(0).standard_normal(A.shape[0])
+    v /= np.linalg.norm(v)
+    rho = 0.0
+    for _ in range(iters):
+        wv = A @ v
+        rho = float(np.linalg.norm(wv))
+        v = wv / rho
+    return rho
+
+
+def rk4_oracle_leg(torch, P, dev, local_rank, n_side=2048, sub_side=256, nsteps=1000):
+    """The time-stepping workload against the oracle.  (1) The 2048^2 set's 256^2 subsample (every
+    8th lattice node in x and y): the GPU's stencil rows against the oracle's (bit for bit), and
+    the derivatives of u0 through the GPU's FP64 weights against the FP64 oracle's weights at
+    those 65,536 nodes.  (2) An independent 256^2 set with the same parameters (seed 6): nsteps
+    of RK4 by the oracle (its own stencils, weights and FP64 fields) against the GPU's graph-
+    replayed steps with FP32 fields on FP64 weights and on FP32 weights (and FP64 fields on FP64
+    weights, the floor), all from the same dt."""
+    import oracle
+
+    out = {"reference": "FP64 oracle"}
+    C = np.stack([S.op_c_vector(o, K) for o in OPS])
+    ns = S.jittered_lattice(n_side, HS, K, jitter=RK4_JITTER, seed=5)
+    n = ns.n
+    sub = np.nonzero((np.arange(n) // n_side % 8 == 0) & (np.arange(n) % n_side % 8 == 0))[0]
+    u0 = S.sincos_field().value(ns.xy)
+    L = P.Labfm(local_rank)
+    L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), True)
+    L.build_weights(C, uniform_order=K, rbf=RK4_RBF, abf_form=RK4_ABF)
+    rp_d, col_d = L.get_neighbours()
+    rp = rp_d.cpu().numpy()
+    lens = rp[sub + 1] - rp[sub]
+    rows = torch.from_numpy(np.concatenate([np.arange(rp[i], rp[i + 1]) for i in sub])).to(dev)
+    col_sub = col_d[rows].cpu().numpy()
+    w_gpu = L.get_weights()[rows].cpu().numpy().astype(np.float64)
+    d_gpu = L.apply(torch.from_numpy(u0).to(dev))[:, torch.from_numpy(sub).to(dev)].cpu().numpy()
+    L.close()
+    del rows, rp_d, col_d
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    orp, ocol = oracle.neighbours_large(ns.xy, ns.h, True, queries=sub)
+    r = oracle.build_weights(ns.xy, ns.h, True, orp, ocol, C, k=K, rbf=RK4_RBF, abf_form=RK4_ABF, queries=sub)
+    d_or = oracle.apply(orp, ocol, r["w"], u0, queries=sub)
+    exact_rows = bool(np.array_equal(np.diff(orp), lens) and np.array_equal(ocol, col_sub))
+    res = {"nodes": int(len(sub)), "stencils_bit_exact": exact_rows, "oracle_status_ok": int((r["status"] == 0).sum()),
+           "oracle_s": time.perf_counter() - t0}
+    if exact_rows:
+        # per node and operator: the weights normwise, ||w_gpu - w_oracle|| / ||w_oracle||, and the
+        # derivative of u0 relative to the sum of its terms, |d_gpu - d_oracle| / sum_j |(u_j - u_i) w_ji|
+        # (the nabla^8 of a smooth mode at h ~ 1e-3 cancels terms ~1e14 times larger than the
+        # result, so its error relative to the result itself only measures that cancellation)
+        starts = orp[:-1]
+        wn = np.sqrt(np.add.reduceat(r["w"] ** 2, starts, axis=0)).T
+        wd = np.sqrt(np.add.reduceat((w_gpu - r["w"]) ** 2, starts, axis=0)).T / wn
+        terms = np.abs(u0[ocol] - np.repeat(u0[sub], lens))[:, None] * np.abs(r["w"])
+        dd = np.abs(d_gpu - d_or) / np.add.reduceat(terms, starts, axis=0).T
+        res["weights_normwise"] = {"median": np.median(wd, axis=1).tolist(), "max": wd.max(axis=1).tolist()}
+        res["deriv_err_over_term_sum"] = {"median": np.median(dd, axis=1).tolist(), "max": dd.max(axis=1).tolist()}
+        res["deriv_err_vs_scale"] = _err_stats(d_gpu, d_or)
+    out["subsample_2048"] = res
+    # (2) an independent 256^2 set, full RK4 on both sides
+    ns = S.jittered_lattice(sub_side, HS, K, jitter=RK4_JITTER, seed=6)
+    h = ns.h[0]
+    beta = np.array([-C_ADV[0], -C_ADV[1], NU, -HV * h ** 8])
+    u0 = S.sincos_field().value(ns.xy)
+    t0 = time.perf_counter()
+    orp, ocol = oracle.neighbours_large(ns.xy, ns.h, True)
+    r = oracle.build_weights(ns.xy, ns.h, True, orp, ocol, C, k=K, rbf=RK4_RBF, abf_form=RK4_ABF)
+    rho = _host_spectral_radius(oracle.operator_matrix(orp, ocol, r["w"], beta))
+    dt = min(0.5 / sub_side / float(np.hypot(*C_ADV)), 0.8 * 2.785 / rho)
+    u_or = oracle.rk4(orp, ocol, r["w"], beta, u0, dt, nsteps)
+    oracle_s = time.perf_counter() - t0
+    T = dt * nsteps
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    exact = np.exp(-8 * np.pi ** 2 * NU * T) * np.sin(2 * np.pi * (x - C_ADV[0] * T)) * \
+        np.cos(2 * np.pi * (y - C_ADV[1] * T))
+    rk = {"nodes": ns.n, "seed": 6, "steps": nsteps, "dt": dt, "spectral_radius_oracle": rho, "oracle_s": oracle_s,
+          "oracle_l2_err_vs_exact": float(np.linalg.norm(u_or - exact) / np.linalg.norm(exact))}
+    sc = float(np.abs(u_or).max())
+    for wdt, fdt in (("f64", torch.float64), ("f64", torch.float32), ("f32", torch.float32)):
+        L = P.Labfm(local_rank)
+        L.build_neighbours(torch.from_numpy(ns.xy).to(dev), torch.from_numpy(ns.h).to(dev), True)
+        L.build_weights(C, uniform_order=K, rbf=RK4_RBF, abf_form=RK4_ABF, weight_dtype=wdt)
+        u = torch.from_numpy(u0).to(dev, fdt)
+        L.step(beta, u, dt, nsteps)
+        got = u.cpu().numpy().astype(np.float64)
+        L.close()
+        key = f"gpu_{'f64' if fdt == torch.float64 else 'f32'}_fields_{wdt}_weights"
+        rk[key] = {"max_diff_vs_oracle": float(np.abs(got - u_or).max() / sc),
+                   "l2_diff_vs_oracle": float(np.linalg.norm(got - u_or) / np.linalg.norm(u_or)),
+                   "l2_err_vs_exact": float(np.linalg.norm(got - exact) / np.linalg.norm(exact))}
+    out["independent_256_rk4"] = rk
+    return out
 
 
 def walls_variable_order(torch, P, dev, local_rank, n_side=1000):
@@ -870,6 +1012,8 @@ def run_labfm(args, rank, world, local_rank):
         # the oracle leg: the CPU baseline, and the accuracy of every build variant against it
         line["cpu_baseline"] = cpu_baseline(ns, field, C, sample=args.cpu_sample)
         line["extra"]["accuracy_vs_oracle"] = accuracy_vs_oracle(torch, P, dev, local_rank)
+        if not SKIP_LARGE:
+            line["extra"]["rk4_2048"]["oracle"] = rk4_oracle_leg(torch, P, dev, local_rank)
     print(json.dumps(line), flush=True)
     L.close()
 

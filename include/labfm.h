@@ -288,7 +288,9 @@ labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, voi
  * Stops when the recurrence residual ||r|| <= tol ||F||, or after max_iter iterations.  The
  * recurrence residual drifts from the true one ||F - A Phi|| in finite precision, so the true
  * residual is then formed; if it is above tol, the iteration restarts from the current Phi
- * (r = F - A Phi), at most 4 times and within max_iter iterations in total.
+ * (r = F - A Phi, shadow residual r^ = r).  A breakdown (rho = (r^, r), (r^, v) or omega
+ * vanishing or not finite) with a finite Phi restarts the same way.  At most 8 restarts, within
+ * max_iter iterations in total.
  * With a periodic node set A has the constants in its null space: fix at least one node with the
  * Dirichlet mask.
  *   op          operator index (0 <= op < n_ops), weights of either dtype
@@ -299,12 +301,40 @@ labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, voi
  *   tol         relative residual target, > 0;  max_iter >= 1
  *   iters_out   host, may be NULL: iterations taken (over all restarts)
  *   resid_out   host, may be NULL: the true relative residual ||F - A Phi|| / ||F|| at exit
- * Returns LABFM_OK only when that true residual is <= tol; LABFM_ERR_NOT_CONVERGED on breakdown,
- * when max_iter ends the iteration, or when the true residual stays above tol after the restarts
+ * Returns LABFM_OK only when that true residual is <= tol; LABFM_ERR_NOT_CONVERGED on a breakdown
+ * that the restarts do not cure, when max_iter ends the iteration, or when the true residual stays
+ * above tol after the restarts
  * (phi holds the last iterate).  Synchronises the context stream.  LABFM_ERR_STATE before labfm_build_weights.
  */
 labfm_status labfm_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet,
                          double tol, int max_iter, int *iters_out, double *resid_out);
+
+/*
+ * labfm_solve with Neumann boundary rows (Sec. 5.2, the ghost-node treatment of a Neumann
+ * boundary): for every boundary node b with a prescribed normal derivative g_b the node set holds
+ * a ghost node g at r_b - n_b dr (n_b the unit normal into the domain), and the row of g is
+ * replaced by the boundary normal derivative operator at b,
+ *     A_gj = n_x w^(op_x)_jb + n_y w^(op_y)_jb  for every j in the stencil of b,
+ *     A_gb = -(sum of those entries),           F_g = g_b,
+ * so that the solution satisfies n . grad Phi = g_b at b while the ghost's value is free.  Every
+ * other row is as in labfm_solve (operator op, identity rows where dirichlet is set).  The ghosts
+ * are ordinary nodes of the stencil search and of the weight build (they complete the support of
+ * the nodes near the wall; their own weights are not used).  The Jacobi scaling of a ghost row is
+ * the inverse of its true diagonal, the entry of the ghost itself within the stencil of b (1 if
+ * the ghost is not in that stencil).
+ *   n_ghost        number of ghost rows, 0 <= n_ghost <= n (0: labfm_solve)
+ *   ghost, parent  device int64[n_ghost]: the ghost's node index and its boundary node b
+ *                  (distinct ghosts; ghost != parent; a ghost may not be a Dirichlet row)
+ *   normal         device double[n_ghost][2]: (n_x, n_y), used as given (the paper's unit normal)
+ *   op_x, op_y     operator indices of the weights giving d/dx and d/dy
+ *   f              F as in labfm_solve, with F_g = g_b at each ghost row
+ * The remaining arguments and the returns are those of labfm_solve; a bad index, a repeated
+ * ghost, a ghost marked Dirichlet or a non-finite normal is LABFM_ERR_ARG (checked on the device
+ * before the iteration).  Synchronises the context stream.
+ */
+labfm_status labfm_solve_neumann(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet,
+                                 int64_t n_ghost, const int64_t *ghost, const int64_t *parent, const double *normal,
+                                 int op_x, int op_y, double tol, int max_iter, int *iters_out, double *resid_out);
 
 /*
  * Stencil search that allocates nothing.  (The paper has no counterpart: this is an interface

@@ -152,6 +152,49 @@ def neighbours(xy, h, periodic, lo=(0.0, 0.0), hi=(1.0, 1.0), queries=None, prec
     return rp, col[: int(rp[-1])]
 
 
+def neighbours_large(xy, h, periodic, lo=(0.0, 0.0), hi=(1.0, 1.0), queries=None):
+    """The stencils of ``neighbours`` for node sets too large for its all-pairs search (millions
+    of nodes): scipy's kd-tree proposes, per query, every node within a radius 1e-9 larger than
+    2 h_i (a superset of the stencil), and the predicate of Sec. 2 then decides in the same
+    floating-point operations as the brute force, in IEEE double without fused multiply-add:
+    dx = x_j - x_i (+-L once past L/2 in a periodic box), r2 = dx*dx + dy*dy, r2 < (2 h_i)^2,
+    j != i.  Returns (row_ptr int64 [nq+1], col int32 [nnz]), rows ascending in j."""
+    from scipy.spatial import cKDTree
+
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    n = xy.shape[0]
+    q = np.arange(n, dtype=np.int64) if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    L = hi - lo
+    if periodic:
+        tree = cKDTree(xy - lo, boxsize=L)
+        pts = xy[q] - lo
+    else:
+        tree = cKDTree(xy)
+        pts = xy[q]
+    rmax = float(2.0 * h[q].max()) * (1.0 + 1e-9) if len(q) else 0.0
+    cand = tree.query_ball_point(pts, r=rmax)
+    cnt = np.array([len(c) for c in cand], dtype=np.int64)
+    row = np.repeat(np.arange(len(q), dtype=np.int64), cnt)
+    j = np.concatenate([np.asarray(c, dtype=np.int64) for c in cand]) if len(q) else np.zeros(0, np.int64)
+    i = q[row]
+    dx = xy[j, 0] - xy[i, 0]
+    dy = xy[j, 1] - xy[i, 1]
+    if periodic:
+        dx = np.where(dx > 0.5 * L[0], dx - L[0], np.where(dx < -0.5 * L[0], dx + L[0], dx))
+        dy = np.where(dy > 0.5 * L[1], dy - L[1], np.where(dy < -0.5 * L[1], dy + L[1], dy))
+    R = 2.0 * h[i]
+    keep = (dx * dx + dy * dy < R * R) & (j != i)
+    row, j = row[keep], j[keep]
+    order = np.lexsort((j, row))
+    row, j = row[order], j[order]
+    rp = np.zeros(len(q) + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(np.bincount(row, minlength=len(q)))
+    return rp, j.astype(np.int32)
+
+
 def build_weights(xy, h, periodic, row_ptr, col, C, k=None, order=None, rbf="wendland_c2",
                   lo=(0.0, 0.0), hi=(1.0, 1.0), queries=None, precision="f64", nthreads=0,
                   want_mhat=False, abf_form="chain"):

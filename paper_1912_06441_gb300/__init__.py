@@ -41,7 +41,8 @@ MAX_OPS = 8
 # every symbol include/labfm.h declares
 C_FUNCTIONS = ["labfm_create", "labfm_destroy", "labfm_last_error", "labfm_set_stream", "labfm_build_neighbours",
                "labfm_get_neighbours", "labfm_build_weights", "labfm_get_weights", "labfm_apply", "labfm_step",
-               "labfm_step_burgers", "labfm_solve", "labfm_build_neighbours_noalloc", "labfm_get_build_info"]
+               "labfm_step_burgers", "labfm_solve", "labfm_solve_neumann", "labfm_build_neighbours_noalloc",
+               "labfm_get_build_info"]
 NOALLOC_MAX_NODES = 262144  # LABFM_NOALLOC_MAX_NODES
 
 _lib = None
@@ -89,6 +90,8 @@ def load_library(path: str | None = None, build_if_missing: bool = False):
     lib.labfm_step_burgers.restype = I
     lib.labfm_solve.argtypes = [P, I, P, P, P, D, I, ct.POINTER(I), ct.POINTER(D)]
     lib.labfm_solve.restype = I
+    lib.labfm_solve_neumann.argtypes = [P, I, P, P, P, I64, P, P, P, I, I, D, I, ct.POINTER(I), ct.POINTER(D)]
+    lib.labfm_solve_neumann.restype = I
     lib.labfm_build_neighbours_noalloc.argtypes = [I, P, I64, P, P, I, P, P, P, P, I64, ct.POINTER(I64)]
     lib.labfm_build_neighbours_noalloc.restype = I
     lib.labfm_get_build_info.argtypes = [P, ct.POINTER(_BuildInfo)]
@@ -315,19 +318,35 @@ class Labfm:
                                                 int(nsteps), pz))
         return u, v
 
-    def solve(self, op: int, f, phi, dirichlet=None, tol: float = 1e-10, max_iter: int = 10000):
+    def solve(self, op: int, f, phi, dirichlet=None, tol: float = 1e-10, max_iter: int = 10000, neumann=None):
         """Solve A Phi = F (Sec. 5.2, eq. poisson_system) with the rows of operator `op` and
         identity rows where ``dirichlet`` is set, by Jacobi-preconditioned BiCGStab; phi (float64,
-        the initial guess) is overwritten.  Returns (iterations, true relative residual); raises
-        LabfmError(LABFM_ERR_NOT_CONVERGED) if the tolerance is not reached."""
+        the initial guess) is overwritten.  ``neumann`` = (ghost, parent, normal, op_x, op_y) adds
+        the Neumann ghost-node rows (labfm_solve_neumann): cuda int64 [n_ghost] ghost and parent
+        node indices, cuda float64 [n_ghost, 2] normals, and the operator indices of d/dx and d/dy.
+        Returns (iterations, true relative residual); raises LabfmError(LABFM_ERR_NOT_CONVERGED) if
+        the tolerance is not reached."""
         torch = _torch()
         pf = self._dev(f, torch.float64, "f", self.n)
         pp = self._dev(phi, torch.float64, "phi", self.n)
         pd = None if dirichlet is None else self._dev(dirichlet, torch.uint8, "dirichlet", self.n)
-        self._sync_stream()
         iters, resid = ct.c_int(0), ct.c_double(0.0)
-        st = self.lib.labfm_solve(self._ctx, int(op), pf, pp, pd, float(tol), int(max_iter), ct.byref(iters),
-                                  ct.byref(resid))
+        if neumann is None:
+            self._sync_stream()
+            st = self.lib.labfm_solve(self._ctx, int(op), pf, pp, pd, float(tol), int(max_iter), ct.byref(iters),
+                                      ct.byref(resid))
+        else:
+            ghost, parent, normal, op_x, op_y = neumann
+            ng = ghost.numel()
+            pg = self._dev(ghost, torch.int64, "ghost")
+            pa = self._dev(parent, torch.int64, "parent")
+            pn = self._dev(normal, torch.float64, "normal")
+            if parent.numel() != ng or normal.numel() != 2 * ng:
+                raise ValueError("ghost, parent and normal must describe the same n_ghost rows")
+            self._sync_stream()
+            st = self.lib.labfm_solve_neumann(self._ctx, int(op), pf, pp, pd, int(ng), pg, pa, pn, int(op_x),
+                                              int(op_y), float(tol), int(max_iter), ct.byref(iters),
+                                              ct.byref(resid))
         self.last_solve = (iters.value, resid.value)
         self._check(st)
         return iters.value, resid.value

@@ -222,7 +222,7 @@ void labfm_destroy(labfm_ctx *ctx)
                       &ctx->cell_nodes, &ctx->counts, &ctx->scan_tmp, &ctx->misc, &ctx->w,
                       &ctx->status_tmp, &ctx->wtilde, &ctx->mscratch, &ctx->mrecs, &ctx->mwstore, &ctx->mfallback, &ctx->wcomb, &ctx->rk_acc,
                       &ctx->rk_stage_a, &ctx->rk_stage_b, &ctx->wburg, &ctx->bu_acc, &ctx->bu_stage_a,
-                      &ctx->bu_stage_b, &ctx->sol_w, &ctx->sol_vec, &ctx->sol_part};
+                      &ctx->bu_stage_b, &ctx->sol_w, &ctx->sol_vec, &ctx->sol_part, &ctx->sol_gmap, &ctx->sol_wg};
     for (DevBuf *b : bufs) b->release();
     ctx->graph.release();
     ctx->graph_burgers.release();
@@ -377,7 +377,34 @@ labfm_status labfm_solve(labfm_ctx *ctx, int op, const double *f, double *phi, c
     if (!f || !phi) return fail(ctx, LABFM_ERR_ARG, "null f or phi");
     if ((const void *)f == (const void *)phi) return fail(ctx, LABFM_ERR_ARG, "f and phi must be distinct buffers");
     if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(ctx, LABFM_ERR_ARG, "need tol > 0 and max_iter >= 1");
-    return run_solve(ctx, op, f, phi, dirichlet, tol, max_iter, iters_out, resid_out);
+    return run_solve(ctx, op, f, phi, dirichlet, SolveNeumann{}, tol, max_iter, iters_out, resid_out);
+}
+
+labfm_status labfm_solve_neumann(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet,
+                                 int64_t n_ghost, const int64_t *ghost, const int64_t *parent, const double *normal,
+                                 int op_x, int op_y, double tol, int max_iter, int *iters_out, double *resid_out)
+{
+    if (!ctx) return LABFM_ERR_ARG;
+    ctx->err.clear();
+    if (!ctx->have_weights) return fail(ctx, LABFM_ERR_STATE, "labfm_build_weights must come first");
+    if (op < 0 || op >= ctx->n_ops) return fail(ctx, LABFM_ERR_ARG, "op must index a built operator");
+    if (!f || !phi) return fail(ctx, LABFM_ERR_ARG, "null f or phi");
+    if ((const void *)f == (const void *)phi) return fail(ctx, LABFM_ERR_ARG, "f and phi must be distinct buffers");
+    if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(ctx, LABFM_ERR_ARG, "need tol > 0 and max_iter >= 1");
+    if (n_ghost < 0 || n_ghost > ctx->n) return fail(ctx, LABFM_ERR_ARG, "need 0 <= n_ghost <= n");
+    SolveNeumann nm;
+    if (n_ghost > 0) {
+        if (!ghost || !parent || !normal) return fail(ctx, LABFM_ERR_ARG, "null ghost, parent or normal");
+        if (op_x < 0 || op_x >= ctx->n_ops || op_y < 0 || op_y >= ctx->n_ops)
+            return fail(ctx, LABFM_ERR_ARG, "op_x and op_y must index built operators");
+        nm.n_ghost = n_ghost;
+        nm.ghost = ghost;
+        nm.parent = parent;
+        nm.normal = normal;
+        nm.op_x = op_x;
+        nm.op_y = op_y;
+    }
+    return run_solve(ctx, op, f, phi, dirichlet, nm, tol, max_iter, iters_out, resid_out);
 }
 
 labfm_status labfm_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int field_dtype, double dt,

@@ -96,7 +96,7 @@ struct labfm_ctx {
     labfm::StepGraph graph_burgers;
 
     // implicit solves (BiCGStab): operator weights as one FP64 stream, nine vectors, partial sums
-    labfm::DevBuf sol_w, sol_vec, sol_part;
+    labfm::DevBuf sol_w, sol_vec, sol_part, sol_gmap, sol_wg;  // sol_gmap/sol_wg: Neumann ghost rows
 
     // launch shapes chosen by the apply / RK4 autotuner:
     // key (kind, n_ops, dtypes, size class of n, mean stencil size) -> (G << 8) | UNR
@@ -160,8 +160,15 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
 labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops, const double *C,
                        int precision, int weight_dtype, int32_t *node_status, int64_t *n_bad_out);
 cudaError_t launch_apply(labfm_ctx *ctx, uint32_t op_mask, const void *f, int field_dtype, void *out);
-labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet, double tol,
-                       int max_iter, int *iters_out, double *resid_out);
+// Neumann ghost rows of an implicit solve (Sec. 5.2); n_ghost = 0: none
+struct SolveNeumann {
+    int64_t n_ghost = 0;
+    const int64_t *ghost = nullptr, *parent = nullptr;  // device [n_ghost]
+    const double *normal = nullptr;                     // device [n_ghost][2]
+    int op_x = 0, op_y = 0;
+};
+labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet,
+                       const SolveNeumann &nm, double tol, int max_iter, int *iters_out, double *resid_out);
 labfm_status run_step_burgers(labfm_ctx *ctx, const double *beta, void *u, void *v, int field_dtype, double dt,
                               int64_t nsteps, const uint8_t *frozen);
 labfm_status run_step(labfm_ctx *ctx, const double *beta, void *u, int field_dtype, double dt, int64_t nsteps,

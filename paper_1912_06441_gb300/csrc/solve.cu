@@ -1,7 +1,9 @@
 // Implicit solves with the global operator matrix of Sec. 5.2 (eq. poisson_system):
 //   A_ij = w^d_ji (j != i),  A_ii = -sum_j w^d_ji,   so (A x)_i = A_ii x_i + sum_j w^d_ji x_j = L^d_i(x),
-// with Dirichlet rows (A_bb = 1, A_bj = 0, F_b = g_b) where the caller's mask is set.  The matrix
-// is never formed: its product is a stencil sum over the context's CSR stencils.
+// with Dirichlet rows (A_bb = 1, A_bj = 0, F_b = g_b) where the caller's mask is set, and Neumann
+// ghost rows (A_gj = n_x w^x_jb + n_y w^y_jb over the stencil of the ghost's parent b, A_gb = minus
+// their sum, F_g = the normal derivative at b).  The matrix is never formed: its product is a
+// stencil sum over the context's CSR stencils.
 //
 // Solver: stabilised bi-conjugate gradients (van der Vorst, SIAM J. Sci. Stat. Comput. 13, 1992)
 // with a Jacobi preconditioner M = diag(A), the preconditioned form with y = M^-1 p, z = M^-1 s:
@@ -174,9 +176,111 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_setup(int64_t n, const 
     dinv[i] = fixed ? 1.0 : (a != 0.0 && isfinite(1.0 / a) ? 1.0 / a : 1.0);
 }
 
+// Neumann ghost rows (Sec. 5.2): gmap[ghost[g]] = g (gmap starts at -1), with the checks the host
+// reads back in flag: bit 0 an index out of range or a ghost that is its own parent, bit 1 a
+// ghost listed twice, bit 2 a ghost row also marked Dirichlet, bit 3 a non-finite normal.
+__global__ void k_ghost_map(int64_t n, int64_t n_ghost, const int64_t *__restrict__ ghost,
+                            const int64_t *__restrict__ parent, const double *__restrict__ normal,
+                            const uint8_t *__restrict__ dirichlet, int32_t *__restrict__ gmap,
+                            unsigned int *__restrict__ flag)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_ghost) return;
+    const int64_t gi = ghost[g], b = parent[g];
+    if (!isfinite(normal[2 * g]) || !isfinite(normal[2 * g + 1])) atomicOr(flag, 8u);
+    if (gi < 0 || gi >= n || b < 0 || b >= n || gi == b) {
+        atomicOr(flag, 1u);
+        return;
+    }
+    if (dirichlet && dirichlet[gi]) atomicOr(flag, 4u);
+    if (atomicCAS(&gmap[gi], -1, (int)g) != -1) atomicOr(flag, 2u);
+}
+
+// goff[g] = sum over g' < g of the stencil size of parent[g'] (where ghost g's weights start in
+// the ghost weight stream), goff[n_ghost] the total; one block, each thread a contiguous run of
+// ghosts, then a scan of the per-thread sums in shared memory.  A parent out of range counts 0
+// (k_ghost_map has flagged it and the solve stops before any use).
+constexpr int GHOST_SCAN_THREADS = 1024;
+__global__ void __launch_bounds__(GHOST_SCAN_THREADS) k_ghost_offsets(int64_t n, int64_t n_ghost,
+                                                                      const int64_t *__restrict__ parent,
+                                                                      const int64_t *__restrict__ row_ptr,
+                                                                      int64_t *__restrict__ goff)
+{
+    __shared__ int64_t sh[GHOST_SCAN_THREADS];
+    const int64_t per = (n_ghost + GHOST_SCAN_THREADS - 1) / GHOST_SCAN_THREADS;
+    const int64_t g0 = (int64_t)threadIdx.x * per, g1 = g0 + per < n_ghost ? g0 + per : n_ghost;
+    auto size_of = [&](int64_t g) -> int64_t {
+        const int64_t b = parent[g];
+        return (b >= 0 && b < n) ? row_ptr[b + 1] - row_ptr[b] : 0;
+    };
+    int64_t run = 0;
+    for (int64_t g = g0; g < g1; g++) run += size_of(g);
+    sh[threadIdx.x] = run;
+    __syncthreads();
+    for (int o = 1; o < GHOST_SCAN_THREADS; o <<= 1) {  // inclusive scan (Hillis-Steele)
+        const int64_t add = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int64_t at = sh[threadIdx.x] - run;  // exclusive prefix of this thread's run
+    for (int64_t g = g0; g < g1; g++) {
+        goff[g] = at;
+        at += size_of(g);
+    }
+    if (threadIdx.x == GHOST_SCAN_THREADS - 1) goff[n_ghost] = sh[threadIdx.x];
+}
+
+// The ghost rows' weights and diagonals: row ghost[g] is n_x L^(op_x) + n_y L^(op_y) at the
+// parent b (Sec. 5.2): entry e of b's stencil gets c_e = n_x w^(op_x)_e + n_y w^(op_y)_e
+// (into wdg from goff[g]), the column of b gets -sum_e c_e (adiag), and the Jacobi scaling uses
+// the row's true diagonal, the c_e of the ghost itself within b's stencil (1 if it is absent or
+// zero).  SOLVE_G lanes per ghost; runs after k_solve_setup, whose values for these rows it
+// replaces.
+template <class WT>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_solve_setup_ghost(
+    int64_t n_ghost, const int64_t *__restrict__ ghost, const int64_t *__restrict__ parent,
+    const double *__restrict__ normal, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const WT *__restrict__ w, int n_ops, int op_x, int op_y, const int64_t *__restrict__ goff,
+    double *__restrict__ wdg, double *__restrict__ adiag, double *__restrict__ dinv)
+{
+    const int lane = threadIdx.x & (SOLVE_G - 1);
+    const int64_t g = ((int64_t)blockIdx.x * SOLVE_THREADS + threadIdx.x) / SOLVE_G;
+    double sum = 0.0, diag = 0.0;
+    int64_t gi = 0;
+    if (g < n_ghost) {
+        gi = ghost[g];
+        const int64_t b = parent[g];
+        const double nx = normal[2 * g], ny = normal[2 * g + 1];
+        const int64_t rs = row_ptr[b], re = row_ptr[b + 1], o = goff[g] - rs;
+        for (int64_t e = rs + lane; e < re; e += SOLVE_G) {
+            const double v = nx * (double)w[e * n_ops + op_x] + ny * (double)w[e * n_ops + op_y];
+            wdg[o + e] = v;
+            sum += v;
+            if (col[e] == gi) diag += v;
+        }
+    }
+    for (int o = SOLVE_G >> 1; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        diag += __shfl_xor_sync(0xffffffffu, diag, o);
+    }
+    if (g >= n_ghost || lane != 0) return;
+    adiag[gi] = -sum;
+    dinv[gi] = (diag != 0.0 && isfinite(1.0 / diag)) ? 1.0 / diag : 1.0;
+}
+
+// The ghost rows as the product kernel reads them (all null when there are none)
+struct GhostRows {
+    const int32_t *gmap = nullptr;   // [n]: ghost ordinal of row i, or -1
+    const int64_t *parent = nullptr; // [n_ghost]
+    const int64_t *goff = nullptr;   // [n_ghost + 1]
+    const double *wdg = nullptr;     // ghost weight stream
+};
+
 // out = A x with the matrix in its global form (Sec. 5.2): out_i = A_ii x_i + sum_j w_ji x_j, one
-// FP64 multiply-add per stencil entry (Dirichlet rows: out_i = x_i); G lanes per node with UNR
-// entries in flight per lane; fused partial dot products (a1 . out), (out . out) into
+// FP64 multiply-add per stencil entry (Dirichlet rows: out_i = x_i; a Neumann ghost row: the
+// stencil of its parent b with the ghost weights, and the diagonal term on x_b); G lanes per node
+// with UNR entries in flight per lane; fused partial dot products (a1 . out), (out . out) into
 // part[3 block + 0, 2]
 template <int G, int UNR>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const int64_t *__restrict__ row_ptr,
@@ -187,19 +291,28 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const i
                                                              const double *__restrict__ x, double *__restrict__ out,
                                                              const double *__restrict__ a1, double *__restrict__ part,
                                                              int step, int nblk2, const double *__restrict__ part2,
-                                                             SolveState *__restrict__ st)
+                                                             SolveState *__restrict__ st, GhostRows gr)
 {
     if (st && st->done) return;
     __shared__ double sh[2 * SOLVE_THREADS];
     const int lane = threadIdx.x & (G - 1);
     const int64_t i = ((int64_t)blockIdx.x * SOLVE_THREADS + threadIdx.x) / G;
     const bool live = i < n;
-    int64_t rs = 0, re = 0;
-    double xi = 0.0;
+    int64_t rs = 0, re = 0, woff = 0;
+    const double *wrow = wd;
+    double xi = 0.0;  // x at the row's diagonal column (i, or a ghost row's parent)
     if (live) {
-        rs = row_ptr[i];
-        re = row_ptr[i + 1];
-        xi = x[i];
+        int64_t src = i;
+        int gidx = -1;
+        if (gr.gmap) gidx = gr.gmap[i];
+        if (gidx >= 0) src = gr.parent[gidx];
+        rs = row_ptr[src];
+        re = row_ptr[src + 1];
+        xi = x[src];
+        if (gidx >= 0) {
+            wrow = gr.wdg;
+            woff = gr.goff[gidx] - rs;
+        }
     }
     double acc = 0.0;
     for (int64_t base = rs; base < re; base += G * UNR) {
@@ -209,7 +322,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_spmv(int64_t n, const i
         for (int q = 0; q < UNR; q++) {
             const int64_t e = base + q * G + lane;
             cj[q] = e < re ? __ldcs(col + e) : -1;
-            wv[q] = e < re ? __ldcs(wd + e) : 0.0;
+            wv[q] = e < re ? __ldcs(wrow + (e + woff)) : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < UNR; q++)
@@ -303,21 +416,23 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve_vec(int64_t n, int phas
 template <int G, int UNR>
 cudaError_t launch_spmv_t(int64_t n, const int64_t *rp, const int32_t *cl, const double *wd, const double *adiag,
                           const uint8_t *dirichlet, const double *x, double *out, const double *a1, double *part,
-                          int step, int nblk2, const double *part2, SolveState *st, cudaStream_t q)
+                          int step, int nblk2, const double *part2, SolveState *st, const GhostRows &gr,
+                          cudaStream_t q)
 {
     const unsigned blocks = (unsigned)((n * G + SOLVE_THREADS - 1) / SOLVE_THREADS);
     k_solve_spmv<G, UNR><<<blocks, SOLVE_THREADS, 0, q>>>(n, rp, cl, wd, adiag, dirichlet, x, out, a1, part, step,
-                                                          nblk2, part2, st);
+                                                          nblk2, part2, st, gr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spmv(int G, int UNR, int64_t n, const int64_t *rp, const int32_t *cl, const double *wd,
                         const double *adiag, const uint8_t *dirichlet, const double *x, double *out, const double *a1,
-                        double *part, int step, int nblk2, const double *part2, SolveState *st, cudaStream_t q)
+                        double *part, int step, int nblk2, const double *part2, SolveState *st, const GhostRows &gr,
+                        cudaStream_t q)
 {
 #define LABFM_SPMV_CASE(g, u)                                                                                   \
     if (G == g && UNR == u) return launch_spmv_t<g, u>(n, rp, cl, wd, adiag, dirichlet, x, out, a1, part, step, \
-                                                       nblk2, part2, st, q);
+                                                       nblk2, part2, st, gr, q);
     LABFM_SPMV_CASE(4, 2) LABFM_SPMV_CASE(4, 4) LABFM_SPMV_CASE(4, 8)
     LABFM_SPMV_CASE(8, 2) LABFM_SPMV_CASE(8, 4) LABFM_SPMV_CASE(8, 8)
     LABFM_SPMV_CASE(16, 2) LABFM_SPMV_CASE(16, 4) LABFM_SPMV_CASE(16, 8)
@@ -327,8 +442,8 @@ cudaError_t launch_spmv(int G, int UNR, int64_t n, const int64_t *rp, const int3
 
 }  // namespace
 
-labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet, double tol,
-                       int max_iter, int *iters_out, double *resid_out)
+labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, const uint8_t *dirichlet,
+                       const SolveNeumann &nm, double tol, int max_iter, int *iters_out, double *resid_out)
 {
     cudaStream_t s = ctx->stream;
     const int64_t n = ctx->n, nnz = ctx->nnz;
@@ -354,6 +469,49 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
         k_solve_setup<float><<<nblk_setup, SOLVE_THREADS, 0, s>>>(n, rp, ctx->w.as<float>(), ctx->n_ops, op,
                                                               ctx->sol_w.as<double>(), dinv, adiag, dirichlet, f, phi);
     LABFM_CUDA_TRY(ctx, cudaGetLastError());
+    // Neumann ghost rows: map, checks and weight offsets, read back with one synchronisation;
+    // then their weights and diagonals replace what the setup wrote for those rows
+    GhostRows gr;
+    if (nm.n_ghost > 0) {
+        const int64_t ng = nm.n_ghost;
+        const size_t map_bytes = ((sizeof(int32_t) * (size_t)n + 15) / 16) * 16;
+        LABFM_CUDA_TRY(ctx, ctx->sol_gmap.reserve(map_bytes + sizeof(int64_t) * (size_t)(ng + 1) + 16));
+        int32_t *gmap = ctx->sol_gmap.as<int32_t>();
+        int64_t *goff = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(gmap) + map_bytes);
+        unsigned int *gflag = reinterpret_cast<unsigned int *>(goff + ng + 1);
+        LABFM_CUDA_TRY(ctx, cudaMemsetAsync(gmap, 0xff, sizeof(int32_t) * (size_t)n, s));  // -1
+        LABFM_CUDA_TRY(ctx, cudaMemsetAsync(gflag, 0, sizeof(unsigned int), s));
+        k_ghost_map<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(n, ng, nm.ghost, nm.parent, nm.normal, dirichlet,
+                                                                 gmap, gflag);
+        k_ghost_offsets<<<1, GHOST_SCAN_THREADS, 0, s>>>(n, ng, nm.parent, rp, goff);
+        LABFM_CUDA_TRY(ctx, cudaGetLastError());
+        unsigned long long *hs = (unsigned long long *)ctx->host_small;
+        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(&hs[0], goff + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        LABFM_CUDA_TRY(ctx, cudaMemcpyAsync(&hs[1], gflag, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        const unsigned flag = (unsigned)(hs[1] & 0xffffffffull);
+        if (flag & 1u) return fail(ctx, LABFM_ERR_ARG, "a ghost or parent index is out of range, or a ghost is its own parent");
+        if (flag & 2u) return fail(ctx, LABFM_ERR_ARG, "a ghost row is listed twice");
+        if (flag & 4u) return fail(ctx, LABFM_ERR_ARG, "a ghost row is also a Dirichlet row");
+        if (flag & 8u) return fail(ctx, LABFM_ERR_ARG, "a ghost normal is not finite");
+        const int64_t total = (int64_t)hs[0];
+        LABFM_CUDA_TRY(ctx, ctx->sol_wg.reserve(sizeof(double) * (size_t)(total > 0 ? total : 1)));
+        double *wdg = ctx->sol_wg.as<double>();
+        const unsigned gblk = (unsigned)((ng * SOLVE_G + SOLVE_THREADS - 1) / SOLVE_THREADS);
+        if (ctx->wdtype == LABFM_F64)
+            k_solve_setup_ghost<double><<<gblk, SOLVE_THREADS, 0, s>>>(ng, nm.ghost, nm.parent, nm.normal, rp, cl,
+                                                                     ctx->w.as<double>(), ctx->n_ops, nm.op_x,
+                                                                     nm.op_y, goff, wdg, adiag, dinv);
+        else
+            k_solve_setup_ghost<float><<<gblk, SOLVE_THREADS, 0, s>>>(ng, nm.ghost, nm.parent, nm.normal, rp, cl,
+                                                                    ctx->w.as<float>(), ctx->n_ops, nm.op_x,
+                                                                    nm.op_y, goff, wdg, adiag, dinv);
+        LABFM_CUDA_TRY(ctx, cudaGetLastError());
+        gr.gmap = gmap;
+        gr.parent = nm.parent;
+        gr.goff = goff;
+        gr.wdg = wdg;
+    }
     SolveState init{};
     init.tol2 = tol * tol;
     init.max_iter = max_iter;
@@ -385,7 +543,7 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
                         for (int rep = 0; rep < 2 && te == cudaSuccess; rep++) {  // warm-up, then timed
                             if (rep) cudaEventRecord(e0, s);
                             te = launch_spmv(gs[gi], us[ui], n, rp, cl, wd, adiag, dirichlet, f, t, nullptr, part, -1,
-                                             0, nullptr, nullptr, s);
+                                             0, nullptr, nullptr, gr, s);
                             if (rep) cudaEventRecord(e1, s);
                         }
                         float ms = 0.0f;
@@ -407,7 +565,7 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
     // step: the scalars the last block forms (-1: none, and no gating on the state)
     auto spmv = [&](cudaStream_t q, const double *x, double *out, const double *a1, int step) {
         launch_spmv(G, UNR, n, rp, cl, wd, adiag, dirichlet, x, out, a1, part, step, step == 4 ? nblk_vec : 0,
-                    step == 4 ? part2 : nullptr, step >= 0 ? st : nullptr, q);
+                    step == 4 ? part2 : nullptr, step >= 0 ? st : nullptr, gr, q);
     };
     auto vec = [&](cudaStream_t q, int phase) {
         k_solve_vec<<<nblk_vec, SOLVE_THREADS, 0, q>>>(n, phase, f, phi, r, rhat, p, v, y, sv, z, t, dinv,
@@ -442,11 +600,16 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "BiCGStab chunk capture");
     }
-    // Chunks of iterations until the device flag ends them; then the true residual.  The
-    // recurrence residual drifts from the true one in finite precision: when the recurrence
-    // says converged but the true residual is above tol, BiCGStab restarts from the current
-    // iterate (r = F - A Phi, r^ = r), at most MAX_RESTARTS times within max_iter in total.
-    constexpr int MAX_RESTARTS = 4;
+    // Chunks of iterations until the device flag ends them; then the true residual.  BiCGStab
+    // restarts from the current iterate (r = F - A Phi, r^ = r), at most MAX_RESTARTS times
+    // within max_iter in total, in two cases: the recurrence residual, which drifts from the
+    // true one in finite precision, says converged while the true residual is above tol; or the
+    // iteration broke down (rho = (r^, r), (r^, v) or omega vanished or was not finite) with a
+    // finite iterate.  The second is the usual remedy for a breakdown: the shadow residual r^
+    // has become orthogonal to the Krylov space, and a fresh r^ = r starts a new one.  (No
+    // launch after the one that flagged the breakdown updates Phi, except when the residual
+    // norm itself was not finite, which the finite-residual condition excludes.)
+    constexpr int MAX_RESTARTS = 8;
     SolveState h{};
     int total = 0, restarts = 0;
     double resid = 0.0;
@@ -476,7 +639,8 @@ labfm_status run_solve(labfm_ctx *ctx, int op, const double *f, double *phi, con
             bb += hp[3 * k + 1];
         }
         resid = std::sqrt(rr) / (bb > 0.0 ? std::sqrt(bb) : 1.0);
-        if (h.done == 1 && std::isfinite(resid) && resid > tol && restarts < MAX_RESTARTS && total < max_iter) {
+        const bool drifted = h.done == 1 && resid > tol, broke_down = h.done == 2;
+        if ((drifted || broke_down) && std::isfinite(resid) && restarts < MAX_RESTARTS && total < max_iter) {
             restarts++;
             init.max_iter = max_iter - total;
             le = cudaMemcpyAsync(st, &init, sizeof(SolveState), cudaMemcpyHostToDevice, s);

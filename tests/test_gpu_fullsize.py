@@ -237,3 +237,27 @@ def test_rk4_lattice2048_order8():
         errs[dt_name] = np.abs(got - exact).max()
     assert errs["f64"] < 1e-7, errs
     assert errs["f32"] < 1e-5, errs
+
+
+def test_rk4_oracle_leg_2048_subsample_and_independent_256():
+    """The time-stepping workload's oracle leg (as bench.py reports it): at the 65,536 nodes of
+    the 2048^2 set's 256^2 subsample the GPU's stencil rows equal the oracle's bit for bit and
+    its FP64 weights agree with the FP64 oracle's (normwise per node, and derivatives relative to
+    the sum of their terms); on an independent 256^2 set with the same parameters, 1000 graph-
+    replayed RK4 steps with FP64 fields equal the oracle's 1000 steps to 1e-11 of max|u|, and
+    with FP32 fields (FP64 or FP32 weights) to the FP32 rounding floor, 5e-6."""
+    import torch
+
+    import bench
+    import paper_1912_06441_gb300 as P
+
+    r = bench.rk4_oracle_leg(torch, P, torch.device("cuda", 0), 0)
+    sub = r["subsample_2048"]
+    assert sub["stencils_bit_exact"] and sub["oracle_status_ok"] == sub["nodes"] == 65536
+    assert max(sub["weights_normwise"]["max"]) <= 1e-9, sub["weights_normwise"]
+    assert max(sub["deriv_err_over_term_sum"]["max"]) <= 1e-11, sub["deriv_err_over_term_sum"]
+    rk = r["independent_256_rk4"]
+    assert rk["gpu_f64_fields_f64_weights"]["max_diff_vs_oracle"] <= 1e-11, rk
+    for key in ("gpu_f32_fields_f64_weights", "gpu_f32_fields_f32_weights"):
+        assert rk[key]["max_diff_vs_oracle"] <= 5e-6, rk
+    assert rk["oracle_l2_err_vs_exact"] < 1e-7

@@ -157,3 +157,105 @@ def test_solve_all_dirichlet_rows_is_exact_and_immediate():
     iters, resid = L.solve(0, torch.from_numpy(f).to(dev), phi, allrows, tol=1e-12)
     assert iters == 0 and resid == 0.0
     assert np.array_equal(phi.cpu().numpy(), f)
+
+
+def _neumann_gpu(nside, field, weight_dtype="f64", tol=1e-13):
+    """labfm_solve_neumann on the Neumann square (Dirichlet walls at x = 0, 1; ghost rows for the
+    walls y = 0, 1), k = 4, weights of (d/dx, d/dy, nabla^2) built on the GPU, and the oracle's
+    direct solve of the same system on the oracle's weights."""
+    import torch
+
+    from tests import test_oracle_pins as OP
+
+    k = 4
+    q, rp, col, r, ex, f = OP.neumann_problem(nside, k, field)
+    L, grp, gcol, w, status, _ = G.gpu_run(q.ns, k, ("dx", "dy", "lap"), rbf="quadratic", abf_form="dw0",
+                                           weight_dtype=weight_dtype)
+    assert np.array_equal(grp, rp) and np.array_equal(gcol, col)
+    assert np.array_equal(status, r["status"])
+    dev = torch.device("cuda", 0)
+    phi = torch.zeros(q.ns.n, dtype=torch.float64, device=dev)
+    nm = (torch.from_numpy(q.ghost).to(dev), torch.from_numpy(q.parent).to(dev),
+          torch.from_numpy(q.normal).to(dev), 0, 1)
+    dm = q.dirichlet.astype(np.uint8)
+    iters, resid = L.solve(2, torch.from_numpy(f).to(dev), phi, torch.from_numpy(dm).to(dev), tol=tol,
+                           max_iter=20000, neumann=nm)
+    ref = oracle.solve_operator(rp, col, r["w"], 2, f, dm, neumann=(q.ghost, q.parent, q.normal, 0, 1))
+    return q, L, phi.cpu().numpy(), ref, ex, iters, resid
+
+
+def test_poisson_neumann_ghost_rows_match_oracle():
+    """Neumann ghost-node rows (Sec. 5.2) through labfm_solve_neumann: for a polynomial of degree
+    4 at k = 4 the GPU solution is the polynomial at every node, ghosts included (each row is
+    exact); for phi = sin(2x + 0.3) cos(3y - 0.2) on 41^2 nodes it equals the oracle's direct
+    solve of the same system to 1e-8 and meets the prescribed normal derivatives, and the error
+    against phi is that of the oracle's solution."""
+    from tests import test_oracle_pins as OP
+
+    q, L, phi, ref, ex, iters, resid = _neumann_gpu(21, OP._neumann_poly_field())
+    assert resid <= 1e-13 and iters > 0
+    assert np.abs(phi - ex).max() <= 1e-9 * np.abs(ex).max()
+    assert np.abs(phi - ref).max() <= 1e-9 * np.abs(ex).max()
+    L.close()
+    field = (lambda x, y: np.sin(2 * x + 0.3) * np.cos(3 * y - 0.2),
+             lambda x, y: 2 * np.cos(2 * x + 0.3) * np.cos(3 * y - 0.2),
+             lambda x, y: -3 * np.sin(2 * x + 0.3) * np.sin(3 * y - 0.2),
+             lambda x, y: -13 * np.sin(2 * x + 0.3) * np.cos(3 * y - 0.2))
+    q, L, phi, ref, ex, iters, resid = _neumann_gpu(41, field)
+    assert np.abs(phi - ref).max() <= 1e-8 * np.abs(ref).max()
+    assert np.array_equal(phi[q.dirichlet], ex[q.dirichlet])
+    keep = np.ones(q.ns.n, bool)
+    keep[q.ghost] = False
+    e_gpu = np.linalg.norm(phi[keep] - ex[keep]) / np.linalg.norm(ex[keep])
+    e_ref = np.linalg.norm(ref[keep] - ex[keep]) / np.linalg.norm(ex[keep])
+    assert abs(e_gpu - e_ref) <= 1e-3 * e_ref and e_gpu < 1e-5
+    # the normal derivative at each Neumann wall node, through the GPU's own d/dx, d/dy apply
+    import torch
+
+    d = L.apply(torch.from_numpy(phi).to(torch.device("cuda", 0))).cpu().numpy()
+    got = q.normal[:, 0] * d[0, q.parent] + q.normal[:, 1] * d[1, q.parent]
+    xb, yb = q.ns.xy[q.parent, 0], q.ns.xy[q.parent, 1]
+    want = q.normal[:, 0] * field[1](xb, yb) + q.normal[:, 1] * field[2](xb, yb)
+    assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
+
+
+def test_poisson_neumann_f32_weights():
+    """The ghost rows from FP32-stored weights (widened to FP64 in the solve): the operator changes
+    by ~1e-7 relative, which the solution follows."""
+    from tests import test_oracle_pins as OP
+
+    q, L, phi, ref, ex, iters, resid = _neumann_gpu(21, OP._neumann_poly_field(), weight_dtype="f32", tol=1e-12)
+    assert np.abs(phi - ref).max() <= 1e-4 * np.abs(ex).max()
+
+
+def test_solve_neumann_rejects_bad_ghost_rows():
+    """Ghost rows that index out of range, repeat a ghost, are their own parent or are also
+    Dirichlet rows are argument errors, checked on the device before the iteration."""
+    import torch
+
+    from paper_1912_06441_gb300 import LabfmError
+    from tests import test_oracle_pins as OP
+
+    k = 4
+    q, rp, col, r, ex, f = OP.neumann_problem(11, k, OP._neumann_poly_field())
+    L, *_ = G.gpu_run(q.ns, k, ("dx", "dy", "lap"), rbf="quadratic", abf_form="dw0")
+    dev = torch.device("cuda", 0)
+    fd = torch.from_numpy(f).to(dev)
+    dm = torch.from_numpy(q.dirichlet.astype(np.uint8)).to(dev)
+    nrm = torch.from_numpy(q.normal).to(dev)
+    gh = torch.from_numpy(q.ghost).to(dev)
+    pa = torch.from_numpy(q.parent).to(dev)
+    bad = {
+        "out of range": (gh.clone().fill_(q.ns.n), pa),
+        "repeated ghost": (torch.cat([gh[:1], gh[:-1]]), pa),
+        "own parent": (gh, gh),
+        "Dirichlet ghost": (torch.cat([torch.zeros(1, dtype=torch.int64, device=dev), gh[1:]]), pa),
+    }
+    for name, (g2, p2) in bad.items():
+        phi = torch.zeros(q.ns.n, dtype=torch.float64, device=dev)
+        with pytest.raises(LabfmError) as ei:
+            L.solve(2, fd, phi, dm, tol=1e-12, neumann=(g2, p2, nrm, 0, 1))
+        assert "ERR_ARG" in str(ei.value), name
+    phi = torch.zeros(q.ns.n, dtype=torch.float64, device=dev)
+    L.solve(2, fd, phi, dm, tol=1e-12, neumann=(gh, pa, nrm, 0, 1))  # the context is still usable
+    assert np.abs(phi.cpu().numpy() - ex).max() <= 1e-9 * np.abs(ex).max()

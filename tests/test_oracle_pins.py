@@ -239,6 +239,21 @@ def test_neighbours_vs_kdtree():
             assert list(mine) == theirs, i
 
 
+def test_large_set_neighbours_equal_the_brute_force():
+    """The kd-tree-proposed stencils for large node sets equal the brute force bit for bit:
+    periodic and non-periodic jittered lattices, a node set with ghosts outside the unit square,
+    a query subset, and a lattice without jitter (nodes exactly 2h apart sit on the strict
+    boundary of the predicate)."""
+    q = S.neumann_square(21, 2.0, 4, 0.5, seed=21).ns
+    cases = [(S.jittered_lattice(40, 2.2, 8, seed=5), None), (S.jittered_lattice(40, 2.2, 8, seed=6, periodic=False), None),
+             (q, None), (S.jittered_lattice(32, 2.0, 4, jitter=0.0, seed=1), None),
+             (S.jittered_lattice(48, 2.2, 8, jitter=0.1, seed=7), np.arange(0, 48 * 48, 37))]
+    for ns, queries in cases:
+        rp, col = oracle.neighbours(ns.xy, ns.h, ns.periodic, ns.lo, ns.hi, queries=queries)
+        rp2, col2 = oracle.neighbours_large(ns.xy, ns.h, ns.periodic, ns.lo, ns.hi, queries=queries)
+        assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
+
+
 # ------------------------------------------------------------------------ M, solve, weights
 
 
