@@ -27,8 +27,11 @@ __all__ = [
     "jittered_lattice",
     "variable_wall_nodes",
     "dirichlet_square",
-    "NeumannSquare",
+    "NeumannSet",
     "neumann_square",
+    "annulus_nodes",
+    "annulus_solution",
+    "annulus_source",
     "HeatSteadyField",
     "ColeBurgersSolution",
     "ColeHopf2DSolution",
@@ -244,13 +247,12 @@ def dirichlet_square(n_side: int, h_over_s: float = 2.0, k: int = 4, eps: float 
 
 
 @dataclass
-class NeumannSquare:
-    """The unit square of ``dirichlet_square`` with a Neumann boundary (Sec. 5.2) on its bottom
-    and top walls: ``ns`` holds the lattice nodes followed by one ghost node per Neumann wall
-    node.  ``dirichlet`` (bool [n]) marks the left and right walls (corners included);
-    ``ghost`` / ``parent`` (int64 [n_ghost]) pair each ghost node with its wall node b;
-    ``normal`` (float64 [n_ghost, 2]) is the unit normal at b pointing into the domain, so that
-    the ghost sits at r_b - n_b s."""
+class NeumannSet:
+    """A node set with Dirichlet and Neumann boundaries (Sec. 5.2): ``ns`` holds the nodes of the
+    domain followed by one ghost node per Neumann boundary node.  ``dirichlet`` (bool [n]) marks
+    the Dirichlet boundary nodes; ``ghost`` / ``parent`` (int64 [n_ghost]) pair each ghost node
+    with its boundary node b; ``normal`` (float64 [n_ghost, 2]) is the unit normal at b pointing
+    into the domain, so that the ghost sits at r_b - n_b s, s = ``spacing``."""
 
     ns: NodeSet
     dirichlet: np.ndarray
@@ -261,7 +263,7 @@ class NeumannSquare:
 
 
 def neumann_square(n_side: int, h_over_s: float = 2.0, k: int = 4, eps: float = 0.5,
-                   seed: int = 1, wall_band: int = 2) -> NeumannSquare:
+                   seed: int = 1, wall_band: int = 2) -> NeumannSet:
     """Node set for Poisson's equation with Dirichlet walls at x = 0, 1 and Neumann walls at
     y = 0, 1 (Sec. 5.2): the lattice of ``dirichlet_square`` (spacing s = 1/(n_side - 1),
     jitter beyond ``wall_band`` rows of a wall), and for every node b of the bottom and top
@@ -290,8 +292,94 @@ def neumann_square(n_side: int, h_over_s: float = 2.0, k: int = 4, eps: float = 
                  wall=np.concatenate([base.wall, np.zeros(ng, dtype=bool)]))
     dirichlet = np.zeros(n0 + ng, dtype=bool)
     dirichlet[:n0] = (i == 0) | (i == m - 1)
-    return NeumannSquare(ns=ns, dirichlet=dirichlet, ghost=ghost, parent=parent,
+    return NeumannSet(ns=ns, dirichlet=dirichlet, ghost=ghost, parent=parent,
                          normal=np.ascontiguousarray(normal), spacing=s)
+
+
+def annulus_nodes(m: int, k: int = 4, eps: float = 0.5, seed: int = 1, shift_iters: int = 10) -> NeumannSet:
+    """Node set of the annular Poisson problem of Sec. 5.2: the annulus 1/8 < r < 1/2 about the
+    origin (inner diameter H/4, outer diameter H, H = 1), spacing dr = 1/m (h/H = 2/m at
+    h = 2 dr), Dirichlet on the outer circle and Neumann on the inner one.  Following the paper's
+    construction: nodes at intervals of about dr along both circles; a noisy Cartesian fill of
+    spacing dr (each coordinate moved by U(-eps dr/sqrt(2), +eps dr/sqrt(2)), eps the maximum
+    displacement over dr) kept where dr/2 inside the domain; temporary ghosts, the same noisy
+    lattice in strips of width 2h outside both circles; ``shift_iters`` passes of the shifting
+    rule of Sec. 5.2 applied to the fill nodes,
+        r_i <- r_i + (dr^2 / h) sum_{j: |r_ji| < h} (|r_ji| / h - 1) r_ji / |r_ji|,  r_ji = r_j - r_i,
+    (all passes from the same positions of the previous pass, neighbours among every node); the
+    temporary ghosts are then dropped and one ghost per inner-circle node b is added at
+    r_b - n_b dr, n_b = r_b / |r_b| (into the domain).  h = 2 dr and order k at every node; the
+    box for the stencil search is [-1/2 - 2h, 1/2 + 2h]^2 (non-periodic)."""
+    from scipy.spatial import cKDTree
+
+    dr = 1.0 / m
+    h = 2.0 * dr
+    r_in, r_out = 0.125, 0.5
+    rings = []
+    for rad in (r_out, r_in):
+        cnt = max(3, int(round(2.0 * math.pi * rad / dr)))
+        th = 2.0 * math.pi * np.arange(cnt) / cnt
+        rings.append(np.stack([rad * np.cos(th), rad * np.sin(th)], axis=1))
+    outer, inner = rings
+    lim = r_out + 2.0 * h + dr
+    g = np.arange(-int(math.ceil(lim / dr)), int(math.ceil(lim / dr)) + 1) * dr
+    gx, gy = np.meshgrid(g, g, indexing="xy")
+    pts = np.stack([gx.ravel(), gy.ravel()], axis=1)
+    u = uniform01(seed, 2 * len(pts))
+    a = eps * dr / math.sqrt(2.0)
+    pts = pts + np.stack([(2.0 * u[0::2] - 1.0) * a, (2.0 * u[1::2] - 1.0) * a], axis=1)
+    rr = np.hypot(pts[:, 0], pts[:, 1])
+    fill = pts[(rr > r_in + 0.5 * dr) & (rr < r_out - 0.5 * dr)]
+    temp = pts[((rr > r_out + 0.5 * dr) & (rr < r_out + 2.0 * h)) | ((rr < r_in - 0.5 * dr) & (rr > r_in - 2.0 * h))]
+    fixed = np.concatenate([outer, inner, temp])
+    for _ in range(shift_iters):
+        allp = np.concatenate([fill, fixed])
+        tree = cKDTree(allp)
+        pairs = tree.query_pairs(h, output_type="ndarray")
+        pairs = pairs[pairs[:, 0] < len(fill)]  # i a fill node (the fill comes first)
+        i, j = pairs[:, 0], pairs[:, 1]
+        rji = allp[j] - allp[i]
+        d = np.hypot(rji[:, 0], rji[:, 1])
+        keep = (d < h) & (d > 0.0)
+        i, j, rji, d = i[keep], j[keep], rji[keep], d[keep]
+        f = ((d / h - 1.0) / d)[:, None] * rji
+        move = np.zeros_like(fill)
+        np.add.at(move, i, f)
+        jf = j < len(fill)  # the pair seen from the fill node j: r_ij = -r_ji
+        np.add.at(move, j[jf], -f[jf])
+        fill = fill + (dr * dr / h) * move
+    nodes = np.concatenate([outer, inner, fill])
+    n_out, n_in = len(outer), len(inner)
+    parent = np.arange(n_out, n_out + n_in, dtype=np.int64)
+    normal = inner / np.hypot(inner[:, 0], inner[:, 1])[:, None]
+    gxy = inner - normal * dr
+    n0 = len(nodes)
+    xy = np.ascontiguousarray(np.concatenate([nodes, gxy]))
+    n = len(xy)
+    ghost = np.arange(n0, n, dtype=np.int64)
+    dirichlet = np.zeros(n, dtype=bool)
+    dirichlet[:n_out] = True
+    wall = np.zeros(n, dtype=bool)
+    wall[:n_out + n_in] = True
+    box = r_out + 2.0 * h
+    ns = NodeSet(xy=xy, h=np.full(n, h), s=np.full(n, dr), order=np.full(n, k, dtype=np.int8), periodic=False,
+                 lo=(-box, -box), hi=(box, box), wall=wall)
+    return NeumannSet(ns=ns, dirichlet=dirichlet, ghost=ghost, parent=parent, normal=np.ascontiguousarray(normal),
+                      spacing=dr)
+
+
+def annulus_solution(x, y):
+    """Exact solution of the annular Poisson problem of Sec. 5.2: r sin(4 pi r) cos(3 theta)."""
+    r, th = np.hypot(x, y), np.arctan2(y, x)
+    return r * np.sin(4 * np.pi * r) * np.cos(3 * th)
+
+
+def annulus_source(x, y):
+    """Its source term as printed in Sec. 5.2 (the Laplacian of ``annulus_solution``):
+    [12 pi cos 4 pi r - (16 pi^2 r - 1/r) sin 4 pi r] cos 3 theta - (9/r) cos 3 theta sin 4 pi r."""
+    r, th = np.hypot(x, y), np.arctan2(y, x)
+    return ((12 * np.pi * np.cos(4 * np.pi * r) - (16 * np.pi ** 2 * r - 1 / r) * np.sin(4 * np.pi * r)) * np.cos(3 * th)
+            - 9 / r * np.cos(3 * th) * np.sin(4 * np.pi * r))
 
 
 # ----------------------------------------------------------------------------------

@@ -259,3 +259,36 @@ def test_solve_neumann_rejects_bad_ghost_rows():
     phi = torch.zeros(q.ns.n, dtype=torch.float64, device=dev)
     L.solve(2, fd, phi, dm, tol=1e-12, neumann=(gh, pa, nrm, 0, 1))  # the context is still usable
     assert np.abs(phi.cpu().numpy() - ex).max() <= 1e-9 * np.abs(ex).max()
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_poisson_annulus_matches_oracle(k):
+    """The annular problem of Sec. 5.2 (Dirichlet outer circle, Neumann inner circle by ghost
+    rows, quadratic ABFs, h/dr = 2) at h/H = 2/49 and 2/97: labfm_solve_neumann on the GPU's
+    weights equals the oracle's direct solve on the oracle's weights to 1e-8, and its error
+    against r sin(4 pi r) cos(3 theta) is the oracle's (so the printed table holds for it too)."""
+    import torch
+
+    from tests import test_oracle_pins as OP
+
+    dev = torch.device("cuda", 0)
+    for m in (49, 97):
+        q, rp, col, r, ex, f = OP.annulus_problem(m, k)
+        L, grp, gcol, w, status, _ = G.gpu_run(q.ns, k, ("dx", "dy", "lap"), rbf="quadratic", abf_form="dw0")
+        assert np.array_equal(grp, rp) and np.array_equal(gcol, col)
+        keep = np.ones(q.ns.n, bool)
+        keep[q.ghost] = False
+        assert (status[keep] == 0).all()
+        phi = torch.zeros(q.ns.n, dtype=torch.float64, device=dev)
+        nm = (torch.from_numpy(q.ghost).to(dev), torch.from_numpy(q.parent).to(dev),
+              torch.from_numpy(q.normal).to(dev), 0, 1)
+        L.solve(2, torch.from_numpy(f).to(dev), phi, torch.from_numpy(q.dirichlet.astype(np.uint8)).to(dev),
+                tol=1e-13, max_iter=50000, neumann=nm)
+        got = phi.cpu().numpy()
+        ref = oracle.solve_operator(rp, col, r["w"], 2, f, q.dirichlet.astype(np.uint8),
+                                    neumann=(q.ghost, q.parent, q.normal, 0, 1))
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (m, np.abs(got - ref).max())
+        e_gpu = np.linalg.norm(got[keep] - ex[keep]) / np.linalg.norm(ex[keep])
+        e_ref = np.linalg.norm(ref[keep] - ex[keep]) / np.linalg.norm(ex[keep])
+        assert abs(e_gpu - e_ref) <= 1e-4 * e_ref, (m, e_gpu, e_ref)
+        L.close()
