@@ -71,7 +71,8 @@ enum {
 /* Arithmetic of the moment-matrix assembly (Eq. disc_form) and solve (Eq. lsys). */
 enum {
     LABFM_PREC_FP64 = 0, /* everything in IEEE double */
-    /* X and W in double; M, its partially pivoted LU, Psi and W . Psi in double-float
+    /* X and W in double; M, its inverse (Gauss-Jordan elimination with partial pivoting), Psi
+     * and W . Psi in double-float
      * (pairs of FP32, ~48 bits, on the FP32 pipes); then iterative refinement on the
      * polynomial-reproduction residual C - sum_j X_j w_j computed in double (the moment
      * conditions of Sec. 3.1).  Default: adaptive per node.  With eta_t the relative size of the
@@ -196,9 +197,10 @@ typedef struct {
     /* per order k (index 1..8): threads that built one node in the FP64 kernel (64, 128: several
      * nodes per CTA; 256: one), as the build autotuner chose them; 0 for orders not built there */
     int32_t fp64_group_threads[LABFM_MAX_ORDER + 1];
-    /* per order k (index 1..8): threads per matrix row (2 or 4) of the mixed builds' double-float
+    /* per order k (index 1..8): threads per matrix row of the mixed builds' double-float
      * inversion, as the build autotuner chose them (timed once per (order, mean stencil size,
-     * n_ops, precision) like the FP64 group size); 0 for orders not built by the mixed kernels */
+     * n_ops, precision) like the FP64 group size): 1 = each row in the registers of one thread,
+     * 2 or 4 = the matrix in shared memory; 0 for orders not built by the mixed kernels */
     int32_t mixed_inv_threads_per_row[LABFM_MAX_ORDER + 1];
 } labfm_build_info;
 

@@ -706,7 +706,9 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
                 }
                 const int64_t nt = std::min<int64_t>(cnt, 16384);
                 float best = 1e30f;
-                for (int cand = 2; cand <= 4 && e == cudaSuccess; cand += 2) {
+                const int cands[3] = {1, 2, 4};  // threads per row: 1 = rows in registers
+                for (int ci = 0; ci < 3 && e == cudaSuccess; ci++) {
+                    const int cand = cands[ci];
                     e = launch_mixed_raw(k, list, nt, cand);  // warm-up
                     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
                     if (e == cudaSuccess) e = launch_mixed_raw(k, list, nt, cand);

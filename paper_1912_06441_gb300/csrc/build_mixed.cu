@@ -794,8 +794,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_mixed_assemble_tc(MixedArgs A
 }
 
 // ------------------------------------------------------------------------------------------
-// B: Gauss-Jordan inversion with partial pivoting, in double-float; one CTA per node with TPR
-// (2 or 4, chosen by the build autotuner) threads per row of the working matrix in shared memory:
+// B: Gauss-Jordan inversion with partial pivoting, in double-float.  Two forms, the build
+// autotuner choosing per order: each row in the registers of one thread (k_mixed_invert_rr,
+// below), or one CTA per node with TPR (2 or 4) threads per row of the working matrix in shared
+// memory:
 // thread t updates the columns q = h, h + TPR, h + 2 TPR, ... of row t / TPR (h = t % TPR), so
 // that TPR P lanes do work and each thread's update is 1/TPR of a row.  Zero columns pad P to a
 // multiple WC of TPR.  The row stride LDM (in 8-byte words) is TPR times an odd number, so the
@@ -951,6 +953,115 @@ __global__ void __launch_bounds__(InvCfg<p_of_k(K), TPR>::NT) k_mixed_invert(Mix
 {
     __shared__ InvShared<p_of_k(K), TPR> sh;
     for (int64_t li = blockIdx.x; li < A.n_list; li += gridDim.x) invert_node<K, TPR>(A, li, sh);
+}
+
+// The same Gauss-Jordan inversion with each row of M held in the registers of one thread (one
+// "thread per row"), NPC nodes per CTA.  Rows are not exchanged: the pivot of column c is the
+// largest |M[r][c]| (then the lowest r) over the rows not yet used as pivots, found with a
+// shared-memory atomicMax on (|hi| bits, ~r); every row then holds its columns c .. p-1 in
+// a[0 .. p-1-c] and the finished columns of the inverse behind them: the update
+//     a[k-1] = a[k] - f prow[k]  (k = 1 .. p-1),   a[p-1] = -f,   f = M[r][c] / pivot
+// (the pivot row: a[k-1] = a[k] / pivot, a[p-1] = 1 / pivot) shifts the row by one column, so
+// that every register index is fixed at compile time and the pivot column is always a[0].  With
+// E the product of the row operations, E M = Pi (the permutation of the pivot rows) and
+// M^-1 = Pi^T E: after p steps a[c] of row r is E[r][p_c], p_c the pivot row of column c, and
+// it is row s_r of the inverse (s_r the column row r was pivot of) at column p_c.  Against the
+// shared-memory version: one shared load (the broadcast pivot row) per multiply-add instead of
+// two loads and a store, and two barriers per column instead of three.
+// Nodes per CTA: 2, 5, 7, 8 for p = 44, 35, 27, 20 (88 of 96, 175 of 192, 189 of 192, 160 of 160
+// lanes busy).  CTAs per SM from a register budget of 2p + 40 per thread (the row's 2p floats and
+// the rest): at p = 44, 128 registers, five CTAs per SM, a few spilled values; a budget without
+// spills (151 registers, four CTAs per SM) measured 1 % slower.
+template <int P> struct RrCfg {
+    static constexpr int NPC = P > 40 ? 2 : (P > 30 ? 5 : (P > 24 ? 7 : 8));
+    static constexpr int NT = (NPC * P + 31) / 32 * 32;
+    static constexpr int MINB = 65536 / (NT * (2 * P + 40)) > 0 ? 65536 / (NT * (2 * P + 40)) : 1;
+};
+
+template <int P, int NPC> struct RrShared {
+    unsigned long long key[NPC][2];  // pivot candidates of columns of even / odd index
+    df prow[NPC][P];                 // the pivot row (a[1 ..] before the update)
+    df inv[NPC];                     // 1 / pivot
+    unsigned char pivrow[NPC][P];    // p_c
+};
+
+template <int K>
+__global__ void __launch_bounds__(RrCfg<p_of_k(K)>::NT, RrCfg<p_of_k(K)>::MINB) k_mixed_invert_rr(MixedArgs A)
+{
+    constexpr int P = p_of_k(K), NPC = RrCfg<P>::NPC;
+    __shared__ RrShared<P, NPC> sh;
+    const int t = threadIdx.x;
+    const int nl = t / P, r = t - nl * P;
+    const bool slot = nl < NPC;
+    for (int64_t g = blockIdx.x; g * NPC < A.n_list; g += gridDim.x) {
+        const int64_t li = g * NPC + nl;
+        bool active = slot && li < A.n_list;
+        if (active) active = A.flag[li] == 0;
+        df a[P];
+        if (active) {
+            const df *row = A.Mg + li * A.mstride + r * P;
+#pragma unroll
+            for (int k = 0; k < P; k++) a[k] = row[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < P; k++) a[k] = df{0.0f, 0.0f};
+        }
+        if (t < NPC) sh.key[t][0] = 0ull;
+        __syncthreads();
+        bool used = false, dead = false;
+        int mystep = 0;
+        for (int c = 0; c < P; c++) {
+            const int b = c & 1;
+            if (active && !used) {
+                const unsigned long long key = ((unsigned long long)__float_as_uint(fabsf(a[0].hi)) << 32) |
+                                               (unsigned long long)(0xffffffffu - (unsigned)r);
+                atomicMax(&sh.key[nl][b], key);
+            }
+            if (t < NPC) sh.key[t][b ^ 1] = 0ull;
+            __syncthreads();
+            const unsigned long long key = slot ? sh.key[nl][b] : 0ull;
+            const unsigned mag = (unsigned)(key >> 32);
+            const int pr = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+            // |pivot| zero, infinite or NaN (NaN bit patterns sort above every finite value)
+            if (!(mag > 0u && mag < 0x7f800000u)) dead = true;
+            const bool go = active && !dead;
+            if (go && r == pr) {
+#pragma unroll
+                for (int k = 1; k < P; k++) sh.prow[nl][k] = a[k];
+                sh.inv[nl] = df_recip(a[0]);
+                sh.pivrow[nl][c] = (unsigned char)r;
+                used = true;
+                mystep = c;
+            }
+            __syncthreads();
+            if (go) {
+                // one update for every row (no divergent branch for the pivot row): the pivot
+                // row clears its registers and takes f = -1/pivot, so that its a[k-1] =
+                // 0 - f prow[k] = prow[k] / pivot and a[p-1] = -f = 1/pivot
+                const df inv = sh.inv[nl];
+                df f = df_mul(a[0], inv);
+                if (r == pr) {
+                    f = df_neg(inv);
+#pragma unroll
+                    for (int k = 1; k < P; k++) a[k] = df{0.0f, 0.0f};
+                }
+                const df *pw = sh.prow[nl];
+#pragma unroll
+                for (int k = 1; k < P; k++) a[k - 1] = df_fms(f, pw[k], a[k]);
+                a[P - 1] = df_neg(f);
+            }
+        }
+        if (active) {
+            if (dead) {
+                if (r == 0) A.flag[li] = 1;
+            } else {
+                df *out = A.Mg + li * A.mstride + mystep * P;
+#pragma unroll
+                for (int c = 0; c < P; c++) out[sh.pivrow[nl][c]] = a[c];
+            }
+        }
+        __syncthreads();  // sh.pivrow and the keys are rewritten by the next group
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1285,7 +1396,10 @@ cudaError_t launch_mixed_k(const MixedArgs &a, int num_sms, bool tc, int inv_tpr
     if (tc) e = launch_tc(k_mixed_assemble_tc<K>, a, TcCfg<K>::smem, num_sms, s);
     else e = launch_persistent(k_mixed_assemble<K>, a, MIX_THREADS, C::smemA, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
-    if (inv_tpr == 4) e = launch_persistent(k_mixed_invert<K, 4>, a, InvCfg<C::P, 4>::NT, 0, a.n_list, num_sms, s);
+    if (inv_tpr == 1)
+        e = launch_persistent(k_mixed_invert_rr<K>, a, RrCfg<C::P>::NT, 0, (a.n_list + RrCfg<C::P>::NPC - 1) / RrCfg<C::P>::NPC,
+                              num_sms, s);
+    else if (inv_tpr == 4) e = launch_persistent(k_mixed_invert<K, 4>, a, InvCfg<C::P, 4>::NT, 0, a.n_list, num_sms, s);
     else e = launch_persistent(k_mixed_invert<K, 2>, a, InvCfg<C::P, 2>::NT, 0, a.n_list, num_sms, s);
     if (e != cudaSuccess) return e;
     return launch_persistent(k_mixed_weights<K>, a, MIX_THREADS, C::smemC, a.n_list, num_sms, s);

@@ -145,7 +145,7 @@ struct MixedArgsPublic {
     void *scratch;
     void *recs;  // [nnz] per-entry records, mixed_record_bytes() each
     int tc;      // 1: moment matrices on the tensor cores (exact BF16 slices), 0: double-float
-    int inv_tpr; // threads per matrix row in the inversion: 2 or 4
+    int inv_tpr; // threads per matrix row in the inversion: 1 (rows in registers), 2 or 4
     unsigned long long *tc_timeout;  // device counter of tensor-core waits that gave up
     void *wstore;  // [nnz][p(k)] double-float W kept between the assembly and the weights, or null
 };
