@@ -171,42 +171,55 @@ __device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__r
     double u = x * iq, v = y * iq;
     double d1, d2, d3;
     rbf_derivs(rbf, q, d1, d2, d3);
-    double up[K + 1], vp[K + 1];
-    up[0] = vp[0] = 1.0;
+    // u^t, v^t for the |r|-polynomials; x^a / a!, y^b / b! for the monomials (one multiply per
+    // element of X: on GB300 every FP64 multiply takes the FP64 pipe's time)
+    double up[K + 1], vp[K + 1], xs[K + 1], ys[K + 1];
+    up[0] = vp[0] = xs[0] = ys[0] = 1.0;
+    {
+        double xp = 1.0, yp = 1.0;
 #pragma unroll
-    for (int t = 1; t <= K; t++) {
-        up[t] = up[t - 1] * u;
-        vp[t] = vp[t - 1] * v;
+        for (int t = 1; t <= K; t++) {
+            up[t] = up[t - 1] * u;
+            vp[t] = vp[t - 1] * v;
+            xp *= x;
+            yp *= y;
+            xs[t] = xp * c_invfact2.v[t][0];
+            ys[t] = yp * c_invfact2.v[t][0];
+        }
     }
-    double qn = 1.0;      // q^n
     double iqn = 1.0;     // q^(1-n)
     double rxx = 0.0, rxy = 0.0, ryy = 0.0;
 #pragma unroll
     for (int n = 1; n <= K; n++) {
-        qn *= q;
         if (n > 1) iqn *= iq;
+        const double d1q = d1 * iqn;  // W = d1 q^(1-n) P for n >= 4
         double mono[K + 1];
 #pragma unroll
         for (int t = 0; t <= n; t++) mono[t] = up[t] * vp[n - t];
 #pragma unroll
         for (int a = n; a >= 0; a--) {
             const int e = p_of_k(n - 1) + (n - a);
-            X[e] = qn * mono[a] * c_invfact2.v[a][n - a];
+            X[e] = xs[a] * ys[n - a];
             double s = 0.0;
 #pragma unroll
             for (int t = a & 1; t <= n; t += 2) s = fma(c_rpoly.c[e][t], mono[t], s);
-            const double dr = s * iqn;
-            double wv = d1 * dr;
+            double wv;
             // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
-            if (n == 2) {
-                if (a == 2) { rxx = dr; wv = fma(d2, u * u, wv); }
-                if (a == 1) { rxy = dr; wv = fma(d2, u * v, wv); }
-                if (a == 0) { ryy = dr; wv = fma(d2, v * v, wv); }
-            } else if (n == 3) {
-                if (a == 3) wv = fma(d3, u * u * u, fma(d2, 3.0 * u * rxx, wv));
-                if (a == 2) wv = fma(d3, u * u * v, fma(d2, v * rxx + 2.0 * u * rxy, wv));
-                if (a == 1) wv = fma(d3, u * v * v, fma(d2, u * ryy + 2.0 * v * rxy, wv));
-                if (a == 0) wv = fma(d3, v * v * v, fma(d2, 3.0 * v * ryy, wv));
+            if (n <= 3) {
+                const double dr = s * iqn;
+                wv = d1 * dr;
+                if (n == 2) {
+                    if (a == 2) { rxx = dr; wv = fma(d2, u * u, wv); }
+                    if (a == 1) { rxy = dr; wv = fma(d2, u * v, wv); }
+                    if (a == 0) { ryy = dr; wv = fma(d2, v * v, wv); }
+                } else if (n == 3) {
+                    if (a == 3) wv = fma(d3, u * u * u, fma(d2, 3.0 * u * rxx, wv));
+                    if (a == 2) wv = fma(d3, u * u * v, fma(d2, v * rxx + 2.0 * u * rxy, wv));
+                    if (a == 1) wv = fma(d3, u * v * v, fma(d2, u * ryy + 2.0 * v * rxy, wv));
+                    if (a == 0) wv = fma(d3, v * v * v, fma(d2, 3.0 * v * ryy, wv));
+                }
+            } else {
+                wv = s * d1q;
             }
             W[e] = wv;
         }

@@ -286,18 +286,21 @@ __device__ __forceinline__ void stage_chunk(const MixedArgs &A, int64_t rs, int 
     if (Xd) {
         for (int t = threadIdx.x; t < nj; t += MIX_THREADS) {
             const double x = src[t * 9], y = src[t * 9 + 1];
-            double xp[K + 1], yp[K + 1];
-            xp[0] = yp[0] = 1.0;
+            // x^a / a! and y^b / b!: one FP64 multiply per element of X
+            double xs[K + 1], ys[K + 1], xp = 1.0, yp = 1.0;
+            xs[0] = ys[0] = 1.0;
 #pragma unroll
             for (int q = 1; q <= K; q++) {
-                xp[q] = xp[q - 1] * x;
-                yp[q] = yp[q - 1] * y;
+                xp *= x;
+                yp *= y;
+                xs[q] = xp * c_invfact2.v[q][0];
+                ys[q] = yp * c_invfact2.v[q][0];
             }
             double *X = Xd + t * LDX;
 #pragma unroll
             for (int e = 0; e < P; e++) {
                 const int a = elem_a(e), b = elem_degree(e) - a;
-                X[e] = xp[a] * yp[b] * c_invfact2.v[a][b];
+                X[e] = xs[a] * ys[b];
             }
 #pragma unroll
             for (int e = P; e < LDX; e++) X[e] = 0.0;
