@@ -200,7 +200,10 @@ typedef struct {
     /* per order k (index 1..8): threads per matrix row of the mixed builds' double-float
      * inversion, as the build autotuner chose them (timed once per (order, mean stencil size,
      * n_ops, precision) like the FP64 group size): 1 = each row in the registers of one thread,
-     * 2 or 4 = the matrix in shared memory; 0 for orders not built by the mixed kernels */
+     * 2 or 4 = the matrix in shared memory; 0 for orders not built by the mixed kernels.  Builds
+     * too small to time (an order with fewer than 4096 nodes) or recorded into a CUDA graph use 1.
+     * The environment variable LABFM_MIXED_INVERSION = registers, shared2 or shared4, read at
+     * each build, fixes the form instead (diagnostics). */
     int32_t mixed_inv_threads_per_row[LABFM_MAX_ORDER + 1];
 } labfm_build_info;
 

@@ -18,6 +18,8 @@
 // node of a CTA-wide order or 256 / G nodes of a grouped one.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "abf.cuh"
@@ -524,6 +526,19 @@ static int precision_nref(int precision, bool &adaptive)
     return forced ? forced - 1 : NREF_ADAPTIVE;
 }
 
+// LABFM_MIXED_INVERSION = registers | shared2 | shared4 fixes the form of the mixed builds'
+// inversion (rows in registers; 2 or 4 threads per row in shared memory) instead of the build
+// autotuner's choice (diagnostics and tests); unset or any other value: the autotuner decides.
+static int mixed_inversion_override()
+{
+    const char *v = std::getenv("LABFM_MIXED_INVERSION");
+    if (!v) return 0;
+    if (std::strcmp(v, "registers") == 0) return 1;
+    if (std::strcmp(v, "shared2") == 0) return 2;
+    if (std::strcmp(v, "shared4") == 0) return 4;
+    return 0;
+}
+
 labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, int rbf, int n_ops, const double *Cin,
                        int precision, int weight_dtype, int32_t *node_status, int64_t *n_bad_out)
 {
@@ -685,7 +700,13 @@ labfm_status run_build(labfm_ctx *ctx, const int8_t *order, int uniform_order, i
     // n_ops, precision) on the whole mixed pipeline over up to 16,384 of the order's nodes (the
     // timing runs' counters are cleared afterwards; their weights are overwritten by the build).
     auto launch_mixed = [&](int k, const int32_t *list, int64_t cnt, double deg) -> cudaError_t {
-        int tpr = 2;
+        // untimed (small or captured builds): rows in registers, the form that won every timing
+        int tpr = 1;
+        const int forced = mixed_inversion_override();
+        if (forced) {
+            ctx->info_inv_tpr[k] = forced;
+            return launch_mixed_raw(k, list, cnt, forced);
+        }
         const uint64_t dkey = (uint64_t)std::min(deg + 0.5, 65535.0);
         const uint64_t key = (dkey << 40) | ((uint64_t)k << 32) | (6ull << 24) | ((uint64_t)n_ops << 16) |
                              ((uint64_t)base_prec << 8);

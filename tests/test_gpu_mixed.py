@@ -127,3 +127,36 @@ def test_mixed_matches_fp64_build_derivatives():
         outs.append(L.apply(torch.from_numpy(f).to(dev)).cpu().numpy())
     err = np.linalg.norm(outs[1] - outs[0], axis=1) / np.linalg.norm(outs[0], axis=1)
     assert np.all(err < 1e-8), err
+
+
+@pytest.mark.parametrize("form,tpr", [("registers", 1), ("shared2", 2), ("shared4", 4)])
+@pytest.mark.parametrize("tc", [False, True])
+def test_every_inversion_form_matches_oracle(form, tpr, tc, monkeypatch):
+    """Each form of the mixed builds' Gauss-Jordan inversion (rows in registers; 2 or 4 threads
+    per row in shared memory), fixed through LABFM_MIXED_INVERSION, at orders 5 and 8: weights
+    against the oracle under the floor-aware tolerance, and the status codes of undersampled,
+    collinear and coincident stencils (order 5)."""
+    monkeypatch.setenv("LABFM_MIXED_INVERSION", form)
+    prec = "mixed_tc" if tc else "mixed"
+    for k in (5, 8):
+        ns = S.jittered_lattice(30, G.HS[k], k, seed=60 + k)
+        ops = G.OPS[k]
+        L, rp, col, w, status, _ = G.gpu_run(ns, k, ops, precision=prec)
+        assert L.get_build_info()["mixed_inv_threads_per_row"][k] == tpr
+        q = np.arange(1, ns.n, 4)
+        rp_q, col_q, idx = G.rows_of(rp, col, q)
+        r64, rld = G.oracle_refs(ns, k, ops, q, rp_q, col_q)
+        assert np.array_equal(status[q], r64["status"])
+        G.assert_weights_parity(w[idx], r64, rld, rp_q, label=f"{prec} {form} k={k}")
+        L.close()
+    xs = np.linspace(0.3, 0.7, 41)
+    xy = np.concatenate([np.stack([xs, np.full_like(xs, 0.5)], 1), [[0.1, 0.1], [0.12, 0.1], [0.1, 0.13]],
+                         [[0.8, 0.8], [0.8, 0.8]], S.uniform01(77, 80).reshape(40, 2) * 0.08 + 0.76])
+    h = np.full(len(xy), 0.06)
+    ns = S.NodeSet(xy=xy, h=h, s=h, order=np.full(len(xy), 5, np.int8), periodic=False, lo=(0.0, 0.0),
+                   hi=(1.0, 1.0))
+    L, rp, col, w, status, _ = G.gpu_run(ns, 5, ("dx", "dy", "lap"), precision=prec)
+    r64 = oracle.build_weights(ns.xy, ns.h, False, rp, col, G.c_matrix(5, ("dx", "dy", "lap")), k=5,
+                               queries=np.arange(ns.n))
+    assert np.array_equal(status, r64["status"]) and set(status.tolist()) >= {1, 2, 3}
+    L.close()
