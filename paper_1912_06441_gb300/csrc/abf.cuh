@@ -156,57 +156,75 @@ constexpr InvFact2 make_invfact2()
 }
 __constant__ InvFact2 c_invfact2 = make_invfact2();
 
-// Monomials and ABFs of one scaled offset (x, y), written to X[0..P), W[0..P).
-// In polar form q = |(x, y)|, (u, v) = (x, y)/q, degree n = a + b:
-//   X_(a,b) = q^n u^a v^b / (a! b!)          d^(a,b)|r| = q^(1-n) P_(a,b)(u, v)
-// and both use the same n+1 products u^t v^(n-t), formed once per degree.  d^(a,b)|r| has the
-// parity of a in x (|r| is even in x and y), so P_(a,b) has only the terms u^t v^(n-t) with t of
-// the parity of a: the others are skipped (their coefficients are exactly zero).  Results go
-// straight to shared memory to keep the register footprint small.
+// The coefficients of the |r|-polynomials on the scaled monomials: P_(a,b)(x, y) =
+// sum_t c[e][t] x^t y^(n-t) = sum_t c[e][t] t! (n-t)! X_(t,n-t), exact integers in double
+// (below 2^26 at order 8)
+constexpr RPolyTable make_rpolyf_table()
+{
+    RPolyTable T = make_rpoly_table();
+    double f[KMAX + 1] = {1, 1, 2, 6, 24, 120, 720, 5040, 40320};
+    for (int e = 0; e < PMAX; e++) {
+        const int n = elem_degree(e);
+        for (int t = 0; t <= n; t++) T.c[e][t] *= f[t] * f[n - t];
+    }
+    return T;
+}
+__constant__ RPolyTable c_rpolyf = make_rpolyf_table();
+
+// Monomials and ABFs of one scaled offset (x, y), written to X[0..P), W[0..P).  With
+// q = |(x, y)| and degree n = a + b:
+//   X_(a,b) = x^a y^b / (a! b!)        d^(a,b)|r| = q^(1-2n) P_(a,b)(x, y)
+// (P_(a,b) homogeneous of degree n), and P_(a,b)(x, y) = sum_t c~[e][t] X_(t,n-t) on the
+// monomials of the same degree, so that one multiply per element forms X and serves W: on GB300
+// every FP64 multiply takes the FP64 pipe's time.  d^(a,b)|r| has the parity of a in x (|r| is
+// even in x and y), so P_(a,b) has only the terms of t of the parity of a: the others are skipped
+// (their coefficients are exactly zero).  Results go straight to shared memory to keep the
+// register footprint small.
 template <int K>
 __device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__restrict__ X, double *__restrict__ W)
 {
     double q = sqrt(x * x + y * y);
     double iq = 1.0 / q;
-    double u = x * iq, v = y * iq;
     double d1, d2, d3;
     rbf_derivs(rbf, q, d1, d2, d3);
-    // u^t, v^t for the |r|-polynomials; x^a / a!, y^b / b! for the monomials (one multiply per
-    // element of X: on GB300 every FP64 multiply takes the FP64 pipe's time)
-    double up[K + 1], vp[K + 1], xs[K + 1], ys[K + 1];
-    up[0] = vp[0] = xs[0] = ys[0] = 1.0;
+    // x^a / a!, y^b / b!
+    double xs[K + 1], ys[K + 1];
+    xs[0] = ys[0] = 1.0;
     {
         double xp = 1.0, yp = 1.0;
 #pragma unroll
         for (int t = 1; t <= K; t++) {
-            up[t] = up[t - 1] * u;
-            vp[t] = vp[t - 1] * v;
             xp *= x;
             yp *= y;
             xs[t] = xp * c_invfact2.v[t][0];
             ys[t] = yp * c_invfact2.v[t][0];
         }
     }
-    double iqn = 1.0;     // q^(1-n)
-    double rxx = 0.0, rxy = 0.0, ryy = 0.0;
+    const double iq2 = iq * iq;
+    double g = iq;  // q^(1-2n)
+    double rxx = 0.0, rxy = 0.0, ryy = 0.0, u = 0.0, v = 0.0;
+    if (K >= 2) {
+        u = x * iq;
+        v = y * iq;
+    }
 #pragma unroll
     for (int n = 1; n <= K; n++) {
-        if (n > 1) iqn *= iq;
-        const double d1q = d1 * iqn;  // W = d1 q^(1-n) P for n >= 4
-        double mono[K + 1];
+        if (n > 1) g *= iq2;
+        const double d1g = d1 * g;  // W = d1 q^(1-2n) P for n >= 4
+        double mono[K + 1];          // X of this degree: mono[t] = X_(t, n-t)
 #pragma unroll
-        for (int t = 0; t <= n; t++) mono[t] = up[t] * vp[n - t];
+        for (int t = 0; t <= n; t++) mono[t] = xs[t] * ys[n - t];
 #pragma unroll
         for (int a = n; a >= 0; a--) {
             const int e = p_of_k(n - 1) + (n - a);
-            X[e] = xs[a] * ys[n - a];
+            X[e] = mono[a];
             double s = 0.0;
 #pragma unroll
-            for (int t = a & 1; t <= n; t += 2) s = fma(c_rpoly.c[e][t], mono[t], s);
+            for (int t = a & 1; t <= n; t += 2) s = fma(c_rpolyf.c[e][t], mono[t], s);
             double wv;
             // chain rule for |alpha| <= 3 (all radial derivatives), W0' only for |alpha| >= 4 (Appendix A)
             if (n <= 3) {
-                const double dr = s * iqn;
+                const double dr = s * g;
                 wv = d1 * dr;
                 if (n == 2) {
                     if (a == 2) { rxx = dr; wv = fma(d2, u * u, wv); }
@@ -219,7 +237,7 @@ __device__ __forceinline__ void eval_xw(double x, double y, int rbf, double *__r
                     if (a == 0) wv = fma(d3, v * v * v, fma(d2, 3.0 * v * ryy, wv));
                 }
             } else {
-                wv = s * d1q;
+                wv = s * d1g;
             }
             W[e] = wv;
         }
