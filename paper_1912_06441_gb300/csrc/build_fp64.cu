@@ -155,16 +155,8 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
             }
         }
 
-        double acc[TM][TN];
-#pragma unroll
-        for (int a = 0; a < TM; a++)
-#pragma unroll
-            for (int b = 0; b < TN; b++) acc[a][b] = 0.0;
-
-        const int nchunks = (ni + NB - 1) / NB;
-        for (int ch = 0; ch < nchunks; ch++) {
-            const int j0 = ch * NB;
-            const int nj = min(NB, ni - j0);
+        // X and W of the chunk's neighbours into shared memory (thread per neighbour)
+        auto stage = [&](int j0, int nj) {
             for (int t = tid; t < nj; t += G) {
                 int j = A.col[rs + j0 + t];
                 double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
@@ -179,23 +171,41 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
 #pragma unroll
                 for (int e = P; e < LDX; e++) X[e] = W[e] = 0.0;
             }
-            gsync<G>(bar);
-            if (tile_active) {
-                for (int j = 0; j < nj; j++) {
-                    const double *X = Xs + j * LDX + rg * TM;
-                    const double *W = Ws + j * LDX + cg * TN;
-                    double xv[TM], wv[TN];
+        };
+        double acc[TM][TN];
+        auto accumulate = [&](int nj) {
+            for (int j = 0; j < nj; j++) {
+                const double *X = Xs + j * LDX + rg * TM;
+                const double *W = Ws + j * LDX + cg * TN;
+                double xv[TM], wv[TN];
 #pragma unroll
-                    for (int a = 0; a < TM; a++) xv[a] = X[a];
+                for (int a = 0; a < TM; a++) xv[a] = X[a];
 #pragma unroll
-                    for (int b = 0; b < TN; b++) wv[b] = W[b];
+                for (int b = 0; b < TN; b++) wv[b] = W[b];
 #pragma unroll
-                    for (int a = 0; a < TM; a++)
+                for (int a = 0; a < TM; a++)
 #pragma unroll
-                        for (int b = 0; b < TN; b++) acc[a][b] = fma(xv[a], wv[b], acc[a][b]);
-                }
+                    for (int b = 0; b < TN; b++) acc[a][b] = fma(xv[a], wv[b], acc[a][b]);
             }
-            if (ch + 1 < nchunks) gsync<G>(bar);
+        };
+        // the first chunk apart, so that its ABF evaluation runs before the accumulators exist
+        // (most nodes have one chunk; with them live the evaluation spills to local memory)
+        const int nchunks = (ni + NB - 1) / NB;
+        const int nj0 = min(NB, ni);
+        stage(0, nj0);
+        gsync<G>(bar);
+#pragma unroll
+        for (int a = 0; a < TM; a++)
+#pragma unroll
+            for (int b = 0; b < TN; b++) acc[a][b] = 0.0;
+        if (tile_active) accumulate(nj0);
+        for (int ch = 1; ch < nchunks; ch++) {
+            const int j0 = ch * NB;
+            const int nj = min(NB, ni - j0);
+            gsync<G>(bar);
+            stage(j0, nj);
+            gsync<G>(bar);
+            if (tile_active) accumulate(nj);
         }
         // M into the augmented matrix, scaled targets into its right-hand columns
         if (tid == 0) s_flag = 0;
