@@ -6,7 +6,11 @@
 // neighbours, a prefix sum gives the CSR row pointers, a second sweep writes the column
 // indices, and each row is sorted ascending.  The distance test is evaluated in IEEE double
 // with explicitly rounded operations (no fused multiply-add), so the result does not depend
-// on the compiler's contraction choices.
+// on the compiler's contraction choices; a float pre-classification with a proven error bound
+// settles every candidate that is not within a thin shell at the radius (on GB300 the double
+// test costs FP64-pipe time per candidate), and the shell goes to the double test, so the
+// stencils are those of the double test bit for bit.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -21,6 +25,13 @@ struct Grid {
     double lo[2], L[2], halfL[2], inv_cs[2];
     int nc[2];
     int periodic;
+    // float pre-filter of the distance test (used where cell_xyf is given): box sides and half
+    // sides in float, the bound E on |dx_float - dx| (roundings of the coordinates, the
+    // difference and the wrap), and the largest (2h)^2 for which the float wrap cannot differ
+    // from the double one on a candidate near the radius
+    float Lf[2], halfLf[2];
+    float E;
+    double r2_wrap_max;
 };
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
@@ -81,14 +92,17 @@ __global__ void k_cell_assign(int64_t n, const double *__restrict__ xy, Grid g, 
 
 __global__ void k_cell_scatter(int64_t n, const double *__restrict__ xy, const int32_t *__restrict__ cell_of,
                                const int64_t *__restrict__ cell_start, int32_t *__restrict__ cursor,
-                               int32_t *__restrict__ cell_nodes, double2 *__restrict__ cell_xy)
+                               int32_t *__restrict__ cell_nodes, double2 *__restrict__ cell_xy,
+                               float2 *__restrict__ cell_xyf)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = cell_of[i];
     int64_t pos = cell_start[c] + atomicAdd(&cursor[c], 1);
     cell_nodes[pos] = (int32_t)i;
-    cell_xy[pos] = make_double2(xy[2 * i], xy[2 * i + 1]);
+    const double x = xy[2 * i], y = xy[2 * i + 1];
+    cell_xy[pos] = make_double2(x, y);
+    if (cell_xyf) cell_xyf[pos] = make_float2((float)x, (float)y);
 }
 
 // The up-to-3 distinct cell coordinates around c along one axis.
@@ -109,12 +123,34 @@ __device__ __forceinline__ int axis_cells(int c, int nc, int periodic, int out[3
     return m;
 }
 
+// The exact distance test of Sec. 2 in IEEE double, explicitly rounded (no contraction).
+__device__ __forceinline__ bool within_exact(double qx, double qy, double xi, double yi, double R2, const Grid &g)
+{
+    double dx = __dsub_rn(qx, xi);
+    double dy = __dsub_rn(qy, yi);
+    if (g.periodic) {
+        if (dx > g.halfL[0]) dx = __dsub_rn(dx, g.L[0]);
+        else if (dx < -g.halfL[0]) dx = __dadd_rn(dx, g.L[0]);
+        if (dy > g.halfL[1]) dy = __dsub_rn(dy, g.L[1]);
+        else if (dy < -g.halfL[1]) dy = __dadd_rn(dy, g.L[1]);
+    }
+    double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    return r2 < R2;
+}
+
 // One sweep over the candidate cells of node i.  WRITE = false: count; true: write col[].
+// With cell_xyf, each candidate is first classified in float: r2f, the squared distance from
+// the float coordinates, differs from the double r2 by at most D = 2E(|dx_f| + |dy_f|) + 2E^2 +
+// 2^-23 r2f (E bounds the error of dx_f and dy_f); a candidate with r2f below or above
+// (2h)^2 by more than 2D + 2^-23 (2h)^2 is decided there, and only the rest (a thin shell at the
+// radius) takes the double test.  The result is the double test's, bit for bit; on GB300 the
+// double test costs FP64-pipe time per candidate, the float one does not.
 template <bool WRITE>
 __global__ void k_sweep(int64_t n, const double *__restrict__ xy, const double *__restrict__ h, Grid g,
                         const int32_t *__restrict__ cell_of, const int64_t *__restrict__ cell_start,
                         const int32_t *__restrict__ cell_nodes, const double2 *__restrict__ cell_xy,
-                        int32_t *__restrict__ counts, const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col)
+                        const float2 *__restrict__ cell_xyf, int32_t *__restrict__ counts,
+                        const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -122,6 +158,10 @@ __global__ void k_sweep(int64_t n, const double *__restrict__ xy, const double *
     double xi = xy[2 * (int64_t)i], yi = xy[2 * (int64_t)i + 1];
     double R = 2.0 * h[i];
     double R2 = __dmul_rn(R, R);
+    // float classification only where the float wrap cannot flip a candidate near the radius
+    const bool filt = cell_xyf != nullptr && (!g.periodic || R2 <= g.r2_wrap_max);
+    const float xif = (float)xi, yif = (float)yi, R2f = (float)R2;
+    const float E = g.E;
     int c = cell_of[i];
     int cx = c % g.nc[0], cy = c / g.nc[0];
     int xs[3], ys[3];
@@ -136,17 +176,29 @@ __global__ void k_sweep(int64_t n, const double *__restrict__ xy, const double *
             for (int64_t p = s; p < e; p++) {
                 int j = cell_nodes[p];
                 if (j == i) continue;
-                double2 q = cell_xy[p];
-                double dx = __dsub_rn(q.x, xi);
-                double dy = __dsub_rn(q.y, yi);
-                if (g.periodic) {
-                    if (dx > g.halfL[0]) dx = __dsub_rn(dx, g.L[0]);
-                    else if (dx < -g.halfL[0]) dx = __dadd_rn(dx, g.L[0]);
-                    if (dy > g.halfL[1]) dy = __dsub_rn(dy, g.L[1]);
-                    else if (dy < -g.halfL[1]) dy = __dadd_rn(dy, g.L[1]);
+                bool in;
+                int decided = 0;  // 1: inside, 2: outside, 0: to the double test
+                if (filt) {
+                    const float2 qf = cell_xyf[p];
+                    float dxf = qf.x - xif, dyf = qf.y - yif;
+                    if (g.periodic) {
+                        if (dxf > g.halfLf[0]) dxf -= g.Lf[0];
+                        else if (dxf < -g.halfLf[0]) dxf += g.Lf[0];
+                        if (dyf > g.halfLf[1]) dyf -= g.Lf[1];
+                        else if (dyf < -g.halfLf[1]) dyf += g.Lf[1];
+                    }
+                    const float r2f = fmaf(dxf, dxf, dyf * dyf);
+                    const float D = 2.0f * E * (fabsf(dxf) + fabsf(dyf)) + 2.0f * E * E + 1.1920929e-7f * r2f;
+                    const float M = 2.0f * D + 1.1920929e-7f * R2f;
+                    decided = r2f < R2f - M ? 1 : (r2f > R2f + M ? 2 : 0);
                 }
-                double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                if (r2 < R2) {
+                if (decided) {
+                    in = decided == 1;
+                } else {
+                    const double2 q = cell_xy[p];
+                    in = within_exact(q.x, q.y, xi, yi, R2, g);
+                }
+                if (in) {
                     if (WRITE) col[base + cnt] = j;
                     cnt++;
                 }
@@ -172,6 +224,25 @@ __global__ void k_sweep(int64_t n, const double *__restrict__ xy, const double *
 
 }  // namespace
 
+// The float pre-filter's constants: E = 2^-21 (B + L) bounds |dx_float - dx| (B the largest
+// coordinate magnitude of the box, L its larger side: the float roundings of both coordinates,
+// of their difference and of the wrap, each at most 2^-24 of a magnitude below 2B + L), and the
+// float test is used in a periodic box only for (2h)^2 <= (0.45 L_min)^2, where a candidate whose
+// float and double wraps differ (|dx| within E of L/2) lies far outside the radius either way.
+static void set_float_filter(Grid &g, const double lo[2], const double hi[2])
+{
+    double B = 0.0, Lmax = 0.0, Lmin = 1e300;
+    for (int d = 0; d < 2; d++) {
+        B = std::max(B, std::max(std::fabs(lo[d]), std::fabs(hi[d])));
+        Lmax = std::max(Lmax, g.L[d]);
+        Lmin = std::min(Lmin, g.L[d]);
+        g.Lf[d] = (float)g.L[d];
+        g.halfLf[d] = (float)g.halfL[d];
+    }
+    g.E = (float)std::ldexp(B + Lmax, -21);
+    g.r2_wrap_max = (0.45 * Lmin) * (0.45 * Lmin);
+}
+
 labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const double *h, int periodic,
                             const double lo[2], const double hi[2], int64_t *nnz_out)
 {
@@ -192,7 +263,7 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
     double hmax;
     memcpy(&hmax, &hs[0], sizeof hmax);
 
-    Grid g;
+    Grid g{};
     g.periodic = periodic;
     double ncell_d[2];
     for (int d = 0; d < 2; d++) {
@@ -215,12 +286,13 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
         g.nc[d] = (int)ncell_d[d];
         g.inv_cs[d] = (double)g.nc[d] / g.L[d];
     }
+    set_float_filter(g, lo, hi);
     int64_t ncells = (int64_t)g.nc[0] * g.nc[1];
 
     LABFM_CUDA_TRY(ctx, ctx->cell_of.reserve(sizeof(int32_t) * n));
     LABFM_CUDA_TRY(ctx, ctx->cell_count.reserve(sizeof(int32_t) * ncells));
     LABFM_CUDA_TRY(ctx, ctx->cell_start.reserve(sizeof(int64_t) * (ncells + 1)));
-    LABFM_CUDA_TRY(ctx, ctx->cell_nodes.reserve(sizeof(int32_t) * n + sizeof(double2) * n + 64));
+    LABFM_CUDA_TRY(ctx, ctx->cell_nodes.reserve(sizeof(int32_t) * n + sizeof(double2) * n + sizeof(float2) * n + 64));
     LABFM_CUDA_TRY(ctx, ctx->counts.reserve(sizeof(int32_t) * n));
     LABFM_CUDA_TRY(ctx, ctx->row_ptr.reserve(sizeof(int64_t) * (n + 1)));
     int32_t *cell_of = ctx->cell_of.as<int32_t>();
@@ -229,6 +301,7 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
     int32_t *cell_nodes = ctx->cell_nodes.as<int32_t>();
     size_t xy_off = ((sizeof(int32_t) * n + 15) / 16) * 16;
     double2 *cell_xy = (double2 *)((char *)ctx->cell_nodes.ptr + xy_off);
+    float2 *cell_xyf = (float2 *)(cell_xy + n);
     int32_t *counts = ctx->counts.as<int32_t>();
     int64_t *row_ptr = ctx->row_ptr.as<int64_t>();
 
@@ -238,10 +311,10 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
     LABFM_CUDA_TRY(ctx, cudaGetLastError());
     LABFM_CUDA_TRY(ctx, exclusive_scan_i32_to_i64(cell_count, cell_start, ncells, ctx->scan_tmp, s));
     LABFM_CUDA_TRY(ctx, cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, s));
-    k_cell_scatter<<<nbn, NB_THREADS, 0, s>>>(n, xy, cell_of, cell_start, cell_count, cell_nodes, cell_xy);
+    k_cell_scatter<<<nbn, NB_THREADS, 0, s>>>(n, xy, cell_of, cell_start, cell_count, cell_nodes, cell_xy, cell_xyf);
     LABFM_CUDA_TRY(ctx, cudaGetLastError());
-    k_sweep<false><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, counts, nullptr,
-                                              nullptr);
+    k_sweep<false><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, cell_xyf, counts,
+                                              nullptr, nullptr);
     LABFM_CUDA_TRY(ctx, cudaGetLastError());
     LABFM_CUDA_TRY(ctx, exclusive_scan_i32_to_i64(counts, row_ptr, n, ctx->scan_tmp, s));
     int64_t *nnz_h = (int64_t *)ctx->host_small;
@@ -250,8 +323,8 @@ labfm_status run_neighbours(labfm_ctx *ctx, int64_t n, const double *xy, const d
     int64_t nnz = *nnz_h;
     if (nnz >= ((int64_t)1 << 40)) return fail(ctx, LABFM_ERR_CAPACITY, "too many stencil entries");
     LABFM_CUDA_TRY(ctx, ctx->col.reserve(sizeof(int32_t) * (nnz > 0 ? nnz : 1)));
-    k_sweep<true><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, nullptr, row_ptr,
-                                             ctx->col.as<int32_t>());
+    k_sweep<true><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, cell_xyf, nullptr,
+                                             row_ptr, ctx->col.as<int32_t>());
     LABFM_CUDA_TRY(ctx, cudaGetLastError());
     LABFM_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     ctx->n = n;
@@ -370,7 +443,7 @@ extern "C" labfm_status labfm_build_neighbours_noalloc(int device, void *stream,
     memcpy(&hmax, &hs[0], sizeof hmax);
 
     // the same grid rule as labfm_build_neighbours, capped at the scratch's cell count
-    Grid g;
+    Grid g{};
     g.periodic = periodic ? 1 : 0;
     double ncell_d[2];
     for (int d = 0; d < 2; d++) {
@@ -398,10 +471,11 @@ extern "C" labfm_status labfm_build_neighbours_noalloc(int device, void *stream,
     NA_TRY(cudaGetLastError());
     NA_TRY(exclusive_scan_i32_to_i64_ws(cell_count, cell_start, ncells, scan_tmp, NA_SCAN_ELEMS, s));
     NA_TRY(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, s));
-    k_cell_scatter<<<nbn, NB_THREADS, 0, s>>>(n, xy, cell_of, cell_start, cell_count, cell_nodes, cell_xy);
+    // (the float pre-filter needs an array the fixed scratch does not hold: the double test alone)
+    k_cell_scatter<<<nbn, NB_THREADS, 0, s>>>(n, xy, cell_of, cell_start, cell_count, cell_nodes, cell_xy, nullptr);
     NA_TRY(cudaGetLastError());
-    k_sweep<false><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, counts, nullptr,
-                                              nullptr);
+    k_sweep<false><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, nullptr, counts,
+                                              nullptr, nullptr);
     NA_TRY(cudaGetLastError());
     NA_TRY(exclusive_scan_i32_to_i64_ws(counts, row_ptr, n, scan_tmp, NA_SCAN_ELEMS, s));
     int64_t nnz = 0;
@@ -411,7 +485,7 @@ extern "C" labfm_status labfm_build_neighbours_noalloc(int device, void *stream,
     if (nnz > col_capacity) return LABFM_ERR_CAPACITY;
     if (nnz > 0) {
         k_sweep<true><<<nbn, NB_THREADS, 0, s>>>(n, xy, h, g, cell_of, cell_start, cell_nodes, cell_xy, nullptr,
-                                                 row_ptr, col);
+                                                 nullptr, row_ptr, col);
         NA_TRY(cudaGetLastError());
     }
     NA_TRY(cudaStreamSynchronize(s));
