@@ -1208,7 +1208,7 @@ __device__ __forceinline__ void weights_node(const MixedArgs &A, int64_t li, dou
         }
         if (tid < MAX_OPS) {
             s_dw2[tid] = 0.0f;
-            s_w2[tid] = 0.0f;
+            if (it == 0) s_w2[tid] = 0.0f;
         }
         __syncthreads();
         for (int ch = 0; ch < nchunks; ch++) {
@@ -1224,32 +1224,31 @@ __device__ __forceinline__ void weights_node(const MixedArgs &A, int64_t li, dou
                     s1 = df_fma(W[m + 1], Psi[(m + 1) * MAX_OPS + d], s1);
                 }
                 if (m < P) s0 = df_fma(W[m], Psi[m * MAX_OPS + d], s0);
-                const double v = df_to_double(df_add(s0, s1));
+                const df sv = df_add(s0, s1);
+                const double v = df_to_double(sv);
                 const int64_t idx = (rs + j0 + j) * n_ops + d;
                 const double wv = it == 0 ? v : A.wt[idx] + v;
                 A.wt[idx] = wv;
                 Wt[j * MAX_OPS + d] = wv;
-                Vt[j * MAX_OPS + d] = (float)v;
+                Vt[j * MAX_OPS + d] = sv.hi;  // the change in float (no FP64 conversion)
             }
             __syncthreads();
             if (A.adaptive) {
-                // per operator (warp d): the chunk's sums of dw^2 and w^2, in float
+                // per operator (warp d): the chunk's sum of dw^2 in float; the sum of w^2 is that of
+                // the first pass (w = dw_0), kept for the later ones, where w changes by a relative
+                // eta << 1 (its effect on eta_t is of the order of eta_t itself)
                 const int wp = tid >> 5, ln = tid & 31;
                 if (wp < n_ops) {
-                    float a2 = 0.0f, b2 = 0.0f;
+                    float a2 = 0.0f;
                     for (int j = ln; j < nj; j += 32) {
-                        const float vf = Vt[j * MAX_OPS + wp], wf = (float)Wt[j * MAX_OPS + wp];
+                        const float vf = Vt[j * MAX_OPS + wp];
                         a2 = fmaf(vf, vf, a2);
-                        b2 = fmaf(wf, wf, b2);
                     }
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-                        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
-                    }
+                    for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
                     if (ln == 0) {
                         s_dw2[wp] += a2;
-                        s_w2[wp] += b2;
+                        if (it == 0) s_w2[wp] += a2;
                     }
                 }
                 __syncthreads();
