@@ -7,8 +7,9 @@
 // barrier), where the p x p system is small and a whole CTA would spend its time in barrier
 // latency with most threads idle.  G per order is chosen by timing (build autotuner).
 // Neighbour data are staged in shared memory in chunks of NB neighbours: Xs[j][m], Ws[j][n]
-// (row stride LDX, a multiple of 4 so that a thread's 4 consecutive W values are one 32-byte
-// load).  The p x p assembly is tiled 2 x 4 per thread in registers across chunks.  The augmented
+// (odd row stride LDX, so that the rows of consecutive neighbours start on distinct banks).  The
+// p x p assembly is tiled 2 x 4 per thread in registers across chunks (two consecutive rows, four
+// columns CG apart).  The augmented
 // matrix [M | Chat] (Chat_alpha = C_alpha h^-|alpha|) is then eliminated in shared memory, one
 // column per step, in the space of the X staging (X is not read again), which keeps a CTA within
 // a quarter of the SM's shared memory: four CTAs per SM.
@@ -57,6 +58,7 @@ template <int K, int G> struct Cfg {
     static constexpr int TM = 2, TN = 4;
     static constexpr int RG = (P + TM - 1) / TM, CG = (P + TN - 1) / TN;
     static_assert(RG * CG <= G, "assembly tile grid exceeds the group");
+    static_assert(CG * TN <= LDX, "the tile's interleaved columns stay within a staged row");
     static constexpr int LDA = P + MAX_OPS + 1;  // augmented row stride (odd: fewer bank conflicts)
     // the augmented matrix reuses the X staging (X is not read after the assembly)
     static_assert((size_t)P * LDA <= (size_t)NB * LDX, "augmented matrix fits the X staging");
@@ -176,12 +178,15 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
         auto accumulate = [&](int nj) {
             for (int j = 0; j < nj; j++) {
                 const double *X = Xs + j * LDX + rg * TM;
-                const double *W = Ws + j * LDX + cg * TN;
+                // columns cg, cg + CG, cg + 2 CG, ...: a warp's loads of one column slot are
+                // consecutive doubles (distinct banks), where TN consecutive columns per thread would
+                // put threads 4 apart on the same banks
+                const double *W = Ws + j * LDX + cg;
                 double xv[TM], wv[TN];
 #pragma unroll
                 for (int a = 0; a < TM; a++) xv[a] = X[a];
 #pragma unroll
-                for (int b = 0; b < TN; b++) wv[b] = W[b];
+                for (int b = 0; b < TN; b++) wv[b] = W[b * C::CG];
 #pragma unroll
                 for (int a = 0; a < TM; a++)
 #pragma unroll
@@ -216,7 +221,7 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
             for (int a = 0; a < TM; a++)
 #pragma unroll
                 for (int b = 0; b < TN; b++) {
-                    int m = rg * TM + a, c = cg * TN + b;
+                    int m = rg * TM + a, c = cg + b * C::CG;
                     if (m < P && c < P) {
                         Am[m * LDA + c] = acc[a][b];
                         finite &= finite_bits(acc[a][b]);

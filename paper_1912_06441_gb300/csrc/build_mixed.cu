@@ -33,14 +33,15 @@ constexpr int NREC = 8;             // per-neighbour record: q, 1/q, u, v, W0', 
 
 template <int K> struct MCfg {
     static constexpr int P = p_of_k(K);
-    // row stride (df) of the per-neighbour arrays: even (16-byte rows for the vector loads) and
-    // 2 mod 4, so that 8-byte accesses of consecutive neighbours conflict at most 2-way
-    static constexpr int LDX = ((P + 1) / 2 * 2) % 4 == 0 ? (P + 1) / 2 * 2 + 2 : (P + 1) / 2 * 2;
-    static constexpr int NB = K >= 7 ? 72 : 64;
-    static_assert(NB * PARTS <= MIX_THREADS, "one evaluation pass per chunk");
     static constexpr int TM = 2, TN = 4;
     static constexpr int RG = (P + TM - 1) / TM, CG = (P + TN - 1) / TN;
+    // row stride (df) of the per-neighbour arrays: odd, so that the 8-byte accesses of consecutive
+    // neighbours (threads) fall on distinct bank pairs, and wide enough for the tile's columns
+    static constexpr int LDX = (CG * TN > P ? CG * TN : P) | 1;
+    static constexpr int NB = K >= 7 ? 72 : 64;
+    static_assert(NB * PARTS <= MIX_THREADS, "one evaluation pass per chunk");
     static_assert(RG * CG <= MIX_THREADS, "assembly tile grid exceeds the CTA");
+    static_assert(CG * TN <= LDX, "the tile's interleaved columns stay within a staged row");
     // kernel A: Xf, Wf (df) + neighbour records
     static constexpr size_t smemA = 8 * ((size_t)2 * NB * LDX + (size_t)NB * NREC);
     // kernel C: Xd (double), Wf (df), records, Psi/rhs (df), the chunk's w~ (double) and its
@@ -380,16 +381,15 @@ __device__ __forceinline__ void assemble_node(const MixedArgs &A, int64_t li, do
         if (tile_active) {
             for (int j = 0; j < nj; j++) {
                 const df *X = Xf + j * LDX + rg * TM;
-                const df *W = Wf + j * LDX + cg * TN;
+                // columns cg, cg + CG, ...: a warp's loads of one column slot are consecutive
+                // 8-byte values (distinct banks), where four consecutive columns per thread (two
+                // 16-byte loads) put threads 4 apart on the same banks
+                const df *W = Wf + j * LDX + cg;
                 df xv[TM], wv[TN];
 #pragma unroll
                 for (int a = 0; a < TM; a++) xv[a] = X[a];
-                float4 w01 = *reinterpret_cast<const float4 *>(W);
-                float4 w23 = *reinterpret_cast<const float4 *>(W + 2);
-                wv[0] = df{w01.x, w01.y};
-                wv[1] = df{w01.z, w01.w};
-                wv[2] = df{w23.x, w23.y};
-                wv[3] = df{w23.z, w23.w};
+#pragma unroll
+                for (int b = 0; b < TN; b++) wv[b] = W[b * C::CG];
 #pragma unroll
                 for (int a = 0; a < TM; a++)
 #pragma unroll
@@ -407,7 +407,7 @@ __device__ __forceinline__ void assemble_node(const MixedArgs &A, int64_t li, do
         for (int a = 0; a < TM; a++)
 #pragma unroll
             for (int b = 0; b < TN; b++) {
-                int m = rg * TM + a, c = cg * TN + b;
+                int m = rg * TM + a, c = cg + b * C::CG;
                 if (m < P && c < P) {
                     Mg[m * P + c] = acc[a][b];
                     finite &= df_isfinite(acc[a][b]);
