@@ -97,7 +97,7 @@ struct MixedArgs {
     void *w;            // [nnz][n_ops] output
     int wdtype;
     double *wt;         // [nnz][n_ops] scratch: unscaled weights w~ in double
-    df *Mg;             // [n_list][mstride] scratch: M, then M^-1 (p x p, row-major)
+    df *Mg;             // [n_list][mstride] scratch: M (row-major), then M^-1 (column-major)
     int64_t mstride;    // elements per node in Mg (p^2)
     int *flag;          // [n_list] scratch: per-node failure bits
     Rec *recs;          // [nnz] per-entry preamble (k_mixed_records)
@@ -944,8 +944,8 @@ __device__ __forceinline__ void invert_node(const MixedArgs &A, int64_t li, InvS
     }
     __syncthreads();
     df *Mo = A.Mg + li * A.mstride;
-    for (int u = t; u < P * P; u += NT) {
-        const int rr = u / P, q = u - rr * P;
+    for (int u = t; u < P * P; u += NT) {  // column-major: element (rr, q) at q * P + rr
+        const int q = u / P, rr = u - q * P;
         Mo[u] = s_m[rr * LDM + s_src[q]];
     }
     __syncthreads();
@@ -1058,9 +1058,9 @@ __global__ void __launch_bounds__(RrCfg<p_of_k(K)>::NT, RrCfg<p_of_k(K)>::MINB) 
             if (dead) {
                 if (r == 0) A.flag[li] = 1;
             } else {
-                df *out = A.Mg + li * A.mstride + mystep * P;
+                df *out = A.Mg + li * A.mstride + mystep;  // column-major, as the shared form
 #pragma unroll
-                for (int c = 0; c < P; c++) out[sh.pivrow[nl][c]] = a[c];
+                for (int c = 0; c < P; c++) out[sh.pivrow[nl][c] * P] = a[c];
             }
         }
         __syncthreads();  // sh.pivrow and the keys are rewritten by the next group
@@ -1190,13 +1190,13 @@ __device__ __forceinline__ void weights_node(const MixedArgs &A, int64_t li, dou
         for (int t = tid; t < P * n_ops; t += MIX_THREADS) {
             int m = t / n_ops, d = t % n_ops;
             df s0 = df{0.0f, 0.0f}, s1 = s0;
-            const df *row = Mi + m * P;
+            const df *col = Mi + m;  // M^-1 is column-major: a warp's rows m are adjacent
             int q = 0;
             for (; q + 1 < P; q += 2) {
-                s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
-                s1 = df_fma(row[q + 1], Rhs[(q + 1) * MAX_OPS + d], s1);
+                s0 = df_fma(col[q * P], Rhs[q * MAX_OPS + d], s0);
+                s1 = df_fma(col[(q + 1) * P], Rhs[(q + 1) * MAX_OPS + d], s1);
             }
-            if (q < P) s0 = df_fma(row[q], Rhs[q * MAX_OPS + d], s0);
+            if (q < P) s0 = df_fma(col[q * P], Rhs[q * MAX_OPS + d], s0);
             Psi[m * MAX_OPS + d] = df_add(s0, s1);
         }
         // w~ (+)= W . Psi over the chunks; the residual r = C~ - sum_j X_j w~_j accumulates
