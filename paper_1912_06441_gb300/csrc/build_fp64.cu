@@ -38,7 +38,6 @@ struct NodeShared {
     double invpiv[PMAX];         // 1 / pivot of each column, reused by the back substitution
     double hpow[KMAX + 1];       // h^-n
     double inv;
-    int piv;
     int flag;  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
 };
 
@@ -125,7 +124,7 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
     double *Am = Xs;                   // [P][LDA]  augmented [M | Chat], over the X staging
     NodeShared &sh = *reinterpret_cast<NodeShared *>(Ws + NB * LDX);
     double *s_psi = sh.psi, *s_invpiv = sh.invpiv, *s_hpow = sh.hpow;
-    int &s_piv = sh.piv, &s_flag = sh.flag;
+    int &s_flag = sh.flag;
     double &s_inv = sh.inv;
 
     const int n_ops = A.n_ops;
@@ -241,7 +240,9 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
         // compares |entry| as bit patterns (non-negative doubles order like their bits; a zero
         // column gives 0, inf and NaN sort above every finite value and are flagged): integer
         // compares, where FP64 compares would take the FP64 pipe's time (7 % of the kernel at
-        // order 8, measured)
+        // order 8, measured).  The group's first warp searches, exchanges the rows and scales the
+        // column on its own, so that a column costs two group barriers (after the scaling and
+        // after the update) instead of four.
         for (int c = 0; c < P && !bad_m; c++) {
             if (tid < 32) {
                 unsigned long long best = 0ull;
@@ -262,9 +263,8 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                         br = orr;
                     }
                 }
+                if (br >= P) br = c;  // the same on every lane after the butterfly
                 if (tid == 0) {
-                    if (br >= P) br = c;
-                    s_piv = br;
                     if (best == 0ull || best >= 0x7ff0000000000000ull) {
                         s_flag |= 1;
                         s_inv = 0.0;
@@ -273,19 +273,17 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                     }
                     s_invpiv[c] = s_inv;
                 }
-            }
-            gsync<G>(bar);
-            const int pr = s_piv;
-            if (pr != c) {
-                for (int t = c + tid; t < W_; t += G) {
-                    double a = Am[c * LDA + t];
-                    Am[c * LDA + t] = Am[pr * LDA + t];
-                    Am[pr * LDA + t] = a;
+                if (br != c) {
+                    for (int t = c + tid; t < W_; t += 32) {
+                        double a = Am[c * LDA + t];
+                        Am[c * LDA + t] = Am[br * LDA + t];
+                        Am[br * LDA + t] = a;
+                    }
                 }
-                gsync<G>(bar);
+                __syncwarp();
+                const double inv = s_inv;
+                for (int r = c + 1 + tid; r < P; r += 32) Am[r * LDA + c] *= inv;
             }
-            const double inv = s_inv;
-            for (int r = c + 1 + tid; r < P; r += G) Am[r * LDA + c] *= inv;
             gsync<G>(bar);
             const int nr = P - c - 1, nc = W_ - c - 1;
             for (int t = tid; t < nr * nc; t += G) {
@@ -294,13 +292,20 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
             }
             gsync<G>(bar);
         }
-        // back substitution on the n_ops right-hand sides
-        for (int c = P - 1; c >= 0 && !bad_m; c--) {
-            if (tid < n_ops) Am[c * LDA + P + tid] *= s_invpiv[c];
+        // back substitution on the n_ops right-hand sides: the column-c step updates rows r < c
+        // with x_c; row c - 1 takes its last update there and is scaled to x_(c-1) at once (the
+        // same product as scaling it at the start of the next step)
+        if (!bad_m) {
+            if (tid < n_ops) Am[(P - 1) * LDA + P + tid] *= s_invpiv[P - 1];
             gsync<G>(bar);
+        }
+        for (int c = P - 1; c > 0 && !bad_m; c--) {
+            const double ipn = s_invpiv[c - 1];
             for (int t = tid; t < c * n_ops; t += G) {
                 int r = t / n_ops, d = t % n_ops;
-                Am[r * LDA + P + d] = fma(-Am[r * LDA + c], Am[c * LDA + P + d], Am[r * LDA + P + d]);
+                double v = fma(-Am[r * LDA + c], Am[c * LDA + P + d], Am[r * LDA + P + d]);
+                if (r == c - 1) v *= ipn;
+                Am[r * LDA + P + d] = v;
             }
             gsync<G>(bar);
         }
