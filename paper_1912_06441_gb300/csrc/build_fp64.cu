@@ -38,7 +38,8 @@ struct NodeShared {
     double invpiv[PMAX];         // 1 / pivot of each column, reused by the back substitution
     double hpow[KMAX + 1];       // h^-n
     double inv;
-    int flag;  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
+    int flag;
+    unsigned char perm[2][PMAX];  // the elimination's rows by position (two lists, alternating)  // bit 0: zero/non-finite pivot, bit 1: non-finite weight, bit 2: non-finite M
 };
 
 // The CTA's dynamic shared memory: that of one order-8 node (72-neighbour chunks), so that four
@@ -236,75 +237,98 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
         gsync<G>(bar);
         const bool bad_m = (s_flag & 4) != 0;
 
-        // Gaussian elimination with partial pivoting (first largest |pivot| wins).  The pivot search
-        // compares |entry| as bit patterns (non-negative doubles order like their bits; a zero
-        // column gives 0, inf and NaN sort above every finite value and are flagged): integer
-        // compares, where FP64 compares would take the FP64 pipe's time (7 % of the kernel at
-        // order 8, measured).  The group's first warp searches, exchanges the rows and scales the
-        // column on its own, so that a column costs two group barriers (after the scaling and
-        // after the update) instead of four.
-        for (int c = 0; c < P && !bad_m; c++) {
-            if (tid < 32) {
-                unsigned long long best = 0ull;
-                int br = P;
-                for (int r = c + tid; r < P; r += 32) {
-                    const unsigned long long v = (unsigned long long)__double_as_longlong(Am[r * LDA + c]) & 0x7fffffffffffffffull;
-                    if (v > best || (v == best && r < br)) {
-                        best = v;
-                        br = r;
-                    }
+        // Gaussian elimination with partial pivoting (first largest |pivot| wins), the rows left in
+        // place: a list of the rows by position (double-buffered, so that the update reads one list
+        // while the next is written) stands for the exchanges.  The pivot search compares |entry|
+        // as bit patterns (non-negative doubles order like their bits; a zero column gives 0, inf
+        // and NaN sort above every finite value and are flagged): integer compares, where FP64
+        // compares would take the FP64 pipe's time (7 % of the kernel at order 8, measured).
+        // Look-ahead: in the step of column c the group's first warp updates column c + 1, finds
+        // its pivot and scales it while the other warps update columns c + 2 on, so that a column
+        // costs one group barrier.
+        unsigned char *permA = sh.perm[0], *permB = sh.perm[1];
+        // pivot of column c by the first warp: `pin` lists the rows by position, `pout` receives
+        // the list with positions c and the pivot's exchanged; the column below the pivot is scaled
+        auto pivot = [&](int c, const unsigned char *pin, unsigned char *pout) {
+            unsigned long long best = 0ull;
+            int bk = P;
+            for (int k = c + tid; k < P; k += 32) {
+                const unsigned long long v = (unsigned long long)__double_as_longlong(Am[pin[k] * LDA + c]) & 0x7fffffffffffffffull;
+                if (v > best || (v == best && k < bk)) {
+                    best = v;
+                    bk = k;
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                    if (ob > best || (ob == best && orr < br)) {
-                        best = ob;
-                        br = orr;
-                    }
-                }
-                if (br >= P) br = c;  // the same on every lane after the butterfly
-                if (tid == 0) {
-                    if (best == 0ull || best >= 0x7ff0000000000000ull) {
-                        s_flag |= 1;
-                        s_inv = 0.0;
-                    } else {
-                        s_inv = 1.0 / Am[br * LDA + c];
-                    }
-                    s_invpiv[c] = s_inv;
-                }
-                if (br != c) {
-                    for (int t = c + tid; t < W_; t += 32) {
-                        double a = Am[c * LDA + t];
-                        Am[c * LDA + t] = Am[br * LDA + t];
-                        Am[br * LDA + t] = a;
-                    }
-                }
-                __syncwarp();
-                const double inv = s_inv;
-                for (int r = c + 1 + tid; r < P; r += 32) Am[r * LDA + c] *= inv;
             }
-            gsync<G>(bar);
-            const int nr = P - c - 1, nc = W_ - c - 1;
-            for (int t = tid; t < nr * nc; t += G) {
-                int r = c + 1 + t / nc, q = c + 1 + t % nc;
-                Am[r * LDA + q] = fma(-Am[r * LDA + c], Am[c * LDA + q], Am[r * LDA + q]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                if (ob > best || (ob == best && ok < bk)) {
+                    best = ob;
+                    bk = ok;
+                }
+            }
+            if (bk >= P) bk = c;  // the same on every lane after the butterfly
+            if (tid == 0) {
+                if (best == 0ull || best >= 0x7ff0000000000000ull) {
+                    s_flag |= 1;
+                    s_inv = 0.0;
+                } else {
+                    s_inv = 1.0 / Am[pin[bk] * LDA + c];
+                }
+                s_invpiv[c] = s_inv;
+            }
+            for (int k = tid; k < P; k += 32) pout[k] = pin[k == c ? bk : (k == bk ? c : k)];
+            __syncwarp();
+            const double inv = s_inv;
+            for (int k = c + 1 + tid; k < P; k += 32) Am[pout[k] * LDA + c] *= inv;
+        };
+        if (!bad_m) {
+            if (tid < 32) {
+                for (int k = tid; k < P; k += 32) permB[k] = (unsigned char)k;
+                __syncwarp();
+                pivot(0, permB, permA);
             }
             gsync<G>(bar);
         }
-        // back substitution on the n_ops right-hand sides: the column-c step updates rows r < c
-        // with x_c; row c - 1 takes its last update there and is scaled to x_(c-1) at once (the
-        // same product as scaling it at the start of the next step)
+        for (int c = 0; c + 1 < P && !bad_m; c++) {
+            const unsigned char *cur = (c & 1) ? permB : permA;  // column c's pivot at position c
+            unsigned char *nxt = (c & 1) ? permA : permB;
+            const int pr = cur[c];
+            const int nr = P - c - 1;
+            if (tid < 32) {
+                for (int k = c + 1 + tid; k < P; k += 32) {
+                    const int r = cur[k];
+                    Am[r * LDA + c + 1] = fma(-Am[r * LDA + c], Am[pr * LDA + c + 1], Am[r * LDA + c + 1]);
+                }
+                __syncwarp();
+                pivot(c + 1, cur, nxt);
+            } else {
+                const int nc = W_ - c - 2;  // columns c + 2 .. W_ - 1
+                for (int t = tid - 32; t < nr * nc; t += G - 32) {
+                    const int k = c + 1 + t / nc, q = c + 2 + t % nc;
+                    const int r = cur[k];
+                    Am[r * LDA + q] = fma(-Am[r * LDA + c], Am[pr * LDA + q], Am[r * LDA + q]);
+                }
+            }
+            gsync<G>(bar);
+        }
+        // back substitution on the n_ops right-hand sides, rows by final position: the column-c
+        // step updates positions k < c with x_c; position c - 1 takes its last update there and is
+        // scaled to x_(c-1) at once (the same product as scaling it at the start of the next step)
+        const unsigned char *fp = ((P - 1) & 1) ? permB : permA;
         if (!bad_m) {
-            if (tid < n_ops) Am[(P - 1) * LDA + P + tid] *= s_invpiv[P - 1];
+            if (tid < n_ops) Am[fp[P - 1] * LDA + P + tid] *= s_invpiv[P - 1];
             gsync<G>(bar);
         }
         for (int c = P - 1; c > 0 && !bad_m; c--) {
             const double ipn = s_invpiv[c - 1];
+            const int rc = fp[c];
             for (int t = tid; t < c * n_ops; t += G) {
-                int r = t / n_ops, d = t % n_ops;
-                double v = fma(-Am[r * LDA + c], Am[c * LDA + P + d], Am[r * LDA + P + d]);
-                if (r == c - 1) v *= ipn;
+                const int k = t / n_ops, d = t % n_ops;
+                const int r = fp[k];
+                double v = fma(-Am[r * LDA + c], Am[rc * LDA + P + d], Am[r * LDA + P + d]);
+                if (k == c - 1) v *= ipn;
                 Am[r * LDA + P + d] = v;
             }
             gsync<G>(bar);
@@ -312,7 +336,9 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
         const bool singular = (s_flag & 5) != 0;  // no weights from a failed elimination
         for (int t = tid; t < P * n_ops; t += G) {
             const int m = t / n_ops, d = t - m * n_ops;
-            s_psi[m * MAX_OPS + d] = Am[m * LDA + P + d];
+            double v = 0.0;  // a non-finite M gives no weights, and no position list is formed
+            if (!bad_m) v = Am[fp[m] * LDA + P + d];
+            s_psi[m * MAX_OPS + d] = v;
         }
         gsync<G>(bar);
 
