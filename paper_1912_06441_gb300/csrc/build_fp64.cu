@@ -315,21 +315,24 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
         }
         // back substitution on the n_ops right-hand sides, rows by final position: the column-c
         // step updates positions k < c with x_c; position c - 1 takes its last update there and is
-        // scaled to x_(c-1) at once (the same product as scaling it at the start of the next step)
+        // scaled to x_(c-1) at once (the same product as scaling it at the start of the next step),
+        // by the first n_ops threads apart from the others' updates: a multiply inside the shared
+        // loop would take FP64 pipe time in every warp of the loop, masked or not
         const unsigned char *fp = ((P - 1) & 1) ? permB : permA;
         if (!bad_m) {
             if (tid < n_ops) Am[fp[P - 1] * LDA + P + tid] *= s_invpiv[P - 1];
             gsync<G>(bar);
         }
         for (int c = P - 1; c > 0 && !bad_m; c--) {
-            const double ipn = s_invpiv[c - 1];
             const int rc = fp[c];
-            for (int t = tid; t < c * n_ops; t += G) {
+            if (tid < n_ops) {
+                const int r = fp[c - 1];
+                Am[r * LDA + P + tid] = fma(-Am[r * LDA + c], Am[rc * LDA + P + tid], Am[r * LDA + P + tid]) * s_invpiv[c - 1];
+            }
+            for (int t = tid; t < (c - 1) * n_ops; t += G) {
                 const int k = t / n_ops, d = t % n_ops;
                 const int r = fp[k];
-                double v = fma(-Am[r * LDA + c], Am[rc * LDA + P + d], Am[r * LDA + P + d]);
-                if (k == c - 1) v *= ipn;
-                Am[r * LDA + P + d] = v;
+                Am[r * LDA + P + d] = fma(-Am[r * LDA + c], Am[rc * LDA + P + d], Am[r * LDA + P + d]);
             }
             gsync<G>(bar);
         }
