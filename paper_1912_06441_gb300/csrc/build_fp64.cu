@@ -97,6 +97,29 @@ __device__ __forceinline__ bool finite_bits(double x)
     return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
+// 1 / a by Newton-Raphson iteration (r <- r + r (1 - a r), which squares the relative error of
+// r at each step) from the single-precision reciprocal of a's leading 23 mantissa bits, formed
+// with integer operations and the FP32 unit: two steps take the start's ~2^-22 to the rounding
+// of the last step (within an ulp of 1/a) in four FP64 multiply-adds.  Used for the pivots, where
+// one lane's division would hold the warp's share of the FP64 pipe for longer.  Subnormal a and
+// |a| >= 2^1022 (a reciprocal at or below the normal range) take the division.
+__device__ __forceinline__ double recip_newton(double a)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const int ef = (int)((b >> 52) & 0x7ff);  // biased exponent of a
+    if (ef < 1 || ef > 2044) return 1.0 / a;
+    const float mf = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));  // 1.f of a, in [1, 2)
+    const unsigned int rb = __float_as_uint(__frcp_rn(mf));                    // in (0.5, 1]
+    // r0 = (1 / mf) 2^-(ef - 1023) with a's sign, assembled as a double
+    const unsigned long long er = (unsigned long long)((int)((rb >> 23) & 0xff) - 127 - ef + 2046);
+    double r = __longlong_as_double((long long)((b & 0x8000000000000000ull) | (er << 52) |
+                                                ((unsigned long long)(rb & 0x7fffff) << 29)));
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
+
 // Named barrier of group g of G threads: 1..2 for G = 128, 3..6 for G = 64 (an id is never used
 // with two thread counts); the CTA-wide group uses the CTA barrier.
 template <int G> __device__ __forceinline__ int group_bar(int g) { return (G == 128 ? 1 : 3) + g; }
@@ -148,7 +171,7 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
             return;
         }
         const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], hi = A.h[i];
-        const double ihi = 1.0 / hi;
+        const double ihi = recip_newton(hi);
         if (tid == 0) {
             double s = 1.0;
             for (int t = 0; t <= K; t++) {
@@ -274,7 +297,7 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                     s_flag |= 1;
                     s_inv = 0.0;
                 } else {
-                    s_inv = 1.0 / Am[pin[bk] * LDA + c];
+                    s_inv = recip_newton(Am[pin[bk] * LDA + c]);
                 }
                 s_invpiv[c] = s_inv;
             }
