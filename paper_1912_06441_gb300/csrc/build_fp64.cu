@@ -46,6 +46,33 @@ struct NodeShared {
 // CTAs fit an SM; a CTA of NG = 256 / G groups gives each group a 1/NG share.
 constexpr size_t SMEM_CTA = (sizeof(double) * ((size_t)2 * 72 * 45) + sizeof(NodeShared) + 15) / 16 * 16;
 
+// Register tile (rows x columns of M per thread) of the assembly for p = P, staged row stride LDX
+// and G threads: the shape of at most 8 accumulators that needs the fewest FP64 warp instructions
+// per neighbour, (warps holding a tile) x (tile size).  A warp's FP64 instruction takes the pipe's
+// time for all 32 lanes, masked or not, so a shape that leaves lanes of the last warp idle, or
+// pads rows or columns, costs what it wastes (2 x 4 at order 7 needs 6 warps x 8 = 48 where
+// 1 x 5 needs 8 x 5 = 40).  Ties keep the earlier, larger shape.
+struct TileShape {
+    int m, n;
+};
+constexpr TileShape pick_tile(int P, int LDX, int G)
+{
+    constexpr TileShape cands[] = {{2, 4}, {4, 2}, {1, 7}, {2, 3}, {3, 2}, {1, 6}, {1, 5},
+                                   {1, 4}, {2, 2}, {1, 3}, {1, 2}, {1, 1}};
+    TileShape best{0, 0};
+    long best_cost = 0;
+    for (const TileShape t : cands) {
+        const int rg = (P + t.m - 1) / t.m, cg = (P + t.n - 1) / t.n;
+        if (rg * cg > G || cg * t.n > LDX || rg * t.m > LDX) continue;
+        const long cost = (long)((rg * cg + 31) / 32) * t.m * t.n;
+        if (best.m == 0 || cost < best_cost) {
+            best = t;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 template <int K, int G> struct Cfg {
     static constexpr int P = p_of_k(K);
     static constexpr int LDX = (P + 3) / 4 * 4 + 1;  // odd: rows of consecutive neighbours on distinct banks
@@ -55,7 +82,9 @@ template <int K, int G> struct Cfg {
     static constexpr size_t GROUP_SMEM = (SMEM_CTA / NG) / 16 * 16;
     static constexpr int NB_FIT = (int)((GROUP_SMEM - sizeof(NodeShared)) / (sizeof(double) * 2 * LDX));
     static constexpr int NB = NB_FIT < 72 ? NB_FIT : 72;
-    static constexpr int TM = 2, TN = 4;
+    static constexpr TileShape TILE = pick_tile(P, LDX, G);
+    static_assert(TILE.m > 0, "no register tile of at most 8 accumulators fits the group");
+    static constexpr int TM = TILE.m, TN = TILE.n;
     static constexpr int RG = (P + TM - 1) / TM, CG = (P + TN - 1) / TN;
     static_assert(RG * CG <= G, "assembly tile grid exceeds the group");
     static_assert(CG * TN <= LDX, "the tile's interleaved columns stay within a staged row");
