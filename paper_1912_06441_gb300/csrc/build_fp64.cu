@@ -87,6 +87,14 @@ template <int K, int G> struct Cfg {
     static constexpr int TM = TILE.m, TN = TILE.n;
     static constexpr int RG = (P + TM - 1) / TM, CG = (P + TN - 1) / TN;
     static_assert(RG * CG <= G, "assembly tile grid exceeds the group");
+    // The last, partly filled warp of tiles takes its tiles' elements one per lane and slot where
+    // that needs fewer FP64 instructions per neighbour than a tile (order 8: 18 tiles = 144
+    // elements in 5 slots instead of 8 accumulators; order 7: 105 elements in 4 instead of 5).
+    static constexpr int NTILE = RG * CG;
+    static constexpr int TAIL_WARP = NTILE / 32;
+    static constexpr int TAIL_ELEMS = (NTILE % 32) * TM * TN;
+    static constexpr int SLOTS = (TAIL_ELEMS + 31) / 32;
+    static constexpr bool SPLIT = NTILE % 32 != 0 && SLOTS < TM * TN;
     static_assert(CG * TN <= LDX, "the tile's interleaved columns stay within a staged row");
     static constexpr int LDA = P + MAX_OPS + 1;  // augmented row stride (odd: fewer bank conflicts)
     // the augmented matrix reuses the X staging (X is not read after the assembly)
@@ -183,7 +191,21 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
     const int n_ops = A.n_ops;
     const int W_ = P + n_ops;  // used columns of the augmented matrix
     const int rg = tid / C::CG, cg = tid % C::CG;
-    const bool tile_active = tid < C::RG * C::CG;
+    const bool tail = C::SPLIT && (tid >> 5) == C::TAIL_WARP;
+    const bool tile_active = tid < C::RG * C::CG && !tail;
+    // element of slot s of a tail-warp lane: row m and column c of M (element lane + 32 s of the
+    // tail warp's tiles, in tile order); a slot past the last element reads the zero padding
+    // column LDX - 1 of X and W and is not written
+    auto tail_elem = [&](int s, int &m, int &c) {
+        const int e = (tid & 31) + 32 * s;
+        if (e >= C::TAIL_ELEMS) {
+            m = c = LDX - 1;
+            return;
+        }
+        const int tile = C::TAIL_WARP * 32 + e / (TM * TN), w = e % (TM * TN);
+        m = (tile / C::CG) * TM + w / TN;
+        c = tile % C::CG + (w % TN) * C::CG;
+    };
 
     {
         const int64_t rs = A.row_ptr[i], re = A.row_ptr[i + 1];
@@ -245,6 +267,16 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
                     for (int b = 0; b < TN; b++) acc[a][b] = fma(xv[a], wv[b], acc[a][b]);
             }
         };
+        auto accumulate_tail = [&](int nj) {
+            int xo[C::SLOTS > 0 ? C::SLOTS : 1], wo[C::SLOTS > 0 ? C::SLOTS : 1];
+#pragma unroll
+            for (int q = 0; q < C::SLOTS; q++) tail_elem(q, xo[q], wo[q]);
+            for (int j = 0; j < nj; j++) {
+                const double *X = Xs + j * LDX, *W = Ws + j * LDX;
+#pragma unroll
+                for (int q = 0; q < C::SLOTS; q++) acc[q / TN][q % TN] = fma(X[xo[q]], W[wo[q]], acc[q / TN][q % TN]);
+            }
+        };
         // the first chunk apart, so that its ABF evaluation runs before the accumulators exist
         // (most nodes have one chunk; with them live the evaluation spills to local memory)
         const int nchunks = (ni + NB - 1) / NB;
@@ -256,6 +288,7 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
 #pragma unroll
             for (int b = 0; b < TN; b++) acc[a][b] = 0.0;
         if (tile_active) accumulate(nj0);
+        else if (tail) accumulate_tail(nj0);
         for (int ch = 1; ch < nchunks; ch++) {
             const int j0 = ch * NB;
             const int nj = min(NB, ni - j0);
@@ -263,22 +296,35 @@ __device__ __forceinline__ void build_node(const BuildArgs &A, int64_t i, double
             stage(j0, nj);
             gsync<G>(bar);
             if (tile_active) accumulate(nj);
+            else if (tail) accumulate_tail(nj);
         }
         // M into the augmented matrix, scaled targets into its right-hand columns
         if (tid == 0) s_flag = 0;
         gsync<G>(bar);
-        if (tile_active) {
+        {
             bool finite = true;
+            if (tile_active) {
 #pragma unroll
-            for (int a = 0; a < TM; a++)
+                for (int a = 0; a < TM; a++)
 #pragma unroll
-                for (int b = 0; b < TN; b++) {
-                    int m = rg * TM + a, c = cg + b * C::CG;
+                    for (int b = 0; b < TN; b++) {
+                        int m = rg * TM + a, c = cg + b * C::CG;
+                        if (m < P && c < P) {
+                            Am[m * LDA + c] = acc[a][b];
+                            finite &= finite_bits(acc[a][b]);
+                        }
+                    }
+            } else if (tail) {
+#pragma unroll
+                for (int q = 0; q < C::SLOTS; q++) {
+                    int m, c;
+                    tail_elem(q, m, c);
                     if (m < P && c < P) {
-                        Am[m * LDA + c] = acc[a][b];
-                        finite &= finite_bits(acc[a][b]);
+                        Am[m * LDA + c] = acc[q / TN][q % TN];
+                        finite &= finite_bits(acc[q / TN][q % TN]);
                     }
                 }
+            }
             // a non-finite entry of M (a neighbour on top of node i: singular ABFs)
             if (!finite) atomicOr(&s_flag, 4);
         }
